@@ -1,0 +1,221 @@
+"""Independent pure-Python APAX mini-codec for tiny inputs (test helper).
+
+A second, deliberately different implementation of the frozen bitstream
+reading, used only to cross-check the C oracle on small random arrays.  It
+rounds with exact rationals (``fractions.Fraction``) and assembles packets as
+one big Python integer, where the oracle uses integer shifts and a bit
+writer.  Paper passages: Sec. 6 (blocks, attenuator, redundancy remover,
+one-block-lag stream decision, 4/6-byte headers, BFPE groups of 4 and JEE
+tokens) and Sec. 4 (profiler formula).
+"""
+from __future__ import annotations
+
+import math
+import struct
+from fractions import Fraction
+
+import numpy as np
+
+INFO = {  # dtype -> (code, bytes, W, Q, header bits)
+    np.dtype(np.int8): (1, 1, 8, None, 32),
+    np.dtype(np.int16): (2, 2, 16, None, 32),
+    np.dtype(np.int32): (3, 4, 32, None, 32),
+    np.dtype(np.float32): (4, 4, 32, 23, 48),
+    np.dtype(np.float64): (5, 8, 32, 29, 48),
+}
+
+
+def atten(c: int) -> Fraction:
+    """a(c) = (256 - m) 2^-(8+k), k = c>>7, m = c&127; a(4095) = 0."""
+    if c == 4095:
+        return Fraction(0)
+    return Fraction(256 - (c & 127), 2 ** (8 + (c >> 7)))
+
+
+def rne(fr: Fraction) -> int:
+    return round(fr)  # Fraction.__round__ rounds half to even
+
+
+def signed_w(v: int, W: int) -> int:
+    v &= (1 << W) - 1
+    return v - (1 << W) if v >> (W - 1) else v
+
+
+def nbits(v: int) -> int:
+    if v == 0:
+        return 0
+    return (v.bit_length() + 1) if v > 0 else ((-v - 1).bit_length() + 1)
+
+
+def block_exp(vals) -> int:
+    m = max((abs(Fraction(float(v))) for v in vals), default=Fraction(0))
+    if m == 0:
+        return 0
+    return math.frexp(float(m))[1]
+
+
+def quant(x, dt, c, Eb):
+    W, Q = INFO[dt][2], INFO[dt][3]
+    if Q is None:
+        return [rne(Fraction(int(v)) * atten(c)) for v in x]
+    return [rne(Fraction(float(v)) * Fraction(2) ** (Q - Eb) * atten(c)) for v in x]
+
+
+def streams(q, W):
+    n = len(q)
+    s0 = [signed_w(v, W) for v in q]
+    s1 = [signed_w(q[i] - (q[i - 1] if i else 0), W) for i in range(n)]
+    s2 = []
+    for i in range(n):
+        if i == 0:
+            v = q[0]
+        elif i == 1:
+            v = q[1] - q[0]
+        else:
+            v = q[i] - 2 * q[i - 1] + q[i - 2]
+        s2.append(signed_w(v, W))
+    return [s0, s1, s2]
+
+
+def exps(u):
+    out = []
+    for g in range(len(u) // 4):
+        e = max(nbits(v) for v in u[4 * g:4 * g + 4])
+        out.append(32 if e == 31 else e)
+    return out
+
+
+def tokens(e):
+    """Greedy JEE token list as nibbles."""
+    def absol(v):
+        v = min(v, 31)
+        return [14 + (v >> 4), v & 15]
+    nib = absol(e[0])
+    d = [None] + [e[i] - e[i - 1] for i in range(1, len(e))]
+    i = 1
+    while i < len(e):
+        if i + 1 < len(e) and abs(d[i]) <= 1 and abs(d[i + 1]) <= 1:
+            nib.append(3 * (d[i] + 1) + (d[i + 1] + 1))
+            i += 2
+        elif abs(d[i]) <= 2:
+            nib.append(11 + d[i])
+            i += 1
+        else:
+            nib += absol(e[i])
+            i += 1
+    return nib
+
+
+def pkt_bits(u, H):
+    e = exps(u)
+    return H + 4 * len(tokens(e)) + 4 * sum(e)
+
+
+def build_packet(u, s, c, Eb, H, plen):
+    e = exps(u)
+    val, pos = 0, 0
+
+    def put(v, n):
+        nonlocal val, pos
+        val |= (v & ((1 << n) - 1)) << pos
+        pos += n
+
+    put(s, 2)
+    put(c, 12)
+    put(plen, 18)
+    if H == 48:
+        put(Eb & 0xFFFF, 16)
+    for t in tokens(e):
+        put(t, 4)
+    for g, eg in enumerate(e):
+        for v in u[4 * g:4 * g + 4]:
+            if eg:
+                put(v, eg)
+    return val.to_bytes(plen, "little")
+
+
+def _blocks(x, N):
+    return [x[j:j + N] for j in range(0, len(x), N)]
+
+
+def _padded_q(xb, dt, c, Eb):
+    q = quant(xb, dt, c, Eb)
+    G = (len(q) + 3) // 4
+    return q + [q[-1]] * (4 * G - len(q))
+
+
+def _best(xb, dt):
+    W, H = INFO[dt][2], INFO[dt][4]
+    Eb = block_exp(xb) if INFO[dt][3] else 0
+    q = _padded_q(xb, dt, 0, Eb)
+    sizes = [pkt_bits(u, H) for u in streams(q, W)]
+    return sizes.index(min(sizes))
+
+
+def minpacket(L, H):
+    G = (L + 3) // 4
+    return 4 * -(-(H + 8 + 4 * ((G - 1 + 1) // 2)) // 32)
+
+
+def budget(L, size, num, den, H):
+    return max((L * size * den // (4 * num)) * 4, minpacket(L, H))
+
+
+def encode(x: np.ndarray, N: int, mode: int, num=1, den=1, code=0) -> bytes:
+    dt = x.dtype
+    code_dt, size, W, Q, H = INFO[dt]
+    x = list(x.reshape(-1).tolist())
+    n = len(x)
+    blocks = _blocks(x, N)
+    nb = len(blocks)
+    best = [_best(b, dt) for b in blocks]
+    packets = []
+    B = budget(N, size, num, den, H) if mode == 0 else 0
+    for j, xb in enumerate(blocks):
+        s = best[0] if j == 0 else best[j - 1]
+        Eb = block_exp(xb) if Q else 0
+        if mode == 1:
+            c = code
+            u = streams(_padded_q(xb, dt, c, Eb), W)[s]
+            plen = 4 * -(-pkt_bits(u, H) // 32)
+        else:
+            bud = budget(len(xb), size, num, den, H)
+
+            def fits(cc):
+                uu = streams(_padded_q(xb, dt, cc, Eb), W)[s]
+                return 4 * -(-pkt_bits(uu, H) // 32) <= bud
+            if fits(0):
+                c = 0
+            else:
+                lo, hi = 0, 4095
+                while hi - lo > 1:
+                    mid = (lo + hi) // 2
+                    if fits(mid):
+                        hi = mid
+                    else:
+                        lo = mid
+                c = hi
+            u = streams(_padded_q(xb, dt, c, Eb), W)[s]
+            plen = bud
+        packets.append(build_packet(u, s, c, Eb, H, plen))
+    head = b"APX1" + bytes([1, code_dt, mode, 1 if mode == 1 else 0])
+    head += struct.pack("<IHHIQ", N, code if mode == 1 else 0, 0, B, n)
+    payload = b"".join(packets)
+    head += struct.pack("<Q", len(payload)) + b"\0" * 4
+    table = b""
+    if mode == 1:
+        offs, pos = [], 0
+        for p in packets:
+            offs.append(pos // 4)
+            pos += len(p)
+        table = struct.pack(f"<{nb}I", *offs)
+        table += b"\0" * ((-len(table)) % 8)
+    return head + table + payload
+
+
+def corr(sxx, sxy, syy):
+    if sxx == 0 and syy == 0:
+        return 1.0
+    if sxx == 0 or syy == 0:
+        return 0.0
+    return sxy / math.sqrt(sxx * syy)
