@@ -1,0 +1,212 @@
+/*
+ * apax.h -- C ABI of the GB300 APAX codec library (libapax_gb300.so).
+ *
+ * The library implements the data-parallel hot path of the APAX universal
+ * numerical encoder and profiler of Wegener, "Universal Numerical Encoder and
+ * Profiler Reduces Computing's Memory Wall with Software, FPGA, and SoC
+ * Implementations" (arXiv 1303.4994):
+ *   - Sec. 6 (encoder block diagram): blocks of 64..16384 samples, a per-block
+ *     attenuator, a redundancy remover choosing among the data and its
+ *     derivatives with the decision of block j carried in block j+1's header,
+ *     and a 4-byte (integer) or 6-byte (float) block header;
+ *   - Sec. 6 (bit packer): block floating point with one exponent per group of
+ *     4 samples and joint exponent encoding of the exponents;
+ *   - Sec. 4 (profiler): a sweep over encoding settings reporting
+ *     r = sum(xy) / sqrt(sum(x^2) sum(y^2)) and a recommended setting at a
+ *     correlation target.
+ * The exact bitstream (field layout, derivative set, attenuation values,
+ * rounding, fixed-rate search, container) follows the readings listed with
+ * the project's design notes; the paper leaves those open.
+ *
+ * Conventions for every call:
+ *   - Pointers named x, y, out, in, workspace, res, points and summary are
+ *     DEVICE pointers unless the comment says host.  res / points / summary
+ *     may also be host-pinned memory mapped into the device address space.
+ *   - The caller owns every buffer.  The library never allocates device
+ *     memory and never synchronises the stream inside an asynchronous call.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).
+ *   - The return value reports argument errors found on the host (0 = the
+ *     work was enqueued).  Errors that depend on the data (non-finite input,
+ *     corrupt stream, output capacity, timeout) are written by the kernels to
+ *     res->status when the work completes; read it after synchronising.
+ *   - Asynchronous calls only enqueue kernels and cudaMemsetAsync; they may be
+ *     captured in a CUDA graph.
+ */
+#ifndef APAX_GB300_H
+#define APAX_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Element types (Sec. 7 datasets: int8/16/32 and 32/64-bit floats). */
+typedef enum { APAX_I8 = 1, APAX_I16 = 2, APAX_I32 = 3, APAX_F32 = 4, APAX_F64 = 5 } apax_dtype;
+
+/* Encoding modes (Sec. 6 adaptive loop: a target packet size, or a fixed
+ * attenuation for a quality target). */
+typedef enum { APAX_FIXED_RATE = 0, APAX_FIXED_QUALITY = 1 } apax_mode;
+
+/* Status codes: returned by calls (host-side checks) and written to
+ * apax_result.status (data-dependent errors). */
+enum {
+    APAX_OK = 0,
+    APAX_ERR_INVALID_ARG = -1, /* bad pointer, count, mode, code, or dtype/n mismatch on decode */
+    APAX_ERR_BLOCK_SIZE = -2,  /* block size outside 64..16384 or not a multiple of 4 (Sec. 6) */
+    APAX_ERR_DTYPE = -3,       /* unknown element type */
+    APAX_ERR_RATE = -4,        /* fixed-rate budget below the all-zero packet or above 2^18 B */
+    APAX_ERR_CAPACITY = -5,    /* output or workspace smaller than required */
+    APAX_ERR_TOO_LARGE = -6,   /* payload beyond 2^32 words (offset table limit) */
+    APAX_ERR_CUDA = -7,        /* a CUDA runtime call failed */
+    APAX_ERR_NONFINITE = -8,   /* NaN or infinity in a float input */
+    APAX_ERR_CORRUPT = -9,     /* malformed stream (header, tokens, offsets, lengths) */
+    APAX_ERR_TIMEOUT = -10     /* a bounded device wait expired (offset scan) */
+};
+
+/* Encoding parameters.
+ *   block_size  N, 64..16384, multiple of 4 (Sec. 6).  256 is the default.
+ *   mode        APAX_FIXED_RATE or APAX_FIXED_QUALITY.
+ *   rate_num, rate_den   fixed rate num:den (e.g. 4:1): every full block's
+ *               packet is exactly floor(N*size*den / (4*num))*4 bytes.
+ *   atten_code  fixed-quality attenuation code c in 0..4095: k = c >> 7,
+ *               m = c & 127, a(c) = (256 - m) 2^-(8+k); 4095 zeroes the data;
+ *               0 is lossless for integer types.
+ */
+typedef struct {
+    uint32_t block_size;
+    int32_t mode;
+    uint32_t rate_num;
+    uint32_t rate_den;
+    uint32_t atten_code;
+    uint32_t reserved;
+} apax_params;
+
+/* Completion record written by the device when a call's work finishes:
+ * status (APAX_OK or a negative code) and, for encode, the container size in
+ * bytes; for decode, the number of elements written. */
+typedef struct {
+    int32_t status;
+    uint32_t pad;
+    uint64_t bytes;
+} apax_result;
+
+/* Size of the encoded container in bytes (host call, no device work).
+ * Fixed rate: the exact size, 40 + (nblocks-1)*B + B_last.  Fixed quality:
+ * a worst-case bound to size the output allocation.  Returns a status. */
+int apax_encoded_size(int dtype, uint64_t n, const apax_params *p, uint64_t *bytes /* host */);
+
+/* Device workspace bytes that apax_encode needs for these arguments
+ * (fixed quality: the tile status words of the offset scan). */
+int apax_workspace_size(int dtype, uint64_t n, const apax_params *p, uint64_t *bytes /* host */);
+
+/* Encode n elements of x (C order, element type dtype) into out, a container
+ * of at most out_capacity bytes: a 40-byte header, for fixed quality an
+ * offset table of nblocks 32-bit word offsets (padded to 8 bytes), then one
+ * packet per block.  workspace must hold apax_workspace_size() bytes; it is
+ * cleared on the stream before use.  res receives the status and the
+ * container size.  Calls that overlap in time on the device must use
+ * distinct workspaces. */
+int apax_encode(const void *x, int dtype, uint64_t n, const apax_params *p, void *out,
+                uint64_t out_capacity, void *workspace, uint64_t workspace_bytes,
+                apax_result *res, void *stream);
+
+/* Fixed-quality encode whose attenuation code is read on the device from
+ * summary->recommended_code (written by apax_profile), so that a
+ * profile -> encode -> decode pipeline needs no host round trip.
+ * p->mode must be APAX_FIXED_QUALITY; p->atten_code is ignored. */
+struct apax_profile_summary;
+int apax_encode_recommended(const void *x, int dtype, uint64_t n, const apax_params *p,
+                            const struct apax_profile_summary *summary, void *out,
+                            uint64_t out_capacity, void *workspace, uint64_t workspace_bytes,
+                            apax_result *res, void *stream);
+
+/* Device workspace bytes of apax_decode / apax_decode_blocks (a status word
+ * and a completion counter). */
+uint64_t apax_decode_workspace_size(void);
+
+/* Decode a container of in_bytes bytes into y (n elements of dtype).  The
+ * container header is checked on the device: a dtype or n different from the
+ * arguments gives APAX_ERR_INVALID_ARG in res->status, a malformed stream
+ * APAX_ERR_CORRUPT.  Never reads past in_bytes.  workspace: at least
+ * apax_decode_workspace_size() bytes, cleared on the stream before use. */
+int apax_decode(const void *in, uint64_t in_bytes, void *y, int dtype, uint64_t n,
+                void *workspace, uint64_t workspace_bytes, apax_result *res, void *stream);
+
+/* Random access (the offset table of fixed-quality containers, j*B for
+ * fixed rate): decode only blocks [block_begin, block_end) into y, which
+ * receives the elements of those blocks starting at y[0].  block_end must
+ * not exceed the container's block count (else APAX_ERR_INVALID_ARG in
+ * res->status). */
+int apax_decode_blocks(const void *in, uint64_t in_bytes, uint64_t block_begin,
+                       uint64_t block_end, void *y, int dtype, uint64_t n, void *workspace,
+                       uint64_t workspace_bytes, apax_result *res, void *stream);
+
+/* Profiler (Sec. 4).  One point per candidate code: the fixed-quality
+ * container size at that code and the reconstruction sums of the decoded y
+ * against x.  Each block's sums are exact and rounded once to binary64; the
+ * array totals add the block values in a fixed fan-in-16 tree, so the
+ * numbers are reproducible bit for bit. */
+typedef struct {
+    uint32_t code;   /* candidate attenuation code */
+    uint32_t flags;  /* bit 0: r >= target */
+    uint64_t bytes;  /* fixed-quality container size at this code */
+    double sx, sy, sxx, sxy, syy, sdd; /* sums of x, y, x^2, xy, y^2, (x-y)^2 */
+    double r;        /* sum(xy) / sqrt(sum(x^2) sum(y^2)) (Sec. 4) */
+} apax_profile_point;
+
+typedef struct apax_profile_summary {
+    int32_t status;            /* APAX_OK or a data error (e.g. non-finite input) */
+    int32_t recommended;       /* index of the recommended candidate */
+    uint32_t recommended_code; /* its code */
+    uint32_t flags;            /* bit 0: even the first candidate misses the target */
+    uint64_t n;                /* elements profiled */
+} apax_profile_summary;
+
+/* Default candidate ladder: c_i = 256 i, i = 0..15 (a = 4^-i, 12 dB steps). */
+#define APAX_PROFILE_DEFAULT_CANDIDATES 16
+
+/* Workspace bytes apax_profile needs for n elements, block size N and ncand
+ * candidates. */
+int apax_profile_workspace_size(int dtype, uint64_t n, uint32_t block_size, int ncand,
+                                uint64_t *bytes /* host */);
+
+/* Sweep ncand candidate codes over x.  candidates (host) must be strictly
+ * increasing multiples of 128 (power-of-two attenuations a = 2^-k); NULL
+ * selects the default ladder (ncand must then be 16).  The recommended
+ * candidate is the largest i with r_j >= target for every j <= i, else 0
+ * with summary->flags bit 0 set.  points (ncand entries) and summary are
+ * written by the device; the call is asynchronous. */
+int apax_profile(const void *x, int dtype, uint64_t n, uint32_t block_size,
+                 const uint16_t *candidates /* host */, int ncand, double target,
+                 void *workspace, uint64_t workspace_bytes, apax_profile_point *points,
+                 apax_profile_summary *summary, void *stream);
+
+/* Derived metrics of one profile point (host call): r, centred Pearson r,
+ * time-domain SNR in dB = 10 log10(sum x^2 / sum d^2), RMS residual in
+ * percent and in dB (Table 3's two RMS columns), and means and population
+ * standard deviations of x, y and d.  out receives 11 doubles in that
+ * order. */
+void apax_derived_metrics(const apax_profile_point *pt, uint64_t n, double *out /* host */);
+
+/* Test hook for the bounded device waits (no counterpart in the paper):
+ * a fixed-quality apax_encode in which tile `stall_tile` (a tile is a group
+ * of consecutive blocks) never publishes its offset, so that its successor's
+ * wait expires after about spin_cycles clock cycles and res->status becomes
+ * APAX_ERR_TIMEOUT.  The kernel still terminates; the output is invalid. */
+int apax_encode_test_stall(const void *x, int dtype, uint64_t n, const apax_params *p, void *out,
+                           uint64_t out_capacity, void *workspace, uint64_t workspace_bytes,
+                           apax_result *res, int64_t stall_tile, int64_t spin_cycles,
+                           void *stream);
+
+/* Human-readable text of a status code. */
+const char *apax_status_string(int status);
+
+/* Library version and the device architecture it was compiled for. */
+const char *apax_build_info(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* APAX_GB300_H */

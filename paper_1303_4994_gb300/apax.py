@@ -1,0 +1,320 @@
+"""Python binding of the C ABI in include/apax.h (argument marshalling only).
+
+Every step of the codec runs in the sm_103a kernels of libapax_gb300.so;
+torch supplies device memory and streams.  The library must be built
+(``paper_1303_4994_gb300.build.build()``); without it every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libapax_gb300.so")
+
+I8, I16, I32, F32, F64 = 1, 2, 3, 4, 5
+FIXED_RATE, FIXED_QUALITY = 0, 1
+TORCH_CODE = {torch.int8: I8, torch.int16: I16, torch.int32: I32, torch.float32: F32,
+              torch.float64: F64}
+CODE_TORCH = {v: k for k, v in TORCH_CODE.items()}
+ELEM_SIZE = {I8: 1, I16: 2, I32: 4, F32: 4, F64: 8}
+
+STATUS = {0: "ok", -1: "invalid argument", -2: "block size", -3: "dtype", -4: "rate",
+          -5: "capacity", -6: "too large", -7: "cuda", -8: "non-finite", -9: "corrupt",
+          -10: "timeout"}
+DEFAULT_CANDIDATES = tuple(256 * i for i in range(16))
+
+
+class ApaxError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(status, status)} ({status})")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("block_size", ctypes.c_uint32), ("mode", ctypes.c_int32),
+                ("rate_num", ctypes.c_uint32), ("rate_den", ctypes.c_uint32),
+                ("atten_code", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class Point(ctypes.Structure):
+    _fields_ = [("code", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("bytes", ctypes.c_uint64),
+                ("sx", ctypes.c_double), ("sy", ctypes.c_double), ("sxx", ctypes.c_double),
+                ("sxy", ctypes.c_double), ("syy", ctypes.c_double), ("sdd", ctypes.c_double),
+                ("r", ctypes.c_double)]
+
+
+class Summary(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("recommended", ctypes.c_int32),
+                ("recommended_code", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("n", ctypes.c_uint64)]
+
+
+POINT_BYTES = ctypes.sizeof(Point)
+SUMMARY_BYTES = ctypes.sizeof(Summary)
+RESULT_BYTES = 16
+
+_lib = None
+
+EXPORTS = ("apax_encoded_size", "apax_workspace_size", "apax_encode", "apax_encode_recommended",
+           "apax_decode_workspace_size", "apax_decode", "apax_decode_blocks",
+           "apax_profile_workspace_size", "apax_profile", "apax_derived_metrics",
+           "apax_encode_test_stall", "apax_status_string", "apax_build_info")
+
+
+def lib():
+    """Load the in-tree library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "paper_1303_4994_gb300.build.build() (nvcc, sm_103a)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, u64, i32, u32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32
+        pP, p64 = ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_uint64)
+        L.apax_encoded_size.argtypes = [i32, u64, pP, p64]
+        L.apax_workspace_size.argtypes = [i32, u64, pP, p64]
+        L.apax_encode.argtypes = [vp, i32, u64, pP, vp, u64, vp, u64, vp, vp]
+        L.apax_encode_recommended.argtypes = [vp, i32, u64, pP, vp, vp, u64, vp, u64, vp, vp]
+        L.apax_decode_workspace_size.argtypes = []
+        L.apax_decode_workspace_size.restype = u64
+        L.apax_decode.argtypes = [vp, u64, vp, i32, u64, vp, u64, vp, vp]
+        L.apax_decode_blocks.argtypes = [vp, u64, u64, u64, vp, i32, u64, vp, u64, vp, vp]
+        L.apax_profile_workspace_size.argtypes = [i32, u64, u32, i32, p64]
+        L.apax_profile.argtypes = [vp, i32, u64, u32, vp, i32, ctypes.c_double, vp, u64, vp, vp,
+                                   vp]
+        L.apax_derived_metrics.argtypes = [ctypes.POINTER(Point), u64, vp]
+        L.apax_derived_metrics.restype = None
+        L.apax_encode_test_stall.argtypes = [vp, i32, u64, pP, vp, u64, vp, u64, vp,
+                                             ctypes.c_int64, ctypes.c_int64, vp]
+        L.apax_status_string.argtypes = [i32]
+        L.apax_status_string.restype = ctypes.c_char_p
+        L.apax_build_info.argtypes = []
+        L.apax_build_info.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(st: int, what: str):
+    if st != 0:
+        raise ApaxError(st, what)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    try:
+        return TORCH_CODE[t.dtype]
+    except KeyError:
+        raise ApaxError(-3, f"unsupported dtype {t.dtype}") from None
+
+
+def params(block_size: int = 256, mode: int = FIXED_QUALITY, rate=(4, 1), code: int = 0) -> Params:
+    return Params(block_size, mode, rate[0], rate[1], code, 0)
+
+
+def encoded_size(dtype_code: int, n: int, p: Params) -> int:
+    out = ctypes.c_uint64()
+    _check(lib().apax_encoded_size(dtype_code, n, ctypes.byref(p), ctypes.byref(out)),
+           "encoded_size")
+    return out.value
+
+
+def workspace_size(dtype_code: int, n: int, p: Params) -> int:
+    out = ctypes.c_uint64()
+    _check(lib().apax_workspace_size(dtype_code, n, ctypes.byref(p), ctypes.byref(out)),
+           "workspace_size")
+    return out.value
+
+
+def decode_workspace_size() -> int:
+    return lib().apax_decode_workspace_size()
+
+
+def profile_workspace_size(dtype_code: int, n: int, block_size: int, ncand: int) -> int:
+    out = ctypes.c_uint64()
+    _check(lib().apax_profile_workspace_size(dtype_code, n, block_size, ncand, ctypes.byref(out)),
+           "profile_workspace_size")
+    return out.value
+
+
+@dataclass
+class Result:
+    status: int
+    bytes: int
+
+
+def read_result(res: torch.Tensor) -> Result:
+    v = res.view(torch.int64).cpu()
+    st = int(v[0].item()) & 0xffffffff
+    if st >= 1 << 31:
+        st -= 1 << 32
+    return Result(st, int(v[1].item()))
+
+
+def new_result(device) -> torch.Tensor:
+    return torch.zeros(RESULT_BYTES, dtype=torch.uint8, device=device)
+
+
+# ----------------------------------------------------------------- encode
+def encode_into(x: torch.Tensor, p: Params, out: torch.Tensor, workspace: torch.Tensor,
+                res: torch.Tensor, stream=None, summary: torch.Tensor | None = None):
+    """Enqueue an encode of the contiguous device tensor x into out (uint8)."""
+    xf = x.reshape(-1)
+    code = _dtype_code(xf)
+    args = (xf.data_ptr(), code, xf.numel(), ctypes.byref(p))
+    tail = (out.data_ptr(), out.numel(), workspace.data_ptr(), workspace.numel(), res.data_ptr(),
+            _stream(stream))
+    if summary is None:
+        _check(lib().apax_encode(*args, *tail), "encode")
+    else:
+        _check(lib().apax_encode_recommended(*args, summary.data_ptr(), *tail),
+               "encode_recommended")
+
+
+def encode(x: torch.Tensor, block_size: int = 256, mode: int = FIXED_QUALITY, rate=(4, 1),
+           code: int = 0, stream=None) -> torch.Tensor:
+    """Encode x (device tensor); returns the container as a uint8 tensor."""
+    assert x.is_cuda and x.is_contiguous()
+    p = params(block_size, mode, rate, code)
+    dc = _dtype_code(x)
+    cap = encoded_size(dc, x.numel(), p)
+    out = torch.empty(cap, dtype=torch.uint8, device=x.device)
+    ws = torch.empty(workspace_size(dc, x.numel(), p), dtype=torch.uint8, device=x.device)
+    res = new_result(x.device)
+    encode_into(x, p, out, ws, res, stream)
+    r = read_result(res)
+    _check(r.status, "encode (device)")
+    return out[:r.bytes]
+
+
+def encode_status(x: torch.Tensor, p: Params, stream=None) -> Result:
+    dc = _dtype_code(x)
+    cap = encoded_size(dc, x.numel(), p)
+    out = torch.empty(cap, dtype=torch.uint8, device=x.device)
+    ws = torch.empty(workspace_size(dc, x.numel(), p), dtype=torch.uint8, device=x.device)
+    res = new_result(x.device)
+    encode_into(x, p, out, ws, res, stream)
+    return read_result(res)
+
+
+def encode_test_stall(x: torch.Tensor, p: Params, stall_tile: int, spin_cycles: int) -> Result:
+    dc = _dtype_code(x)
+    cap = encoded_size(dc, x.numel(), p)
+    out = torch.empty(cap, dtype=torch.uint8, device=x.device)
+    ws = torch.empty(workspace_size(dc, x.numel(), p), dtype=torch.uint8, device=x.device)
+    res = new_result(x.device)
+    _check(lib().apax_encode_test_stall(x.data_ptr(), dc, x.numel(), ctypes.byref(p),
+                                        out.data_ptr(), cap, ws.data_ptr(), ws.numel(),
+                                        res.data_ptr(), stall_tile, spin_cycles,
+                                        _stream(None)), "encode_test_stall")
+    return read_result(res)
+
+
+# ----------------------------------------------------------------- decode
+def decode_into(stream_t: torch.Tensor, y: torch.Tensor, workspace: torch.Tensor,
+                res: torch.Tensor, stream=None, blocks=None):
+    yf = y.reshape(-1)
+    code = _dtype_code(yf)
+    if blocks is None:
+        _check(lib().apax_decode(stream_t.data_ptr(), stream_t.numel(), yf.data_ptr(), code,
+                                 yf.numel(), workspace.data_ptr(), workspace.numel(),
+                                 res.data_ptr(), _stream(stream)), "decode")
+    else:
+        b0, b1, n = blocks
+        _check(lib().apax_decode_blocks(stream_t.data_ptr(), stream_t.numel(), b0, b1,
+                                        yf.data_ptr(), code, n, workspace.data_ptr(),
+                                        workspace.numel(), res.data_ptr(), _stream(stream)),
+               "decode_blocks")
+
+
+def decode(stream_t: torch.Tensor, dtype: torch.dtype, n: int, stream=None,
+           check: bool = True):
+    """Decode a container (uint8 device tensor) into a new tensor of n elements.
+    Returns the tensor, or (tensor, Result) when check is False."""
+    y = torch.empty(n, dtype=dtype, device=stream_t.device)
+    ws = torch.empty(decode_workspace_size(), dtype=torch.uint8, device=stream_t.device)
+    res = new_result(stream_t.device)
+    decode_into(stream_t, y, ws, res, stream)
+    r = read_result(res)
+    if check:
+        _check(r.status, "decode (device)")
+        return y
+    return y, r
+
+
+def decode_blocks(stream_t: torch.Tensor, dtype: torch.dtype, n: int, b0: int, b1: int,
+                  block_size: int, stream=None):
+    L = min(n, b1 * block_size) - b0 * block_size
+    y = torch.empty(max(L, 0), dtype=dtype, device=stream_t.device)
+    ws = torch.empty(decode_workspace_size(), dtype=torch.uint8, device=stream_t.device)
+    res = new_result(stream_t.device)
+    decode_into(stream_t, y, ws, res, stream, blocks=(b0, b1, n))
+    r = read_result(res)
+    _check(r.status, "decode_blocks (device)")
+    return y
+
+
+# ----------------------------------------------------------------- profile
+def profile_into(x: torch.Tensor, block_size: int, candidates, target: float,
+                 workspace: torch.Tensor, points: torch.Tensor, summary: torch.Tensor,
+                 stream=None):
+    xf = x.reshape(-1)
+    code = _dtype_code(xf)
+    if candidates is None:
+        cptr, nc = None, 16
+    else:
+        arr = (ctypes.c_uint16 * len(candidates))(*candidates)
+        cptr, nc = ctypes.cast(arr, ctypes.c_void_p), len(candidates)
+    _check(lib().apax_profile(xf.data_ptr(), code, xf.numel(), block_size, cptr, nc, target,
+                              workspace.data_ptr(), workspace.numel(), points.data_ptr(),
+                              summary.data_ptr(), _stream(stream)), "profile")
+
+
+def profile_buffers(x: torch.Tensor, block_size: int, ncand: int):
+    dev = x.device
+    ws = torch.empty(profile_workspace_size(_dtype_code(x), x.numel(), block_size, ncand),
+                     dtype=torch.uint8, device=dev)
+    pts = torch.zeros(POINT_BYTES * ncand, dtype=torch.uint8, device=dev)
+    summ = torch.zeros(SUMMARY_BYTES, dtype=torch.uint8, device=dev)
+    return ws, pts, summ
+
+
+def read_points(points: torch.Tensor, ncand: int):
+    raw = points.cpu().numpy().tobytes()
+    return [Point.from_buffer_copy(raw, i * POINT_BYTES) for i in range(ncand)]
+
+
+def read_summary(summary: torch.Tensor) -> Summary:
+    return Summary.from_buffer_copy(summary.cpu().numpy().tobytes())
+
+
+def profile(x: torch.Tensor, block_size: int = 256, candidates=DEFAULT_CANDIDATES,
+            target: float = 0.99999, stream=None):
+    """Returns (points, summary)."""
+    nc = len(candidates)
+    ws, pts, summ = profile_buffers(x, block_size, nc)
+    profile_into(x, block_size, list(candidates), target, ws, pts, summ, stream)
+    return read_points(pts, nc), read_summary(summ)
+
+
+DERIVED = ("r", "r_centred", "snr_db", "rms_pct", "rms_db", "mean_x", "mean_y", "mean_d",
+           "std_x", "std_y", "std_d")
+
+
+def derived(point: Point, n: int) -> dict:
+    out = (ctypes.c_double * 11)()
+    lib().apax_derived_metrics(ctypes.byref(point), n, ctypes.cast(out, ctypes.c_void_p))
+    return dict(zip(DERIVED, list(out)))
+
+
+def build_info() -> str:
+    return lib().apax_build_info().decode()

@@ -1,0 +1,431 @@
+// apax_host.cu -- C ABI of the codec: argument validation, container sizes,
+// workspace layout, launch planning.  No allocation, no stream sync.
+#include <math.h>
+#include <string.h>
+
+#include "apax_block.cuh"
+#include "apax_kernels.h"
+
+using namespace apax;
+
+namespace {
+
+struct Fmt {
+    int size, W, F, H;
+};
+
+int fmt_of(int dtype, Fmt &f)
+{
+    switch (dtype) {
+    case APAX_I8: f = {1, 8, 0, 32}; return APAX_OK;
+    case APAX_I16: f = {2, 16, 0, 32}; return APAX_OK;
+    case APAX_I32: f = {4, 32, 0, 32}; return APAX_OK;
+    case APAX_F32: f = {4, 32, 1, 48}; return APAX_OK;
+    case APAX_F64: f = {8, 32, 1, 48}; return APAX_OK;
+    default: return APAX_ERR_DTYPE;
+    }
+}
+
+bool block_size_ok(uint32_t N) { return N >= 64 && N <= 16384 && (N % 4) == 0; }
+
+uint64_t pad32(uint64_t bits) { return 4 * ((bits + 31) / 32); }
+
+uint64_t minpacket(const Fmt &f, uint64_t L)
+{
+    uint64_t G = (L + 3) / 4;
+    return pad32((uint64_t)f.H + 8 + 4 * ((G - 1 + 1) / 2));
+}
+
+uint64_t budget(const Fmt &f, uint64_t L, uint32_t num, uint32_t den)
+{
+    uint64_t b = (L * (uint64_t)f.size * den / (4ull * num)) * 4;
+    uint64_t mp = minpacket(f, L);
+    return b > mp ? b : mp;
+}
+
+uint64_t table_bytes(uint64_t nb) { return ((4 * nb) + 7) / 8 * 8; }
+
+int check(int dtype, const apax_params *p, Fmt &f)
+{
+    if (!p) return APAX_ERR_INVALID_ARG;
+    int st = fmt_of(dtype, f);
+    if (st) return st;
+    if (!block_size_ok(p->block_size)) return APAX_ERR_BLOCK_SIZE;
+    if (p->mode == APAX_FIXED_RATE) {
+        if (p->rate_num == 0 || p->rate_den == 0) return APAX_ERR_RATE;
+        uint64_t B = ((uint64_t)p->block_size * f.size * p->rate_den / (4ull * p->rate_num)) * 4;
+        if (B < minpacket(f, p->block_size) || B >= (1u << 18)) return APAX_ERR_RATE;
+    } else if (p->mode == APAX_FIXED_QUALITY) {
+        if (p->atten_code > 4095) return APAX_ERR_INVALID_ARG;
+    } else {
+        return APAX_ERR_INVALID_ARG;
+    }
+    return APAX_OK;
+}
+
+// Encoder launch plan: warps per CTA limited by shared memory.
+struct Plan {
+    int wpc;
+    uint32_t pkt_words, ebuf_words;
+    size_t smem;
+    uint64_t ntiles;
+};
+
+// The shared packet buffer holds the largest possible packet, or the whole
+// fixed-rate budget when that is larger (packets are padded to it).
+Plan plan_encode(const Fmt &f, uint32_t N, uint64_t nb, uint64_t fr_budget_bytes)
+{
+    Plan pl;
+    pl.pkt_words = max_packet_words(f.H, f.W, N);
+    if (fr_budget_bytes / 4 > pl.pkt_words) pl.pkt_words = (uint32_t)(fr_budget_bytes / 4);
+    pl.ebuf_words = ((N / 4) + 3) / 4;
+    const size_t per = (size_t)(pl.pkt_words + pl.ebuf_words) * 4;
+    int wpc = 8;
+    while (wpc > 1 && (size_t)wpc * per > 200 * 1024) --wpc;
+    pl.wpc = wpc;
+    pl.smem = (size_t)wpc * per;
+    pl.ntiles = nb ? (nb + wpc - 1) / wpc : 1;
+    return pl;
+}
+
+constexpr uint64_t kWsHead = 64;  // ticket, done, status (+ padding)
+
+int cuda_fail(cudaError_t e) { return e == cudaSuccess ? APAX_OK : APAX_ERR_CUDA; }
+
+int encode_impl(const void *x, int dtype, uint64_t n, const apax_params *p,
+                const uint32_t *code_dev, void *out, uint64_t cap, void *ws, uint64_t wsb,
+                apax_result *res, int64_t stall, int64_t spin, void *stream)
+{
+    Fmt f;
+    int st = check(dtype, p, f);
+    if (st) return st;
+    if ((!x && n) || !out || !ws) return APAX_ERR_INVALID_ARG;
+    // the container is written as 32-bit words; inputs at element alignment
+    if (((uintptr_t)out & 3) || ((uintptr_t)ws & 7) || ((uintptr_t)x % f.size))
+        return APAX_ERR_INVALID_ARG;
+    uint64_t need_ws;
+    apax_workspace_size(dtype, n, p, &need_ws);
+    if (wsb < need_ws) return APAX_ERR_CAPACITY;
+    const uint32_t N = p->block_size;
+    const uint64_t nb = (n + N - 1) / N;
+    const uint64_t B = p->mode == APAX_FIXED_RATE ? budget(f, N, p->rate_num, p->rate_den) : 0;
+    const Plan pl = plan_encode(f, N, nb, B);
+    EncArgs a;
+    memset(&a, 0, sizeof a);
+    a.x = x;
+    a.n = n;
+    a.N = N;
+    a.nb = nb;
+    a.dtype = dtype;
+    a.mode = p->mode;
+    a.code = p->atten_code;
+    a.code_dev = code_dev;
+    a.out = (uint8_t *)out;
+    a.cap = cap;
+    a.pkt_words = pl.pkt_words;
+    a.ebuf_words = pl.ebuf_words;
+    a.ntiles = pl.ntiles;
+    a.res = res;
+    a.spin_limit = spin;
+    a.test_stall_tile = stall;
+    if (p->mode == APAX_FIXED_RATE) {
+        a.rate_num = p->rate_num;
+        a.rate_den = p->rate_den;
+        a.B = (uint32_t)budget(f, N, p->rate_num, p->rate_den);
+        uint64_t total;
+        apax_encoded_size(dtype, n, p, &total);
+        if (cap < total) return APAX_ERR_CAPACITY;
+        a.fr_payload = total - 40;
+        a.poff = 40;
+    } else {
+        a.poff = 40 + table_bytes(nb);
+        if (cap < a.poff) return APAX_ERR_CAPACITY;
+    }
+    uint8_t *w = (uint8_t *)ws;
+    a.ticket = (unsigned *)(w + 0);
+    a.done = (unsigned *)(w + 4);
+    a.status = (int *)(w + 8);
+    a.tiles = (unsigned long long *)(w + kWsHead);
+    cudaStream_t s = (cudaStream_t)stream;
+    st = cuda_fail(cudaMemsetAsync(ws, 0, need_ws, s));
+    if (st) return st;
+    return cuda_fail(launch_encode(a, pl.wpc, pl.smem, s));
+}
+
+int decode_impl(const void *in, uint64_t in_bytes, uint64_t b0, uint64_t b1, bool ranged,
+                void *y, int dtype, uint64_t n, void *ws, uint64_t wsb, apax_result *res,
+                void *stream)
+{
+    Fmt f;
+    int st = fmt_of(dtype, f);
+    if (st) return st;
+    if (!in || (!y && n) || !ws) return APAX_ERR_INVALID_ARG;
+    if (((uintptr_t)in & 3) || ((uintptr_t)ws & 7) || ((uintptr_t)y % f.size))
+        return APAX_ERR_INVALID_ARG;
+    if (wsb < apax_decode_workspace_size()) return APAX_ERR_CAPACITY;
+    if (b0 > b1) return APAX_ERR_INVALID_ARG;
+    DecArgs a;
+    memset(&a, 0, sizeof a);
+    a.in = (const uint8_t *)in;
+    a.in_bytes = in_bytes;
+    a.y = y;
+    a.dtype = dtype;
+    a.n = n;
+    a.b0 = b0;
+    a.b1 = b1;
+    a.ranged = ranged;
+    uint8_t *w = (uint8_t *)ws;
+    a.done = (unsigned *)(w + 4);
+    a.status = (int *)(w + 8);
+    a.res = res;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int wpc = 8;
+    // enough warps for every block of the smallest legal block size
+    const uint64_t blocks = ranged ? (b1 - b0) : (n + 63) / 64;
+    uint64_t ctas = (blocks + wpc - 1) / wpc;
+    const uint64_t cap = (uint64_t)sms * 6;
+    if (ctas > cap) ctas = cap;
+    if (ctas == 0) ctas = 1;
+    a.nctas = (unsigned)ctas;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = cuda_fail(cudaMemsetAsync(ws, 0, apax_decode_workspace_size(), s));
+    if (st) return st;
+    return cuda_fail(launch_decode(a, wpc, s));
+}
+
+}  // namespace
+
+extern "C" {
+
+int apax_encoded_size(int dtype, uint64_t n, const apax_params *p, uint64_t *bytes)
+{
+    Fmt f;
+    int st = check(dtype, p, f);
+    if (st) return st;
+    if (!bytes) return APAX_ERR_INVALID_ARG;
+    const uint32_t N = p->block_size;
+    const uint64_t nb = (n + N - 1) / N;
+    if (nb == 0) {
+        *bytes = 40;
+        return APAX_OK;
+    }
+    const uint64_t Lend = n - (nb - 1) * N;
+    if (p->mode == APAX_FIXED_RATE) {
+        *bytes = 40 + (nb - 1) * budget(f, N, p->rate_num, p->rate_den) +
+                 budget(f, Lend, p->rate_num, p->rate_den);
+    } else {
+        const uint64_t full = pad32((uint64_t)f.H + 8ull * (N / 4) + (uint64_t)f.W * N);
+        const uint64_t Gl = (Lend + 3) / 4;
+        const uint64_t last = pad32((uint64_t)f.H + 8ull * Gl + (uint64_t)f.W * 4ull * Gl);
+        *bytes = 40 + table_bytes(nb) + (nb - 1) * full + last;
+    }
+    return APAX_OK;
+}
+
+int apax_workspace_size(int dtype, uint64_t n, const apax_params *p, uint64_t *bytes)
+{
+    Fmt f;
+    int st = check(dtype, p, f);
+    if (st) return st;
+    if (!bytes) return APAX_ERR_INVALID_ARG;
+    const uint64_t nb = (n + p->block_size - 1) / p->block_size;
+    const uint64_t B =
+        p->mode == APAX_FIXED_RATE ? budget(f, p->block_size, p->rate_num, p->rate_den) : 0;
+    const Plan pl = plan_encode(f, p->block_size, nb, B);
+    *bytes = kWsHead + (p->mode == APAX_FIXED_QUALITY ? 8 * pl.ntiles : 0);
+    return APAX_OK;
+}
+
+int apax_encode(const void *x, int dtype, uint64_t n, const apax_params *p, void *out,
+                uint64_t out_capacity, void *workspace, uint64_t workspace_bytes,
+                apax_result *res, void *stream)
+{
+    return encode_impl(x, dtype, n, p, nullptr, out, out_capacity, workspace, workspace_bytes,
+                       res, -1, 1ll << 31, stream);
+}
+
+int apax_encode_recommended(const void *x, int dtype, uint64_t n, const apax_params *p,
+                            const struct apax_profile_summary *summary, void *out,
+                            uint64_t out_capacity, void *workspace, uint64_t workspace_bytes,
+                            apax_result *res, void *stream)
+{
+    if (!p || p->mode != APAX_FIXED_QUALITY || !summary) return APAX_ERR_INVALID_ARG;
+    return encode_impl(x, dtype, n, p, &summary->recommended_code, out, out_capacity, workspace,
+                       workspace_bytes, res, -1, 1ll << 31, stream);
+}
+
+int apax_encode_test_stall(const void *x, int dtype, uint64_t n, const apax_params *p, void *out,
+                           uint64_t out_capacity, void *workspace, uint64_t workspace_bytes,
+                           apax_result *res, int64_t stall_tile, int64_t spin_cycles,
+                           void *stream)
+{
+    if (!p || p->mode != APAX_FIXED_QUALITY || spin_cycles <= 0) return APAX_ERR_INVALID_ARG;
+    return encode_impl(x, dtype, n, p, nullptr, out, out_capacity, workspace, workspace_bytes,
+                       res, stall_tile, spin_cycles, stream);
+}
+
+uint64_t apax_decode_workspace_size(void) { return kWsHead; }
+
+int apax_decode(const void *in, uint64_t in_bytes, void *y, int dtype, uint64_t n,
+                void *workspace, uint64_t workspace_bytes, apax_result *res, void *stream)
+{
+    // block count is unknown on the host (N is in the container): the kernel
+    // bounds the range by the container's block count
+    return decode_impl(in, in_bytes, 0, ~0ull, false, y, dtype, n, workspace, workspace_bytes,
+                       res, stream);
+}
+
+int apax_decode_blocks(const void *in, uint64_t in_bytes, uint64_t block_begin,
+                       uint64_t block_end, void *y, int dtype, uint64_t n, void *workspace,
+                       uint64_t workspace_bytes, apax_result *res, void *stream)
+{
+    return decode_impl(in, in_bytes, block_begin, block_end, true, y, dtype, n, workspace,
+                       workspace_bytes, res, stream);
+}
+
+int apax_profile_workspace_size(int dtype, uint64_t n, uint32_t block_size, int ncand,
+                                uint64_t *bytes)
+{
+    Fmt f;
+    int st = fmt_of(dtype, f);
+    if (st) return st;
+    if (!block_size_ok(block_size)) return APAX_ERR_BLOCK_SIZE;
+    if (ncand < 1 || ncand > 32 || !bytes) return APAX_ERR_INVALID_ARG;
+    const uint64_t nb = (n + block_size - 1) / block_size;
+    const uint64_t nruns = (nb + 15) / 16;
+    const uint64_t Qn = 2 + 4 * (uint64_t)ncand;
+    const uint64_t head = kWsHead + 8 * 32;
+    const uint64_t runs = 8 * Qn * (nruns ? nruns : 1);
+    const uint64_t scratch = 8 * Qn * 2 * (((nruns + 15) / 16) + 1);
+    *bytes = head + runs + scratch;
+    return APAX_OK;
+}
+
+int apax_profile(const void *x, int dtype, uint64_t n, uint32_t block_size,
+                 const uint16_t *candidates, int ncand, double target, void *workspace,
+                 uint64_t workspace_bytes, apax_profile_point *points,
+                 apax_profile_summary *summary, void *stream)
+{
+    Fmt f;
+    int st = fmt_of(dtype, f);
+    if (st) return st;
+    if (!block_size_ok(block_size)) return APAX_ERR_BLOCK_SIZE;
+    uint16_t def[16];
+    if (!candidates) {
+        if (ncand != APAX_PROFILE_DEFAULT_CANDIDATES) return APAX_ERR_INVALID_ARG;
+        for (int i = 0; i < 16; ++i) def[i] = (uint16_t)(256 * i);
+        candidates = def;
+    }
+    if (ncand < 1 || ncand > 32 || (!x && n) || !points || !summary || !workspace)
+        return APAX_ERR_INVALID_ARG;
+    if (((uintptr_t)workspace & 15) || ((uintptr_t)x % f.size) || ((uintptr_t)points & 7) ||
+        ((uintptr_t)summary & 7))
+        return APAX_ERR_INVALID_ARG;
+    for (int i = 0; i < ncand; ++i) {
+        // power-of-two attenuations only (m = 0), strictly increasing
+        if (candidates[i] > 4095 || (candidates[i] & 127)) return APAX_ERR_INVALID_ARG;
+        if (i && candidates[i] <= candidates[i - 1]) return APAX_ERR_INVALID_ARG;
+    }
+    if (!(target == target)) return APAX_ERR_INVALID_ARG;
+    uint64_t need;
+    st = apax_profile_workspace_size(dtype, n, block_size, ncand, &need);
+    if (st) return st;
+    if (workspace_bytes < need) return APAX_ERR_CAPACITY;
+    const uint64_t nb = (n + block_size - 1) / block_size;
+    ProfArgs a;
+    memset(&a, 0, sizeof a);
+    a.x = x;
+    a.n = n;
+    a.N = block_size;
+    a.nb = nb;
+    a.dtype = dtype;
+    a.ncand = ncand;
+    for (int i = 0; i < ncand; ++i) a.codes[i] = candidates[i];
+    a.nruns = (nb + 15) / 16;
+    uint8_t *w = (uint8_t *)workspace;
+    a.done = (unsigned *)(w + 4);
+    a.status = (int *)(w + 8);
+    a.bytes = (unsigned long long *)(w + kWsHead);
+    const uint64_t Qn = 2 + 4 * (uint64_t)ncand;
+    a.run_sums = (double *)(w + kWsHead + 8 * 32);
+    a.scratch = a.run_sums + Qn * (a.nruns ? a.nruns : 1);
+    a.target = target;
+    a.points = points;
+    a.summary = summary;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = cuda_fail(cudaMemsetAsync(workspace, 0, kWsHead + 8 * 32, s));
+    if (st) return st;
+    return cuda_fail(launch_profile(a, s));
+}
+
+static double corr_host(double sxx, double sxy, double syy)
+{
+    if (sxx == 0.0 && syy == 0.0) return 1.0;
+    if (sxx == 0.0 || syy == 0.0) return 0.0;
+    double p = sxx * syy;
+    if (isfinite(p) && p >= 2.2250738585072014e-308) return sxy / sqrt(p);
+    return (sxy / sqrt(sxx)) / sqrt(syy);
+}
+
+void apax_derived_metrics(const apax_profile_point *pt, uint64_t n, double *out)
+{
+    const double sx = pt->sx, sy = pt->sy, sxx = pt->sxx, sxy = pt->sxy, syy = pt->syy,
+                 sdd = pt->sdd;
+    out[0] = corr_host(sxx, sxy, syy);
+    if (n == 0) {
+        for (int i = 1; i < 11; ++i) out[i] = 0.0;
+        return;
+    }
+    const double nn = (double)n;
+    const double vx = sxx - sx * sx / nn, vy = syy - sy * sy / nn, cv = sxy - sx * sy / nn;
+    if (vx <= 0.0 && vy <= 0.0) out[1] = 1.0;
+    else if (vx <= 0.0 || vy <= 0.0) out[1] = 0.0;
+    else out[1] = cv / sqrt(vx * vy);
+    if (sdd == 0.0) {
+        out[2] = INFINITY;
+        out[3] = 0.0;
+        out[4] = -INFINITY;
+    } else if (sxx == 0.0) {
+        out[2] = -INFINITY;
+        out[3] = INFINITY;
+        out[4] = INFINITY;
+    } else {
+        out[2] = 10.0 * log10(sxx / sdd);
+        out[3] = 100.0 * sqrt(sdd / sxx);
+        out[4] = 20.0 * log10(out[3] / 100.0);
+    }
+    const double mx = sx / nn, my = sy / nn, md = (sx - sy) / nn;
+    out[5] = mx;
+    out[6] = my;
+    out[7] = md;
+    double t = sxx / nn - mx * mx;
+    out[8] = sqrt(t > 0.0 ? t : 0.0);
+    t = syy / nn - my * my;
+    out[9] = sqrt(t > 0.0 ? t : 0.0);
+    t = sdd / nn - md * md;
+    out[10] = sqrt(t > 0.0 ? t : 0.0);
+}
+
+const char *apax_status_string(int status)
+{
+    switch (status) {
+    case APAX_OK: return "ok";
+    case APAX_ERR_INVALID_ARG: return "invalid argument";
+    case APAX_ERR_BLOCK_SIZE: return "block size outside 64..16384 or not a multiple of 4";
+    case APAX_ERR_DTYPE: return "unknown element type";
+    case APAX_ERR_RATE: return "fixed rate outside the representable packet sizes";
+    case APAX_ERR_CAPACITY: return "output or workspace too small";
+    case APAX_ERR_TOO_LARGE: return "payload beyond 2^32 words";
+    case APAX_ERR_CUDA: return "CUDA runtime error";
+    case APAX_ERR_NONFINITE: return "non-finite float input";
+    case APAX_ERR_CORRUPT: return "corrupt stream";
+    case APAX_ERR_TIMEOUT: return "bounded device wait expired";
+    default: return "unknown status";
+    }
+}
+
+const char *apax_build_info(void) { return "apax-gb300 1.0 sm_103a"; }
+
+}  // extern "C"

@@ -1,0 +1,77 @@
+// apax_kernels.h -- argument blocks and launchers shared by the host layer
+// and the kernel translation units (internal; not part of the C ABI).
+#pragma once
+
+#include <stdint.h>
+#include <cuda_runtime.h>
+
+#include "../../include/apax.h"
+
+namespace apax {
+
+struct EncArgs {
+    const void *x;
+    uint64_t n;
+    uint32_t N;
+    uint64_t nb;        // blocks
+    int dtype;
+    int mode;           // 0 fixed rate, 1 fixed quality
+    uint32_t code;      // fixed-quality code
+    const uint32_t *code_dev;  // if set: code read on the device
+    uint32_t B;         // fixed-rate budget of a full block
+    uint32_t rate_num, rate_den;
+    uint64_t fr_payload; // fixed-rate payload bytes (exact, host computed)
+    uint8_t *out;
+    uint64_t cap;
+    uint64_t poff;      // payload offset in the container
+    uint32_t pkt_words, ebuf_words;  // per-warp shared-memory layout
+    uint64_t ntiles;
+    // workspace
+    unsigned *ticket;
+    unsigned *done;
+    int *status;
+    unsigned long long *tiles;
+    long long spin_limit;      // clock cycles of a bounded wait
+    long long test_stall_tile; // test hook: this tile never publishes (-1: off)
+    apax_result *res;
+};
+
+struct DecArgs {
+    const uint8_t *in;
+    uint64_t in_bytes;
+    void *y;
+    int dtype;
+    uint64_t n;
+    uint64_t b0, b1;    // block range to decode
+    bool ranged;        // y receives blocks [b0, b1) from y[0]
+    unsigned *done;
+    int *status;
+    unsigned nctas;
+    apax_result *res;
+};
+
+struct ProfArgs {
+    const void *x;
+    uint64_t n;
+    uint32_t N;
+    uint64_t nb;
+    int dtype;
+    int ncand;
+    uint32_t codes[32];
+    uint64_t nruns;     // level-1 nodes (16 blocks each)
+    double *run_sums;   // [nruns][2 + 4*ncand]: sx, sxx, then (sy, sxy, syy, sdd) per candidate
+    unsigned long long *bytes;  // [ncand] payload bytes (atomic)
+    int *status;
+    unsigned *done;
+    unsigned nctas;
+    double target;
+    double *scratch;    // tree levels
+    apax_profile_point *points;
+    apax_profile_summary *summary;
+};
+
+cudaError_t launch_encode(const EncArgs &a, int wpc, size_t smem, cudaStream_t s);
+cudaError_t launch_decode(const DecArgs &a, int wpc, cudaStream_t s);
+cudaError_t launch_profile(const ProfArgs &a, cudaStream_t s);
+
+}  // namespace apax

@@ -1,0 +1,99 @@
+"""C-ABI checks that need no GPU: the library builds, loads and exports every
+function include/apax.h declares; host-side sizes and argument checks agree
+with the oracle's closed forms."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1303_4994_gb300 import apax as A
+from paper_1303_4994_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return A.lib()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "apax.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(apax_\w+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(A.EXPORTS)
+    assert "sm_103a" in A.build_info()
+
+
+NP = {1: np.int8, 2: np.int16, 3: np.int32, 4: np.float32, 5: np.float64}
+
+
+@pytest.mark.parametrize("dt", [1, 2, 3, 4, 5])
+def test_encoded_size_matches_oracle(lib, dt):
+    rng = np.random.default_rng(dt)
+    for _ in range(60):
+        N = int(rng.choice([64, 68, 256, 1000, 4096, 16384]))
+        n = int(rng.integers(0, 5 * N))
+        mode = int(rng.integers(0, 2))
+        num, den = [(2, 1), (3, 1), (4, 1), (6, 1), (5, 2), (1, 2)][int(rng.integers(0, 6))]
+        p = A.params(N, mode, (num, den), 0)
+        try:
+            want = O.encoded_size(NP[dt], n, N, mode, num, den, 0)
+        except O.OracleError as e:
+            with pytest.raises(A.ApaxError) as g:
+                A.encoded_size(dt, n, p)
+            assert g.value.status == e.status
+            continue
+        assert A.encoded_size(dt, n, p) == want
+
+
+def test_argument_errors(lib):
+    for N in (0, 60, 63, 66, 16388):
+        with pytest.raises(A.ApaxError) as e:
+            A.encoded_size(2, 100, A.params(N))
+        assert e.value.status == -2
+    with pytest.raises(A.ApaxError) as e:
+        A.encoded_size(9, 100, A.params(256))
+    assert e.value.status == -3
+    with pytest.raises(A.ApaxError) as e:  # 64:1 on int8 is below the all-zero packet
+        A.encoded_size(1, 1000, A.params(256, A.FIXED_RATE, (64, 1)))
+    assert e.value.status == -4
+    with pytest.raises(A.ApaxError) as e:
+        A.encoded_size(4, 1000, A.params(256, A.FIXED_QUALITY, (1, 1), 5000))
+    assert e.value.status == -1
+    assert lib.apax_status_string(-9) == b"corrupt stream"
+    # fixed-rate size of the int16 sensor workload at 4:1
+    assert A.encoded_size(2, 262144, A.params(256, A.FIXED_RATE, (4, 1))) == 131112
+
+
+def test_derived_metrics_match_oracle(lib):
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        s = rng.standard_normal(6) * 10 ** rng.uniform(-3, 3, 6)
+        s[2] = abs(s[2]); s[4] = abs(s[4]); s[5] = abs(s[5])
+        if rng.random() < 0.2:
+            s[5] = 0.0
+        n = int(rng.integers(1, 10 ** 6))
+        p = A.Point(0, 0, 0, *s.tolist(), 0.0)
+        got = A.derived(p, n)
+        want = O.derived(s, n)
+        for k in want:
+            assert got[k] == want[k] or (np.isnan(got[k]) and np.isnan(want[k])), k
+
+
+def test_profile_argument_checks(lib):
+    out = ctypes.c_uint64()
+    assert lib.apax_profile_workspace_size(4, 1000, 256, 16, ctypes.byref(out)) == 0
+    assert out.value > 0
+    assert lib.apax_profile_workspace_size(4, 1000, 256, 33, ctypes.byref(out)) == -1

@@ -1,0 +1,254 @@
+"""GPU parity: the CUDA library against the CPU oracle, through the C ABI.
+
+Bit-exact bar: encoded containers are byte-identical, decoded arrays are
+bit-identical, profiler sums and correlations are identical binary64 values.
+Sizes span several tiles (8 blocks each) with ragged tails; edge cases cover
+empty/one-sample arrays, block sizes at both limits (multi-chunk blocks),
+adversarial float values (subnormals, huge exponents, zeros), corrupt
+streams, non-finite input and the bounded-wait timeout.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1303_4994_gb300 import apax as A
+from paper_1303_4994_gb300 import build as B
+from paper_1303_4994_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+NP = {1: np.int8, 2: np.int16, 3: np.int32, 4: np.float32, 5: np.float64}
+TT = {1: torch.int8, 2: torch.int16, 3: torch.int32, 4: torch.float32, 5: torch.float64}
+UINT = {1: np.uint8, 2: np.uint16, 3: np.uint32, 4: np.uint32, 5: np.uint64}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+    A.lib()
+    torch.cuda.init()
+
+
+def _data(dt, n, rng, kind=0):
+    if dt <= 3:
+        info = np.iinfo(NP[dt])
+        if kind == 0:
+            return rng.integers(info.min, info.max, n, endpoint=True).astype(NP[dt])
+        t = np.arange(n)
+        x = np.sin(t * 0.03) * info.max * 0.6 + rng.normal(0, 3, n)
+        return np.clip(np.rint(x), info.min, info.max).astype(NP[dt])
+    if kind == 0:
+        return (rng.standard_normal(n) * np.exp(rng.uniform(-8, 8, n))).astype(NP[dt])
+    if kind == 1:
+        return np.cumsum(rng.standard_normal(n)).astype(NP[dt])
+    # adversarial: zeros, subnormals, huge values, mixed binades
+    fi = np.finfo(NP[dt])
+    x = (rng.standard_normal(n) * np.exp(rng.uniform(-80, 80, n))).astype(NP[dt])
+    x[::7] = 0
+    x[3::11] = fi.smallest_subnormal * rng.integers(1, 9, len(x[3::11]))
+    if n > 5:
+        x[5] = fi.max
+        x[4] = -fi.max / 3
+    return x
+
+
+def _gpu_encode(x, p):
+    xt = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    return A.encode(xt, p.block_size, p.mode, (p.rate_num, p.rate_den), p.atten_code)
+
+
+def _bits(a):
+    a = np.ascontiguousarray(a)
+    return a.view(UINT[O.DTYPE_CODE[a.dtype]])
+
+
+def _roundtrip(x, N, mode, rate, code):
+    n = x.size
+    want = O.encode(x, N, mode, rate[0], rate[1], code)
+    p = A.params(N, mode, rate, code)
+    got = _gpu_encode(x, p)
+    gb = got.cpu().numpy().tobytes()
+    assert len(gb) == len(want), (len(gb), len(want))
+    if gb != want:
+        diff = np.nonzero(np.frombuffer(gb, np.uint8) != np.frombuffer(want, np.uint8))[0]
+        raise AssertionError(f"container differs at byte {diff[0]} of {len(want)} "
+                             f"({len(diff)} bytes)")
+    ydt = TT[O.DTYPE_CODE[x.dtype]]
+    y = A.decode(got, ydt, n).cpu().numpy()
+    yo = O.decode(want, x.dtype, n)
+    np.testing.assert_array_equal(_bits(y), _bits(yo))
+    return got, y
+
+
+@pytest.mark.parametrize("dt", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_parity_small_all_types(dt, mode):
+    rng = np.random.default_rng(100 * dt + mode)
+    N = 256
+    for n in (1, 3, N - 1, N, N + 1, 37 * N + 13):
+        for kind in (0, 1, 2) if dt >= 4 else (0, 1):
+            x = _data(dt, n, rng, kind)
+            if mode == 1:
+                for code in (0, 300, int(rng.integers(0, 4096)), 2048 + 5, 4095):
+                    _roundtrip(x, N, 1, (1, 1), code)
+            else:
+                for rate in ((4, 1), (2, 1), (6, 1)):
+                    try:
+                        O.encoded_size(x.dtype, n, N, 0, rate[0], rate[1])
+                    except O.OracleError:
+                        continue
+                    _roundtrip(x, N, 0, rate, 0)
+
+
+@pytest.mark.parametrize("dt", [2, 4, 5])
+@pytest.mark.parametrize("N", [64, 68, 1000, 4096, 16384])
+def test_parity_block_sizes(dt, N):
+    rng = np.random.default_rng(N + dt)
+    n = 3 * N + 17
+    x = _data(dt, n, rng, 1)
+    _roundtrip(x, N, 1, (1, 1), 256)
+    _roundtrip(x, N, 1, (1, 1), 0)
+    try:
+        O.encoded_size(x.dtype, n, N, 0, 4, 1)
+        _roundtrip(x, N, 0, (4, 1), 0)
+    except O.OracleError:
+        pass
+
+
+def test_empty_array():
+    for dt in (2, 4):
+        x = np.zeros(0, dtype=NP[dt])
+        want = O.encode(x, 256, 1)
+        got = _gpu_encode(x, A.params(256, 1))
+        assert got.cpu().numpy().tobytes() == want
+        y = A.decode(got, TT[dt], 0)
+        assert y.numel() == 0
+
+
+def test_sensor_trace_full_size_fixed_rate():
+    """int16 sensor trace, 262,144 samples, fixed rate 4:1: full parity."""
+    x = synth.sensor_trace()
+    got, y = _roundtrip(x, 256, 0, (4, 1), 0)
+    assert got.numel() == 131112
+
+
+def test_decode_blocks_random_access():
+    rng = np.random.default_rng(5)
+    for mode, dt in ((1, 4), (0, 2), (1, 5)):
+        x = _data(dt, 256 * 50 + 77, rng, 1)
+        c = _gpu_encode(x, A.params(256, mode, (4, 1), 700))
+        full = O.decode(c.cpu().numpy().tobytes(), x.dtype, x.size)
+        for _ in range(10):
+            b0 = int(rng.integers(0, 51))
+            b1 = int(rng.integers(b0, 52))
+            y = A.decode_blocks(c, TT[dt], x.size, b0, b1, 256).cpu().numpy()
+            np.testing.assert_array_equal(_bits(y), _bits(full[b0 * 256:min(b1 * 256, x.size)]))
+
+
+def test_decode_rejects_mismatch_and_corruption():
+    rng = np.random.default_rng(6)
+    x = _data(4, 256 * 20 + 5, rng, 1)
+    c = _gpu_encode(x, A.params(256, 1, (1, 1), 256))
+    _, r = A.decode(c, torch.float64, x.size, check=False)
+    assert r.status == -1
+    _, r = A.decode(c, torch.float32, x.size + 1, check=False)
+    assert r.status == -1
+    cb = c.cpu().numpy()
+    for trial in range(300):
+        b = cb.copy()
+        i = int(rng.integers(0, len(b)))
+        b[i] ^= np.uint8(1 << int(rng.integers(0, 8)))
+        st_o = O.decode_status(b.tobytes(), np.float32, x.size)
+        yg, r = A.decode(torch.from_numpy(b).cuda(), torch.float32, x.size, check=False)
+        if st_o == 0:
+            assert r.status == 0
+            yo = O.decode(b.tobytes(), np.float32, x.size)
+            np.testing.assert_array_equal(_bits(yg.cpu().numpy()), _bits(yo))
+        else:
+            assert r.status < 0, (trial, i, st_o)
+    # truncation
+    for cut in (0, 10, 39, 40, 48, len(cb) // 2, len(cb) - 4):
+        _, r = A.decode(c[:cut].contiguous(), torch.float32, x.size, check=False)
+        assert r.status < 0
+
+
+def test_nonfinite_input_reports_status():
+    x = np.ones(1000, dtype=np.float32)
+    x[700] = np.nan
+    r = A.encode_status(torch.from_numpy(x).cuda(), A.params(256, 1))
+    assert r.status == -8
+    x[700] = np.inf
+    r = A.encode_status(torch.from_numpy(x).cuda(), A.params(256, 0, (4, 1)))
+    assert r.status == -8
+
+
+def test_bounded_wait_timeout_then_context_usable():
+    rng = np.random.default_rng(7)
+    x = torch.from_numpy(_data(4, 256 * 8 * 6, rng, 1)).cuda()
+    r = A.encode_test_stall(x, A.params(256, 1, (1, 1), 256), stall_tile=2, spin_cycles=1 << 22)
+    assert r.status == -10
+    # the context is still usable and correct afterwards
+    _roundtrip(x.cpu().numpy(), 256, 1, (1, 1), 256)
+
+
+# ----------------------------------------------------------------- profiler
+def _profile_parity(x, N, cands, target):
+    pts_o, rec_o, missed_o = O.profile(x, N=N, candidates=cands, target=target)
+    xt = torch.from_numpy(np.ascontiguousarray(x).reshape(-1)).cuda()
+    pts, summ = A.profile(xt, N, cands, target)
+    assert summ.status == 0
+    for po, pg in zip(pts_o, pts):
+        assert po.code == pg.code
+        assert po.bytes == pg.bytes, (po.code, po.bytes, pg.bytes)
+        for f in ("sx", "sy", "sxx", "sxy", "syy", "sdd", "r"):
+            assert getattr(po, f) == getattr(pg, f), (po.code, f, getattr(po, f), getattr(pg, f))
+    assert summ.recommended == rec_o and bool(summ.flags & 1) == missed_o
+    assert summ.recommended_code == cands[rec_o]
+    return pts, summ
+
+
+@pytest.mark.parametrize("dt", [1, 2, 3, 4, 5])
+def test_profile_parity_small(dt):
+    rng = np.random.default_rng(dt)
+    N = 256
+    x = _data(dt, 256 * 37 + 19, rng, 1)
+    _profile_parity(x, N, list(A.DEFAULT_CANDIDATES), 0.9999)
+    _profile_parity(x, N, [0, 128, 384, 1024, 3968], 0.99999)
+
+
+@pytest.mark.parametrize("dt", [4, 5])
+def test_profile_parity_adversarial_floats(dt):
+    rng = np.random.default_rng(40 + dt)
+    x = _data(dt, 256 * 9 + 3, rng, 2)
+    _profile_parity(x, 256, list(A.DEFAULT_CANDIDATES), 0.9999)
+    _profile_parity(x, 64, [0, 512, 3840], 0.9)
+
+
+def test_profile_parity_image_field():
+    x = synth.grf2d(512, 512, seed=11)
+    pts, summ = _profile_parity(x, 256, list(A.DEFAULT_CANDIDATES), 0.9999)
+    assert 0 < summ.recommended < 15
+
+
+def test_profile_parity_field3d():
+    x = synth.field3d(32, seed=12)
+    _profile_parity(x, 256, list(A.DEFAULT_CANDIDATES), 0.99999)
+
+
+def test_encode_recommended_matches_host_code():
+    x = synth.grf2d(256, 256, seed=13)
+    xt = torch.from_numpy(x.reshape(-1)).cuda()
+    nc = 16
+    ws, pts, summ = A.profile_buffers(xt, 256, nc)
+    A.profile_into(xt, 256, list(A.DEFAULT_CANDIDATES), 0.9999, ws, pts, summ)
+    p = A.params(256, 1)
+    cap = A.encoded_size(4, xt.numel(), p)
+    out = torch.empty(cap, dtype=torch.uint8, device="cuda")
+    ews = torch.empty(A.workspace_size(4, xt.numel(), p), dtype=torch.uint8, device="cuda")
+    res = A.new_result("cuda")
+    A.encode_into(xt, p, out, ews, res, summary=summ)
+    r = A.read_result(res)
+    s = A.read_summary(summ)
+    want = O.encode(x, 256, 1, 1, 1, s.recommended_code)
+    assert r.status == 0 and out[:r.bytes].cpu().numpy().tobytes() == want
