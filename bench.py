@@ -267,7 +267,7 @@ def run_ours(args, rank, world, local_rank):
     return line
 
 
-def cpu_baseline(rows: int = 128):
+def cpu_baseline(rows: int = 1024):
     """The oracle, as it stands, on a bounded slice of the same workload:
     profile (16 codes) + fixed-quality encode at the recommended code +
     decode of the first `rows` rows of the field, single-threaded."""
@@ -291,7 +291,7 @@ def run_reference(args, rank, world):
     steps = []
     cb = None
     for i in range(max(args.warmup, 0) + args.steps):
-        cb = cpu_baseline(rows=32)
+        cb = cpu_baseline(rows=256)
         if i >= args.warmup:
             steps.append(cb)
     v = float(np.mean([s["value"] for s in steps]))

@@ -936,6 +936,13 @@ int oracle_metrics(const void *x, const void *y, int dtype, uint64_t n, uint32_t
 /* r = sum(xy) / sqrt(sum(x^2) sum(y^2)), the Sec. 4 formula in binary64. */
 double oracle_corr(double sxx, double sxy, double syy)
 {
+    /* sums beyond binary64 give a quiet NaN with a fixed bit pattern */
+    if (!isfinite(sxx) || !isfinite(sxy) || !isfinite(syy)) {
+        uint64_t b = 0x7ff8000000000000ull;
+        double r;
+        memcpy(&r, &b, sizeof r);
+        return r;
+    }
     if (sxx == 0.0 && syy == 0.0) return 1.0;
     if (sxx == 0.0 || syy == 0.0) return 0.0;
     double p = sxx * syy;

@@ -243,7 +243,12 @@ def decode(stream_t: torch.Tensor, dtype: torch.dtype, n: int, stream=None,
     y = torch.empty(n, dtype=dtype, device=stream_t.device)
     ws = torch.empty(decode_workspace_size(), dtype=torch.uint8, device=stream_t.device)
     res = new_result(stream_t.device)
-    decode_into(stream_t, y, ws, res, stream)
+    try:
+        decode_into(stream_t, y, ws, res, stream)
+    except ApaxError as e:
+        if check:
+            raise
+        return y, Result(e.status, 0)
     r = read_result(res)
     if check:
         _check(r.status, "decode (device)")

@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(256) k_decode(DecArgs a)
 
     // container header (checked by every warp)
     const uint8_t *in = a.in;
-    bool ok = a.in_bytes >= 40 && in[0] == 'A' && in[1] == 'P' && in[2] == 'X' && in[3] == '1' &&
+    bool ok = in && a.in_bytes >= 40 && in[0] == 'A' && in[1] == 'P' && in[2] == 'X' && in[3] == '1' &&
               in[4] == 1;
     int err = -9;
     uint32_t N = 0, B = 0;

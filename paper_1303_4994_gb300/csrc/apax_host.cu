@@ -159,7 +159,8 @@ int decode_impl(const void *in, uint64_t in_bytes, uint64_t b0, uint64_t b1, boo
     Fmt f;
     int st = fmt_of(dtype, f);
     if (st) return st;
-    if (!in || (!y && n) || !ws) return APAX_ERR_INVALID_ARG;
+    const bool need_y = ranged ? b1 > b0 : n > 0;
+    if ((!in && in_bytes) || (!y && need_y) || !ws) return APAX_ERR_INVALID_ARG;
     if (((uintptr_t)in & 3) || ((uintptr_t)ws & 7) || ((uintptr_t)y % f.size))
         return APAX_ERR_INVALID_ARG;
     if (wsb < apax_decode_workspace_size()) return APAX_ERR_CAPACITY;
@@ -362,6 +363,12 @@ int apax_profile(const void *x, int dtype, uint64_t n, uint32_t block_size,
 
 static double corr_host(double sxx, double sxy, double syy)
 {
+    if (!isfinite(sxx) || !isfinite(sxy) || !isfinite(syy)) {
+        const uint64_t b = 0x7ff8000000000000ull;
+        double r;
+        memcpy(&r, &b, sizeof r);
+        return r;
+    }
     if (sxx == 0.0 && syy == 0.0) return 1.0;
     if (sxx == 0.0 || syy == 0.0) return 0.0;
     double p = sxx * syy;

@@ -399,6 +399,9 @@ __global__ void k_tree(const double *in, double *out, uint64_t cnt, int Qn)
 
 __device__ double corr_r(double sxx, double sxy, double syy)
 {
+    // sums beyond binary64 give a quiet NaN with a fixed bit pattern
+    if (!isfinite(sxx) || !isfinite(sxy) || !isfinite(syy))
+        return __longlong_as_double(0x7ff8000000000000ll);
     if (sxx == 0.0 && syy == 0.0) return 1.0;
     if (sxx == 0.0 || syy == 0.0) return 0.0;
     const double p = __dmul_rn(sxx, syy);
