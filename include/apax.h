@@ -189,6 +189,27 @@ int apax_profile(const void *x, int dtype, uint64_t n, uint32_t block_size,
  * order. */
 void apax_derived_metrics(const apax_profile_point *pt, uint64_t n, double *out /* host */);
 
+/* Encode without any allocation (no counterpart in the paper: this entry
+ * exists for callers that cannot allocate device memory at all -- code
+ * running inside another runtime's allocator or memory-pool hook, paths that
+ * must never block on the driver's allocator, or plug-ins whose host owns
+ * every device buffer).  Same arguments and results as apax_encode, minus
+ * the workspace: the scratch lives in one fixed device array of
+ * APAX_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * the process exits.  Limit: the call must need no more scratch than that
+ * (apax_workspace_size() <= APAX_NOALLOC_SCRATCH_BYTES: 64 bytes plus 8 per
+ * tile of up to 8 blocks for fixed quality, i.e. about 67 million elements at
+ * block size 256; fixed rate always fits); larger calls return
+ * APAX_ERR_CAPACITY without touching the device.  The first call on each
+ * device looks up the array's device address (once, with that device
+ * current), so make it before capturing any stream into a graph.  Each call
+ * clears the scratch words it uses on its stream; all calls share the one
+ * array, so calls that overlap on the GPU (other streams, other threads)
+ * race and must be serialised by the caller. */
+#define APAX_NOALLOC_SCRATCH_BYTES (256u << 10)
+int apax_encode_noalloc(const void *x, int dtype, uint64_t n, const apax_params *p, void *out,
+                        uint64_t out_capacity, apax_result *res, void *stream);
+
 /* Test hook for the bounded device waits (no counterpart in the paper):
  * a fixed-quality apax_encode in which tile `stall_tile` (a tile is a group
  * of consecutive blocks) never publishes its offset, so that its successor's

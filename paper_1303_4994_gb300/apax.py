@@ -63,7 +63,9 @@ _lib = None
 EXPORTS = ("apax_encoded_size", "apax_workspace_size", "apax_encode", "apax_encode_recommended",
            "apax_decode_workspace_size", "apax_decode", "apax_decode_blocks",
            "apax_profile_workspace_size", "apax_profile", "apax_derived_metrics",
-           "apax_encode_test_stall", "apax_status_string", "apax_build_info")
+           "apax_encode_test_stall", "apax_status_string", "apax_build_info",
+           "apax_encode_noalloc")
+NOALLOC_SCRATCH_BYTES = 256 << 10
 
 
 def lib():
@@ -91,6 +93,7 @@ def lib():
         L.apax_derived_metrics.restype = None
         L.apax_encode_test_stall.argtypes = [vp, i32, u64, pP, vp, u64, vp, u64, vp,
                                              ctypes.c_int64, ctypes.c_int64, vp]
+        L.apax_encode_noalloc.argtypes = [vp, i32, u64, pP, vp, u64, vp, vp]
         L.apax_status_string.argtypes = [i32]
         L.apax_status_string.restype = ctypes.c_char_p
         L.apax_build_info.argtypes = []
@@ -194,6 +197,17 @@ def encode(x: torch.Tensor, block_size: int = 256, mode: int = FIXED_QUALITY, ra
     r = read_result(res)
     _check(r.status, "encode (device)")
     return out[:r.bytes]
+
+
+def encode_noalloc_into(x: torch.Tensor, p: Params, out: torch.Tensor, res: torch.Tensor,
+                        stream=None):
+    """Enqueue apax_encode_noalloc: the encode with its scratch in the library's
+    fixed device array instead of a caller workspace (for callers that cannot
+    allocate).  Overlapping calls share that array and must be serialised."""
+    xf = x.reshape(-1)
+    _check(lib().apax_encode_noalloc(xf.data_ptr(), _dtype_code(xf), xf.numel(), ctypes.byref(p),
+                                     out.data_ptr(), out.numel(), res.data_ptr(),
+                                     _stream(stream)), "encode_noalloc")
 
 
 def encode_status(x: torch.Tensor, p: Params, stream=None) -> Result:

@@ -198,6 +198,16 @@ int decode_impl(const void *in, uint64_t in_bytes, uint64_t b0, uint64_t b1, boo
 
 }  // namespace
 
+namespace apax {
+int encode_with_workspace(const void *x, int dtype, uint64_t n, const apax_params *p, void *out,
+                          uint64_t out_capacity, void *workspace, uint64_t workspace_bytes,
+                          apax_result *res, void *stream)
+{
+    return encode_impl(x, dtype, n, p, nullptr, out, out_capacity, workspace, workspace_bytes, res,
+                       -1, 1ll << 31, stream);
+}
+}  // namespace apax
+
 extern "C" {
 
 int apax_encoded_size(int dtype, uint64_t n, const apax_params *p, uint64_t *bytes)

@@ -74,4 +74,9 @@ cudaError_t launch_encode(const EncArgs &a, int wpc, size_t smem, cudaStream_t s
 cudaError_t launch_decode(const DecArgs &a, int wpc, cudaStream_t s);
 cudaError_t launch_profile(const ProfArgs &a, cudaStream_t s);
 
+// apax_encode with an already-sized workspace supplied by another entry point.
+int encode_with_workspace(const void *x, int dtype, uint64_t n, const apax_params *p, void *out,
+                          uint64_t out_capacity, void *workspace, uint64_t workspace_bytes,
+                          apax_result *res, void *stream);
+
 }  // namespace apax
