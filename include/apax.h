@@ -198,8 +198,8 @@ void apax_derived_metrics(const apax_profile_point *pt, uint64_t n, double *out 
  * APAX_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
  * the process exits.  Limit: the call must need no more scratch than that
  * (apax_workspace_size() <= APAX_NOALLOC_SCRATCH_BYTES: 64 bytes plus 8 per
- * tile of up to 8 blocks for fixed quality, i.e. about 67 million elements at
- * block size 256; fixed rate always fits); larger calls return
+ * tile of up to 16 blocks for fixed quality, i.e. about 134 million elements
+ * at block size 256; fixed rate always fits); larger calls return
  * APAX_ERR_CAPACITY without touching the device.  The first call on each
  * device looks up the array's device address (once, with that device
  * current), so make it before capturing any stream into a graph.  Each call

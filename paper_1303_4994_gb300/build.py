@@ -16,7 +16,7 @@ LIB = os.path.join(HERE, "libapax_gb300.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["apax_host.cu", "apax_encode.cu", "apax_decode.cu", "apax_profile.cu",
            "apax_noalloc.cu"]
-HEADERS = ["apax_device.cuh", "apax_block.cuh", "apax_exact.cuh", "apax_kernels.h"]
+HEADERS = ["apax_device.cuh", "apax_team.cuh", "apax_exact.cuh", "apax_kernels.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-fmad=false",
          "--expt-relaxed-constexpr", "-Xptxas", "-warn-spills"]

@@ -1,10 +1,8 @@
 // apax_device.cuh -- device building blocks of the APAX codec kernels (sm_103a).
 //
-// Mapping: one warp owns one codec block.  A block is walked in chunks of
-// 256 samples; lane l holds samples 8l..8l+7 of the chunk, i.e. the two
-// BFPE groups 2l and 2l+1 (Sec. 6: one exponent per group of 4 samples).
-// Everything here is integer arithmetic on IEEE bit patterns, so results are
-// bit-identical to any exact implementation of the same reading.
+// Element-type traits, the attenuator's quantiser and the decoder's exact
+// rounding.  Everything here is integer arithmetic on IEEE bit patterns, so
+// results are bit-identical to any exact implementation of the same reading.
 #pragma once
 
 #include <stdint.h>
@@ -12,7 +10,6 @@
 
 namespace apax {
 
-constexpr int kChunk = 256;  // samples per warp pass
 constexpr unsigned kFull = 0xffffffffu;
 
 // ---------------------------------------------------------------- dtypes
@@ -73,25 +70,6 @@ __device__ __forceinline__ uint64_t warp_max_u64(uint64_t v)
     return v;
 }
 
-// Spread the 32 bits of x to the even bit positions of a 64-bit word.
-__device__ __forceinline__ uint64_t spread_even(uint32_t x)
-{
-    uint64_t v = x;
-    v = (v | (v << 16)) & 0x0000FFFF0000FFFFull;
-    v = (v | (v << 8)) & 0x00FF00FF00FF00FFull;
-    v = (v | (v << 4)) & 0x0F0F0F0F0F0F0F0Full;
-    v = (v | (v << 2)) & 0x3333333333333333ull;
-    v = (v | (v << 1)) & 0x5555555555555555ull;
-    return v;
-}
-
-// 64-bit position mask of a chunk from two per-lane predicates (group 2l, 2l+1).
-__device__ __forceinline__ uint64_t ballot64(bool even_pred, bool odd_pred)
-{
-    uint32_t be = __ballot_sync(kFull, even_pred), bo = __ballot_sync(kFull, odd_pred);
-    return spread_even(be) | (spread_even(bo) << 1);
-}
-
 // ---------------------------------------------------------------- integers
 __device__ __forceinline__ int32_t sext_w(uint32_t v, int W)
 {
@@ -111,17 +89,6 @@ __device__ __forceinline__ uint64_t rne_shift_u64(uint64_t P, int s)
     if (s <= 0) return P << (-s);
     if (s >= 64) return 0;
     return (P + ((uint64_t)1 << (s - 1)) - 1 + ((P >> s) & 1)) >> s;
-}
-
-// bits() of a group (Sec. 6 BFPE exponent): max over the values of the
-// two's-complement width, 0 for an all-zero group, 31 promoted to 32.
-__device__ __forceinline__ int group_exp(int32_t a, int32_t b, int32_t c, int32_t d)
-{
-    uint32_t mag = (uint32_t)(a ^ (a >> 31)) | (uint32_t)(b ^ (b >> 31)) |
-                   (uint32_t)(c ^ (c >> 31)) | (uint32_t)(d ^ (d >> 31));
-    uint32_t any = (uint32_t)(a | b | c | d);
-    int e = any ? 33 - __clz(mag) : 0;
-    return e == 31 ? 32 : e;
 }
 
 // ---------------------------------------------------------------- attenuator
@@ -216,99 +183,6 @@ __device__ __forceinline__ typename DT_<DT>::bits round_to_format(int64_t V, int
     }
     if (neg) out |= (B)1 << (sizeof(B) * 8 - 1);
     return out;
-}
-
-// ---------------------------------------------------------------- streams
-// Redundancy remover (Sec. 5, Sec. 6): S0 the data, S1 first differences,
-// S2 second differences (u_1 = q_1 - q_0), all within the block, mod 2^W.
-struct Prev2 {  // last two quantised values before this lane's first sample
-    int32_t p1, p2;
-};
-
-template <int W>
-__device__ __forceinline__ void derive(const int32_t (&q)[8], int s, int32_t p1, int32_t p2,
-                                       bool block_start, int32_t (&u)[8])
-{
-    if (s == 0) {
-#pragma unroll
-        for (int t = 0; t < 8; ++t) u[t] = sext_w((uint32_t)q[t], W);
-    } else if (s == 1) {
-        uint32_t prev = block_start ? 0u : (uint32_t)p1;
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            u[t] = sext_w((uint32_t)q[t] - prev, W);
-            prev = (uint32_t)q[t];
-        }
-    } else {
-        uint32_t a = block_start ? 0u : (uint32_t)p2, b = block_start ? 0u : (uint32_t)p1;
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            uint32_t v = (uint32_t)q[t] - 2u * b + a;
-            if (t == 1 && block_start) v = (uint32_t)q[1] - (uint32_t)q[0];
-            u[t] = sext_w(v, W);
-            a = b;
-            b = (uint32_t)q[t];
-        }
-    }
-}
-
-// ---------------------------------------------------------------- JEE masks
-// Greedy JEE pairing (Sec. 6): in every maximal run of diffs in [-1,1] the
-// tokens start at even offsets from the run start (a joint token when the
-// next diff is also in the run, else a single token).  For a 64-bit mask S of
-// such positions, return the even-offset positions.  If `odd_start0`, the run
-// that begins at bit 0 continues a run of the previous chunk with its bit 0
-// at an odd offset.  Adding a run's start bit to S carries through the run
-// and clears it, which separates runs by the parity of their start.
-__device__ __forceinline__ uint64_t jee_even_offsets(uint64_t S, bool odd_start0)
-{
-    const uint64_t EV = 0x5555555555555555ull, OD = ~EV;
-    uint64_t R = S & ~(S << 1);
-    uint64_t Re = R & EV;
-    if (odd_start0) Re &= ~1ull;
-    uint64_t X = S + Re;
-    // a continued run's start bit was not added, so it stays in runs_odd
-    uint64_t runs_even = S & ~X, runs_odd = S & X;
-    return (runs_even & EV) | (runs_odd & OD);
-}
-
-// Token statistics of one chunk of exponents.
-struct ChunkTok {
-    int nib;       // nibbles of the tokens that start in this chunk
-    bool carry;    // last valid position: small diff at even offset
-    int last_e;    // exponent of the last valid group
-};
-
-// e0/e1: exponents of groups 2l and 2l+1 of this chunk; G_c: valid groups in
-// the chunk; first: this is chunk 0 (its group 0 is the absolute token);
-// eprev / carry_in: exponent of the last group of the previous chunk and its
-// pairing state.
-__device__ __forceinline__ ChunkTok chunk_tokens(int e0, int e1, int G_c, bool first, int eprev,
-                                                 bool carry_in)
-{
-    const unsigned l = lane_id();
-    int ep = __shfl_up_sync(kFull, e1, 1);
-    if (l == 0) ep = eprev;
-    int g0 = 2 * (int)l, g1 = g0 + 1;
-    bool v0 = g0 < G_c, v1 = g1 < G_c;
-    bool pos0 = !(first && l == 0);  // group 0 of the block has no diff
-    int d0 = e0 - ep, d1 = e1 - e0;
-    bool s0 = v0 && pos0 && d0 >= -1 && d0 <= 1;
-    bool s1 = v1 && d1 >= -1 && d1 <= 1;
-    uint64_t S = ballot64(s0, s1);
-    uint64_t E = jee_even_offsets(S, carry_in && !first);
-    // non-small diffs: one nibble if |d| == 2, else an absolute token (2)
-    bool n0 = v0 && pos0 && !s0, n1 = v1 && !s1;
-    bool a0 = n0 && (d0 > 2 || d0 < -2), a1 = n1 && (d1 > 2 || d1 < -2);
-    uint32_t bn0 = __ballot_sync(kFull, n0), bn1 = __ballot_sync(kFull, n1);
-    uint32_t ba0 = __ballot_sync(kFull, a0), ba1 = __ballot_sync(kFull, a1);
-    ChunkTok r;
-    r.nib = __popcll(E & S) + __popc(bn0) + __popc(bn1) + __popc(ba0) + __popc(ba1) +
-            (first ? 2 : 0);
-    int lastg = G_c - 1;
-    r.carry = (lastg >= 0) && ((E & S) >> lastg & 1);
-    r.last_e = __shfl_sync(kFull, (lastg & 1) ? e1 : e0, lastg >> 1);
-    return r;
 }
 
 }  // namespace apax

@@ -1,18 +1,18 @@
 // apax_encode.cu -- block encoder kernels (Sec. 6 encoder and bit packer).
 //
-// One warp encodes one block; a CTA of WPC warps is one tile of WPC
-// consecutive blocks.  Each warp
+// A team of TS threads encodes one block; a CTA's teams form one tile of
+// consecutive blocks.  Each team
 //   1. decides its stream from the predecessor block at code 0 (the
 //      one-block lag of Sec. 6: block j+1 carries block j's best stream),
 //   2. picks the attenuation code (fixed quality: given; fixed rate: the
 //      BISECT search against the block budget),
-//   3. computes exponents, JEE tokens and mantissas into a shared-memory
-//      packet.
+//   3. writes exponents, JEE tokens and mantissas into a shared-memory
+//      packet image, which is then copied out with coalesced word stores.
 // Fixed-rate packets land at j*B.  Fixed-quality packet offsets come from a
 // device-wide exclusive scan over tiles with decoupled look-back (Merrill &
 // Garland 2016): tiles take tickets in launch order, publish their word
 // count, and walk back over predecessors with a bounded spin.
-#include "apax_block.cuh"
+#include "apax_team.cuh"
 #include "apax_kernels.h"
 
 namespace apax {
@@ -47,7 +47,7 @@ __device__ void write_container_header(const EncArgs &a, int code)
 
 // Bounded wait on a predecessor tile's status word.
 __device__ __forceinline__ uint64_t wait_tile(unsigned long long *tiles, uint64_t t,
-                                              long long limit, int *status, bool &timed_out)
+                                              long long limit, int *status)
 {
     volatile unsigned long long *p = tiles + t;
     uint64_t v = *p;
@@ -58,95 +58,245 @@ __device__ __forceinline__ uint64_t wait_tile(unsigned long long *tiles, uint64_
         v = *p;
         if (v) return v;
         if (clock64() - t0 > limit) {
-            timed_out = true;
             set_status(status, -10);
             return kFlagP;  // treat as a zero prefix so successors finish
         }
     }
 }
 
-template <int DT, int MODE>
-__global__ void __launch_bounds__(256) k_encode(EncArgs a)
+__device__ __forceinline__ uint32_t pad32_bytes(uint32_t bits) { return 4u * ((bits + 31u) >> 5); }
+
+template <int DT>
+__device__ __forceinline__ uint32_t min_packet(int L)
+{
+    const int G = (L + 3) >> 2;
+    return pad32_bytes((uint32_t)DT_<DT>::H + 8u + 4u * (uint32_t)((G - 1 + 1) >> 1));
+}
+
+template <int DT>
+__device__ __forceinline__ uint32_t fr_budget(int L, uint32_t num, uint32_t den)
+{
+    const uint64_t b = ((uint64_t)L * DT_<DT>::S * den / (4ull * num)) * 4ull;
+    const uint32_t mp = min_packet<DT>(L);
+    return b > mp ? (uint32_t)b : mp;
+}
+
+__device__ __forceinline__ uint32_t abs_token(int e)
+{
+    const int v = e >= 31 ? 31 : e;
+    return (uint32_t)(14 + (v >> 4)) | ((uint32_t)(v & 15) << 4);
+}
+
+// Append `cnt` nibbles (value tok) to the thread's token bit stream at
+// nibble position *pos, flushing complete words into pkt.
+struct NibWriter {
+    uint64_t acc;
+    int fill;       // bits in acc
+    uint32_t word;  // packet word index acc starts at
+    uint32_t *pkt;
+    __device__ __forceinline__ void start(uint32_t *p, uint32_t bit)
+    {
+        pkt = p;
+        word = bit >> 5;
+        fill = (int)(bit & 31);
+        acc = 0;
+    }
+    __device__ __forceinline__ void put(uint32_t v, int nbits)
+    {
+        acc |= (uint64_t)v << fill;
+        fill += nbits;
+        if (fill >= 32) {
+            atomicOr(&pkt[word], (uint32_t)acc);
+            acc >>= 32;
+            fill -= 32;
+            ++word;
+        }
+    }
+    __device__ __forceinline__ void flush()
+    {
+        if (fill > 0 && acc) atomicOr(&pkt[word], (uint32_t)acc);
+    }
+};
+
+// ---------------------------------------------------------------- kernel
+template <int DT, int TS, int MODE>
+__global__ void __launch_bounds__(128) k_encode(EncArgs a)
 {
     extern __shared__ uint32_t smem[];
     __shared__ uint64_t s_tile;
-    __shared__ uint32_t s_words[8];
+    __shared__ uint32_t s_words[16];
     __shared__ uint64_t s_base;
-    const int wid = threadIdx.x >> 5;
-    const int lane = threadIdx.x & 31;
-    const int wpc = blockDim.x >> 5;
-    using raw = typename DT_<DT>::raw;
-    constexpr int H = DT_<DT>::H;
+    using T = DT_<DT>;
+    using raw = typename T::raw;
+    using lt = typename LaneT<DT>::t;
+    constexpr int H = T::H;
+    const int team = threadIdx.x / TS, t = tlane<TS>();
+    const int nteams = blockDim.x / TS;
+    const int gp = a.gp;
 
     if (threadIdx.x == 0) s_tile = MODE == 1 ? (uint64_t)atomicAdd(a.ticket, 1u) : blockIdx.x;
     __syncthreads();
     const uint64_t tile = s_tile;
-    const uint64_t j = tile * (uint64_t)wpc + (uint64_t)wid;
-    const bool active = j < a.nb;
+    const uint64_t j = tile * (uint64_t)nteams + (uint64_t)team;
     int code = (int)a.code;
     if (a.code_dev) code = (int)*a.code_dev;
-
-    uint32_t *pkt = smem + (size_t)wid * (a.pkt_words + a.ebuf_words);
+    uint32_t *pkt = smem + (size_t)team * (a.pkt_words + a.ebuf_words);
     uint8_t *ebuf = reinterpret_cast<uint8_t *>(pkt + a.pkt_words);
-
     if (tile == 0 && threadIdx.x == 0) write_container_header(a, code);
 
-    uint32_t words = 0;  // packet words of this warp's block
-    if (active) {
-        const raw *x = reinterpret_cast<const raw *>(a.x);
-        BlockView<DT> prev, cur;
-        // stream decision: best(j-1) (block 0 uses its own best)
-        open_block<DT>(prev, x, a.n, a.N, j == 0 ? 0 : j - 1);
-        open_block<DT>(cur, x, a.n, a.N, j);
-        if (cur.bad && lane == 0) set_status(a.status, -8);
-        const int s = best_stream<DT>(prev);
-        uint32_t plen;
-        if (MODE == 0) {
-            const uint32_t budget = cur.L == (int)a.N ? a.B : fr_budget<DT>(cur.L, a.rate_num, a.rate_den);
-            code = fr_search<DT>(cur, s, budget);
-            plen = budget;
-        }
-        int32_t u[8];
-        int sume, nib;
-        final_pass<DT>(cur, code, s, ebuf, u, sume, nib);
-        const uint32_t bits = (uint32_t)H + 4u * (uint32_t)nib + 4u * (uint32_t)sume;
-        if (MODE == 1) plen = pad32_bytes(bits);
-        words = plen >> 2;
-        for (uint32_t t = lane; t < words; t += 32) pkt[t] = 0;
-        __syncwarp();
-        if (lane == 0) {
-            uint32_t h0 = (uint32_t)s | ((uint32_t)code << 2) | (plen << 14);
-            atomicOr(&pkt[0], h0);
-            if (H == 48) atomicOr(&pkt[1], (uint32_t)(uint16_t)(int16_t)cur.Eb);
-        }
-        write_tokens(ebuf, cur.G, H, pkt);
-        write_mantissas<DT>(cur, code, s, ebuf, (uint32_t)H + 4u * (uint32_t)nib, u, pkt);
-        __syncwarp();
+    const raw *x = reinterpret_cast<const raw *>(a.x);
+    // stream decision: best(j-1) at code 0 (block 0 uses its own)
+    int s;
+    {
+        TBlock<DT> pv;
+        open_team_block<DT, TS>(pv, x, a.n, a.N, a.nb, j == 0 ? 0 : j - 1, gp);
+        uint32_t bb[3];
+        team_eval<DT, TS>(pv, 0, 7u, bb);
+        s = 0;
+        if (bb[1] < bb[s]) s = 1;
+        if (bb[2] < bb[s]) s = 2;
     }
+    TBlock<DT> b;
+    open_team_block<DT, TS>(b, x, a.n, a.N, a.nb, j, gp);
+    if (b.active && b.bad && t == 0) set_status(a.status, -8);
+    uint32_t plen = 0;
+    if (MODE == 0) {
+        const uint32_t budget = b.L == (int)a.N ? a.B : fr_budget<DT>(b.L, a.rate_num, a.rate_den);
+        uint32_t bits[3];
+        team_eval<DT, TS>(b, 0, 1u << s, bits);
+        const bool fits0 = pad32_bytes(bits[s]) <= budget;
+        int lo = 0, hi = 4095;
+        // Teams of one warp share shuffles, so every team runs the same 12
+        // halvings unless all of them already fit at code 0.
+        if (!__all_sync(kFull, fits0)) {
+#pragma unroll 1
+            for (int it = 0; it < 12; ++it) {  // at most 12 halvings close [0, 4095]
+                const int mid = (lo + hi) >> 1;
+                team_eval<DT, TS>(b, mid, 1u << s, bits);
+                if (hi - lo > 1) {
+                    if (pad32_bytes(bits[s]) <= budget) hi = mid;
+                    else lo = mid;
+                }
+            }
+        }
+        code = fits0 ? 0 : hi;
+        plen = budget;
+    }
+
+    // final pass: the chosen stream's exponents into ebuf, token counts
+    const Quant<DT> Q(code, b.Eb);
+    TokCount tc;
+    tc.init();
+    {
+        int32_t qp, s1p;
+        seg_carry<DT>(b, Q, 4 * b.g0, qp, s1p);
+#pragma unroll 1
+        for (int g = b.g0; g < b.g1; ++g) {
+            lt xv[4];
+            load4<DT>(b, 4 * g, xv);
+            int32_t q[4], v0[4], v1[4], v2[4];
+            group_streams<DT>(b, Q, g, xv, qp, s1p, q, v0, v1, v2);
+            const int e = exp_from_or(s == 0 ? or4(v0) : (s == 1 ? or4(v1) : or4(v2)));
+            ebuf[g] = (uint8_t)e;
+            tc.push(e, true);
+        }
+    }
+    int nib_total, sume_total, nib_mine;
+    bool s_in;
+    team_tokens<TS>(tc, b.g0 == 0, nib_total, sume_total, &s_in, &nib_mine);
+    const uint32_t bits = (uint32_t)H + 4u * (uint32_t)nib_total + 4u * (uint32_t)sume_total;
+    if (MODE == 1) plen = pad32_bytes(bits);
+    const uint32_t words = b.active ? plen >> 2 : 0;
+    for (uint32_t w = t; w < words; w += TS) pkt[w] = 0;
+    __syncwarp();
+    // team scans before any divergence: every lane of the warp takes part
+    const int nib_before = team_incl_scan<TS>(nib_mine) - nib_mine;
+    const int sume_before = team_incl_scan<TS>(tc.sume) - tc.sume;
+    if (b.active) {
+        if (t == 0) {
+            atomicOr(&pkt[0], (uint32_t)s | ((uint32_t)code << 2) | (plen << 14));
+            if (H == 48) atomicOr(&pkt[1], (uint32_t)(uint16_t)(int16_t)b.Eb);
+        }
+        // tokens of my groups (Sec. 6 JEE), starting at my nibble offset
+        NibWriter nw;
+        nw.start(pkt, (uint32_t)H + 4u * (uint32_t)nib_before);
+        bool st = s_in;
+        int eprev = b.g0 > 0 && b.g0 < b.G ? ebuf[b.g0 - 1] : 0;
+#pragma unroll 1
+        for (int g = b.g0; g < b.g1; ++g) {
+            const int e = ebuf[g];
+            if (g == 0) {
+                nw.put(abs_token(e), 8);
+                st = false;
+            } else {
+                const int d = e - eprev;
+                if ((unsigned)(d + 1) <= 2u) {
+                    if (st) {
+                        st = false;  // second diff of the previous joint token
+                    } else {
+                        const int dn = g + 1 < b.G ? (int)ebuf[g + 1] - e : 99;
+                        if ((unsigned)(dn + 1) <= 2u) nw.put((uint32_t)(3 * (d + 1) + (dn + 1)), 4);
+                        else nw.put((uint32_t)(11 + d), 4);
+                        st = true;
+                    }
+                } else {
+                    if ((unsigned)(d + 2) <= 4u) nw.put((uint32_t)(11 + d), 4);
+                    else nw.put(abs_token(e), 8);
+                    st = false;
+                }
+            }
+            eprev = e;
+        }
+        nw.flush();
+        // mantissas of my groups after the token section
+        NibWriter mw;
+        mw.start(pkt, (uint32_t)H + 4u * (uint32_t)nib_total + 4u * (uint32_t)sume_before);
+        int32_t qp, s1p;
+        seg_carry<DT>(b, Q, 4 * b.g0, qp, s1p);
+#pragma unroll 1
+        for (int g = b.g0; g < b.g1; ++g) {
+            lt xv[4];
+            load4<DT>(b, 4 * g, xv);
+            int32_t q[4], v0[4], v1[4], v2[4];
+            group_streams<DT>(b, Q, g, xv, qp, s1p, q, v0, v1, v2);
+            const int e = ebuf[g];
+            if (e) {
+                const uint32_t m = e >= 32 ? 0xffffffffu : ((1u << e) - 1u);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const uint32_t u = (uint32_t)(s == 0 ? v0[i] : (s == 1 ? v1[i] : v2[i]));
+                    mw.put(u & m, e);
+                }
+            }
+        }
+        mw.flush();
+    }
+    __syncthreads();
 
     uint64_t off_words;  // packet start in payload words
     if (MODE == 1) {
-        if (lane == 0) s_words[wid] = words;
+        if (t == 0) s_words[team] = words;
         __syncthreads();
-        if (wid == 0) {
-            uint32_t v = lane < wpc ? s_words[lane] : 0;
-            uint32_t incl = warp_incl_scan(v);
-            uint32_t total = __shfl_sync(kFull, incl, 31);
-            if (lane < wpc) s_words[lane] = incl - v;
-            if (lane == 0) {
-                bool to = false;
+        if (threadIdx.x < 32) {
+            const int l = threadIdx.x;
+            const uint32_t v = l < nteams ? s_words[l] : 0;
+            const uint32_t incl = warp_incl_scan(v);
+            const uint32_t total = __shfl_sync(kFull, incl, 31);
+            __syncwarp();
+            if (l < nteams) s_words[l] = incl - v;
+            if (l == 0) {
                 uint64_t excl = 0;
                 const bool hook = a.test_stall_tile == (long long)tile;
                 if (tile == 0) {
                     if (!hook) atomicExch(a.tiles, kFlagP | total);
                 } else {
                     if (!hook) atomicExch(a.tiles + tile, kFlagA | total);
-                    int64_t t = (int64_t)tile - 1;
-                    while (t >= 0) {
-                        uint64_t st = wait_tile(a.tiles, (uint64_t)t, a.spin_limit, a.status, to);
+                    int64_t tt = (int64_t)tile - 1;
+                    while (tt >= 0) {
+                        const uint64_t st = wait_tile(a.tiles, (uint64_t)tt, a.spin_limit, a.status);
                         excl += st & kValMask;
                         if ((st & ~kValMask) == kFlagP) break;
-                        --t;
+                        --tt;
                     }
                     if (!hook) atomicExch(a.tiles + tile, kFlagP | ((excl + total) & kValMask));
                 }
@@ -154,26 +304,26 @@ __global__ void __launch_bounds__(256) k_encode(EncArgs a)
             }
         }
         __syncthreads();
-        off_words = s_base + s_words[wid];
+        off_words = s_base + s_words[team];
     } else {
         off_words = j * (uint64_t)(a.B >> 2);
     }
 
-    if (active) {
+    if (b.active) {
         const uint64_t start = a.poff + 4ull * off_words;
-        if (MODE == 1) {
+        if (MODE == 1 && t == 0) {
             if (off_words > 0xffffffffull) {
-                if (lane == 0) set_status(a.status, -6);
-            } else if (lane == 0) {
+                set_status(a.status, -6);
+            } else {
                 reinterpret_cast<uint32_t *>(a.out + 40)[j] = (uint32_t)off_words;
                 if (j == a.nb - 1 && (a.nb & 1)) reinterpret_cast<uint32_t *>(a.out + 40)[j + 1] = 0;
             }
         }
         if (start + 4ull * words > a.cap) {
-            if (lane == 0) set_status(a.status, -5);
+            if (t == 0) set_status(a.status, -5);
         } else {
             uint32_t *dst = reinterpret_cast<uint32_t *>(a.out + start);
-            for (uint32_t t = lane; t < words; t += 32) dst[t] = pkt[t];
+            for (uint32_t w = t; w < words; w += TS) dst[w] = pkt[w];
         }
     }
 
@@ -181,7 +331,7 @@ __global__ void __launch_bounds__(256) k_encode(EncArgs a)
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        unsigned prev = atomicAdd(a.done, 1u);
+        const unsigned prev = atomicAdd(a.done, 1u);
         if (prev == a.ntiles - 1) {
             __threadfence();
             uint64_t payload;
@@ -201,31 +351,30 @@ __global__ void __launch_bounds__(256) k_encode(EncArgs a)
     }
 }
 
-template <int DT>
-static cudaError_t launch_dt(const EncArgs &a, int wpc, size_t smem, cudaStream_t s)
+template <int DT, int TS>
+static cudaError_t launch_ts(const EncArgs &a, int threads, size_t smem, cudaStream_t s)
 {
-    if (a.mode == 1) {
-        auto k = k_encode<DT, 1>;
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k<<<(unsigned)a.ntiles, 32 * wpc, smem, s>>>(a);
-    } else {
-        auto k = k_encode<DT, 0>;
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k<<<(unsigned)a.ntiles, 32 * wpc, smem, s>>>(a);
-    }
+    auto k = a.mode == 1 ? k_encode<DT, TS, 1> : k_encode<DT, TS, 0>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<(unsigned)a.ntiles, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_encode(const EncArgs &a, int wpc, size_t smem, cudaStream_t s)
+template <int DT>
+static cudaError_t launch_dt(const EncArgs &a, int ts, int threads, size_t smem, cudaStream_t s)
+{
+    return ts == 8 ? launch_ts<DT, 8>(a, threads, smem, s) : launch_ts<DT, 32>(a, threads, smem, s);
+}
+
+cudaError_t launch_encode(const EncArgs &a, int ts, int threads, size_t smem, cudaStream_t s)
 {
     switch (a.dtype) {
-    case 1: return launch_dt<1>(a, wpc, smem, s);
-    case 2: return launch_dt<2>(a, wpc, smem, s);
-    case 3: return launch_dt<3>(a, wpc, smem, s);
-    case 4: return launch_dt<4>(a, wpc, smem, s);
-    default: return launch_dt<5>(a, wpc, smem, s);
+    case 1: return launch_dt<1>(a, ts, threads, smem, s);
+    case 2: return launch_dt<2>(a, ts, threads, smem, s);
+    case 3: return launch_dt<3>(a, ts, threads, smem, s);
+    case 4: return launch_dt<4>(a, ts, threads, smem, s);
+    default: return launch_dt<5>(a, ts, threads, smem, s);
     }
 }
 

@@ -3,7 +3,7 @@
 #include <math.h>
 #include <string.h>
 
-#include "apax_block.cuh"
+#include "apax_team.cuh"
 #include "apax_kernels.h"
 
 using namespace apax;
@@ -63,10 +63,13 @@ int check(int dtype, const apax_params *p, Fmt &f)
     return APAX_OK;
 }
 
-// Encoder launch plan: warps per CTA limited by shared memory.
+// Encoder launch plan.  A team of TS threads owns a block; its shared
+// memory holds the block's packet image and exponent bytes.  Teams of 8
+// (16 per 128-thread CTA) when that fits, else teams of 32 (one per warp).
 struct Plan {
-    int wpc;
+    int ts, threads;
     uint32_t pkt_words, ebuf_words;
+    int gp;
     size_t smem;
     uint64_t ntiles;
 };
@@ -80,11 +83,21 @@ Plan plan_encode(const Fmt &f, uint32_t N, uint64_t nb, uint64_t fr_budget_bytes
     if (fr_budget_bytes / 4 > pl.pkt_words) pl.pkt_words = (uint32_t)(fr_budget_bytes / 4);
     pl.ebuf_words = ((N / 4) + 3) / 4;
     const size_t per = (size_t)(pl.pkt_words + pl.ebuf_words) * 4;
-    int wpc = 8;
-    while (wpc > 1 && (size_t)wpc * per > 200 * 1024) --wpc;
-    pl.wpc = wpc;
-    pl.smem = (size_t)wpc * per;
-    pl.ntiles = nb ? (nb + wpc - 1) / wpc : 1;
+    const size_t cap = 200 * 1024;
+    if (16 * per <= cap) {
+        pl.ts = 8;
+        pl.threads = 128;
+    } else {
+        pl.ts = 32;
+        int warps = 4;
+        while (warps > 1 && (size_t)warps * per > cap) --warps;
+        pl.threads = 32 * warps;
+    }
+    const int nteams = pl.threads / pl.ts;
+    const int G = (int)(N / 4);
+    pl.gp = (G + pl.ts - 1) / pl.ts;
+    pl.smem = (size_t)nteams * per;
+    pl.ntiles = nb ? (nb + nteams - 1) / nteams : 1;
     return pl;
 }
 
@@ -124,6 +137,7 @@ int encode_impl(const void *x, int dtype, uint64_t n, const apax_params *p,
     a.cap = cap;
     a.pkt_words = pl.pkt_words;
     a.ebuf_words = pl.ebuf_words;
+    a.gp = pl.gp;
     a.ntiles = pl.ntiles;
     a.res = res;
     a.spin_limit = spin;
@@ -149,7 +163,7 @@ int encode_impl(const void *x, int dtype, uint64_t n, const apax_params *p,
     cudaStream_t s = (cudaStream_t)stream;
     st = cuda_fail(cudaMemsetAsync(ws, 0, need_ws, s));
     if (st) return st;
-    return cuda_fail(launch_encode(a, pl.wpc, pl.smem, s));
+    return cuda_fail(launch_encode(a, pl.ts, pl.threads, pl.smem, s));
 }
 
 int decode_impl(const void *in, uint64_t in_bytes, uint64_t b0, uint64_t b1, bool ranged,
@@ -176,24 +190,30 @@ int decode_impl(const void *in, uint64_t in_bytes, uint64_t b0, uint64_t b1, boo
     a.b1 = b1;
     a.ranged = ranged;
     uint8_t *w = (uint8_t *)ws;
-    a.done = (unsigned *)(w + 4);
+    a.done = (unsigned *)(w + 16);
     a.status = (int *)(w + 8);
     a.res = res;
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int wpc = 8;
-    // enough warps for every block of the smallest legal block size
+    // Grid-stride over blocks.  The small-block launch (16 teams of 8 per
+    // CTA) sizes its grid for the smallest legal block size; the large-block
+    // launch (4 teams of 32) for blocks of more than 4096 samples.
     const uint64_t blocks = ranged ? (b1 - b0) : (n + 63) / 64;
-    uint64_t ctas = (blocks + wpc - 1) / wpc;
-    const uint64_t cap = (uint64_t)sms * 6;
+    uint64_t ctas = (blocks + 15) / 16;
+    const uint64_t cap = (uint64_t)sms * 8;
     if (ctas > cap) ctas = cap;
     if (ctas == 0) ctas = 1;
     a.nctas = (unsigned)ctas;
+    const uint64_t lblocks = ranged ? (b1 - b0) : (n + 4095) / 4096;
+    uint64_t lctas = (lblocks + 3) / 4;
+    if (lctas > (uint64_t)sms * 4) lctas = (uint64_t)sms * 4;
+    if (lctas == 0) lctas = 1;
+    a.nctas_large = (unsigned)lctas;
     cudaStream_t s = (cudaStream_t)stream;
     st = cuda_fail(cudaMemsetAsync(ws, 0, apax_decode_workspace_size(), s));
     if (st) return st;
-    return cuda_fail(launch_decode(a, wpc, s));
+    return cuda_fail(launch_decode(a, s));
 }
 
 }  // namespace
@@ -355,6 +375,7 @@ int apax_profile(const void *x, int dtype, uint64_t n, uint32_t block_size,
     a.ncand = ncand;
     for (int i = 0; i < ncand; ++i) a.codes[i] = candidates[i];
     a.nruns = (nb + 15) / 16;
+    a.gp = (int)((block_size / 4 + 7) / 8);  // teams of 8 threads
     uint8_t *w = (uint8_t *)workspace;
     a.done = (unsigned *)(w + 4);
     a.status = (int *)(w + 8);

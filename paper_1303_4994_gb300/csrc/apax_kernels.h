@@ -24,7 +24,8 @@ struct EncArgs {
     uint8_t *out;
     uint64_t cap;
     uint64_t poff;      // payload offset in the container
-    uint32_t pkt_words, ebuf_words;  // per-warp shared-memory layout
+    uint32_t pkt_words, ebuf_words;  // per-team shared-memory layout
+    int gp;             // groups per team thread
     uint64_t ntiles;
     // workspace
     unsigned *ticket;
@@ -44,9 +45,9 @@ struct DecArgs {
     uint64_t n;
     uint64_t b0, b1;    // block range to decode
     bool ranged;        // y receives blocks [b0, b1) from y[0]
-    unsigned *done;
+    unsigned *done;     // two completion counters (one per size class)
     int *status;
-    unsigned nctas;
+    unsigned nctas, nctas_large;
     apax_result *res;
 };
 
@@ -59,6 +60,7 @@ struct ProfArgs {
     int ncand;
     uint32_t codes[32];
     uint64_t nruns;     // level-1 nodes (16 blocks each)
+    int gp;             // groups per team thread
     double *run_sums;   // [nruns][2 + 4*ncand]: sx, sxx, then (sy, sxy, syy, sdd) per candidate
     unsigned long long *bytes;  // [ncand] payload bytes (atomic)
     int *status;
@@ -70,8 +72,8 @@ struct ProfArgs {
     apax_profile_summary *summary;
 };
 
-cudaError_t launch_encode(const EncArgs &a, int wpc, size_t smem, cudaStream_t s);
-cudaError_t launch_decode(const DecArgs &a, int wpc, cudaStream_t s);
+cudaError_t launch_encode(const EncArgs &a, int ts, int threads, size_t smem, cudaStream_t s);
+cudaError_t launch_decode(const DecArgs &a, cudaStream_t s);
 cudaError_t launch_profile(const ProfArgs &a, cudaStream_t s);
 
 // apax_encode with an already-sized workspace supplied by another entry point.

@@ -46,7 +46,7 @@ def _spectral_field(shape, slope: float, rng) -> np.ndarray:
     k2 = sum(g * g for g in grids)
     with np.errstate(divide="ignore"):
         amp = np.where(k2 > 0, k2 ** (-slope / 4.0), 0.0)
-    f = np.fft.irfftn(F * amp, s=shape)
+    f = np.fft.irfftn(F * amp, s=shape, axes=list(range(len(shape))))
     f -= f.mean()
     return f / f.std()
 

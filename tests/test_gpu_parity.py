@@ -187,7 +187,8 @@ def test_nonfinite_input_reports_status():
 
 def test_bounded_wait_timeout_then_context_usable():
     rng = np.random.default_rng(7)
-    x = torch.from_numpy(_data(4, 256 * 8 * 6, rng, 1)).cuda()
+    # 64 tiles at any team geometry (a tile holds at most 16 blocks of 256)
+    x = torch.from_numpy(_data(4, 256 * 16 * 64, rng, 1)).cuda()
     r = A.encode_test_stall(x, A.params(256, 1, (1, 1), 256), stall_tile=2, spin_cycles=1 << 22)
     assert r.status == -10
     # the context is still usable and correct afterwards

@@ -72,12 +72,24 @@ def test_noalloc_matches_encode_twice(lib):
 
 
 def test_noalloc_rejects_more_tiles_than_its_array(lib):
-    # a fixed-quality encode of 67.2 million float32 samples needs more tile
-    # words than the fixed array holds: refused on the host
-    n = (A.NOALLOC_SCRATCH_BYTES - 64) // 8 * 8 * 256 + 256
+    # the smallest fixed-quality float32 encode (whole 256-sample blocks)
+    # whose tile table no longer fits the fixed array: refused on the host
     p = A.params(256, A.FIXED_QUALITY, (1, 1), 0)
-    need = A.workspace_size(A.F32, n, p)
-    assert need > A.NOALLOC_SCRATCH_BYTES
+
+    def need(blocks):
+        return A.workspace_size(A.F32, 256 * blocks, p)
+
+    lo, hi = 1, 2
+    while need(hi) <= A.NOALLOC_SCRATCH_BYTES:
+        lo, hi = hi, 2 * hi
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        if need(mid) <= A.NOALLOC_SCRATCH_BYTES:
+            lo = mid
+        else:
+            hi = mid
+    n = 256 * hi
+    assert need(hi) > A.NOALLOC_SCRATCH_BYTES >= need(lo)
     x = torch.zeros(n, dtype=torch.float32, device="cuda")
     cap = A.encoded_size(A.F32, n, p)
     out = torch.empty(cap, dtype=torch.uint8, device="cuda")
