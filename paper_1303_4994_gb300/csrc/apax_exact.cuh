@@ -245,16 +245,18 @@ struct SmemAcc {
         for (int i = ND - 1; i >= 0; --i)
             if (d[i]) { top = i; break; }
         if (top < 0) return 0.0;
-        auto bitat = [&](int b) -> uint64_t {
-            return b >= 0 ? (((uint64_t)d[b >> 5] >> (b & 31)) & 1ull) : 0ull;
-        };
-        const int topbit = 32 * top + (32 - __clz((uint32_t)d[top])) - 1;
-        const int lowbit = topbit - 63;
-        uint64_t win = 0;
-        for (int b = topbit; b >= lowbit; --b) win = (win << 1) | bitat(b);
-        bool st = false;
-        for (int b = lowbit - 1; b >= 0 && !st; --b) st = bitat(b) != 0;
-        // sticky folded into bit 0, below the rounding point of a 64-bit window
+        // the top three digits as one 96-bit value; its leading one becomes
+        // bit 63 of a 64-bit window, and everything below folds into a
+        // sticky bit (bit 0, below the rounding point)
+        const uint32_t w2 = (uint32_t)d[top];
+        const uint32_t w1 = top >= 1 ? (uint32_t)d[top - 1] : 0u;
+        const uint32_t w0 = top >= 2 ? (uint32_t)d[top - 2] : 0u;
+        const u128 V = ((u128)w2 << 64) | ((u128)w1 << 32) | (u128)w0;
+        const int sh = 32 - __clz(w2);  // 1..32
+        const uint64_t win = (uint64_t)(V >> sh);
+        bool st = (V & (((u128)1 << sh) - 1)) != 0;
+        for (int i = 0; i < top - 2 && !st; ++i) st = d[i] != 0;
+        const int lowbit = 32 * (top - 2) + sh;  // position of the window's bit 0
         uint64_t L[4] = {win | (st ? 1ull : 0ull), 0, 0, 0};
         return round_limbs(L, 64, lowbit + LO, neg);
     }

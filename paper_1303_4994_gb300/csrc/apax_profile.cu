@@ -187,6 +187,7 @@ __global__ void __launch_bounds__(128) k_profile(ProfArgs a)
     long long *accmem = reinterpret_cast<long long *>(bv + (size_t)nteams * Qn);
     __shared__ uint32_t s_fb[kRun];   // fallback requests: bit 0 block, bit 1+i candidate i
     __shared__ int s_ok[kRun];
+    __shared__ uint64_t s_txx[kRun][4];  // f32: sum x^2 of the tiny samples (side grid)
 
     const int gp = a.gp;
     const uint64_t j = (uint64_t)blockIdx.x * nteams + team;
@@ -210,6 +211,7 @@ __global__ void __launch_bounds__(128) k_profile(ProfArgs a)
     // ---- block sums of x and x^2
     double blk_x[2] = {0.0, 0.0};
     bool tiny = false;
+    bool side = false;  // f32: block sums and sum d^2 on the 256-bit side grids
     i128 sxx128 = 0;   // f32: sum X^2, X = x 2^(47-Eb)
     W256 wxx;          // f64: window 2^(2Eb - kWin)
     w256_zero(wxx);
@@ -243,8 +245,51 @@ __global__ void __launch_bounds__(128) k_profile(ProfArgs a)
         sxx128 = team_sum_i128(mine);
         sx = team_sum_i64(sx);
         tiny = team_sum<TS>((int)tiny) > 0;
-        blk_x[0] = round_i128((i128)sx, b.Eb - 47);
-        blk_x[1] = round_i128(sxx128, 2 * b.Eb - 94);
+        // Samples below 2^(Eb-24) quantise to 0 at every power-of-two code, so
+        // they enter only sum x, sum x^2 and sum d^2 = sum x^2: exact 256-bit
+        // side sums on finer grids (LSB 2^(Eb-237) and 2^(2Eb-239)).
+        if (__any_sync(kFull, tiny)) {
+            W256 tx, txx;
+            w256_zero(tx);
+            w256_zero(txx);
+            bool deep = false;  // below even the side grids
+            if (tiny) {
+#pragma unroll 1
+                for (int i = 4 * b.g0; i < min(4 * ge, b.L); ++i) {
+                    const uint32_t v = (uint32_t)__ldg(reinterpret_cast<const uint32_t *>(b.p) + i);
+                    const int bexp = (int)((v >> 23) & 0xff);
+                    if (!(v & 0x7fffffffu) || (bexp != 0 && bexp - bmax + 23 >= 0)) continue;
+                    const int ex = (bexp ? bexp : 1) - 150;
+                    const uint32_t Mt = (v & 0x7fffffu) | (bexp ? 0x800000u : 0u);
+                    const int px = ex - (b.Eb - 237), pxx = 2 * ex - (2 * b.Eb - 239);
+                    if (px < 0 || pxx < 0 || b.Eb < -80) {  // subnormal blocks: fallback
+                        deep = true;
+                        continue;
+                    }
+                    w256_add(tx, (u128)Mt, px, (v >> 31) != 0);
+                    w256_add(txx, (u128)((uint64_t)Mt * Mt), pxx, false);
+                }
+            }
+            tx = team_sum_w256(tx);
+            txx = team_sum_w256(txx);
+            deep = team_sum<TS>((int)deep) > 0;
+            if (tiny && !deep) {
+                if (t == 0) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) s_txx[team][i] = txx.l[i];  // tiny part only
+                }
+                w256_add(tx, (u128)(sx < 0 ? -sx : sx), 190, sx < 0);
+                w256_add(txx, (u128)sxx128, 145, false);
+                blk_x[0] = round_w256(tx, b.Eb - 237);
+                blk_x[1] = round_w256(txx, 2 * b.Eb - 239);
+                side = true;
+            }
+            tiny = deep;  // only these still need the exact fallback
+        }
+        if (!side) {
+            blk_x[0] = round_i128((i128)sx, b.Eb - 47);
+            blk_x[1] = round_i128(sxx128, 2 * b.Eb - 94);
+        }
     } else if constexpr (DT == 5) {
         W256 wx;
         w256_zero(wx);
@@ -408,7 +453,16 @@ __global__ void __launch_bounds__(128) k_profile(ProfArgs a)
                     // sum d^2 on the grid 2^(2Eb - 94): Sxx - A 2^(48+2k) - B 2^(25+2k)
                     const i128 dd = sxx128 - st.A * ((i128)1 << (48 + 2 * k)) -
                                     st.B * ((i128)1 << (25 + 2 * k));
-                    v[3] = round_i128(dd, 2 * b.Eb - 94);
+                    if (side) {
+                        // dd (>= 0) is the exact sum d^2 of the other samples
+                        W256 w;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) w.l[i] = s_txx[team][i];
+                        w256_add(w, (u128)dd, 145, false);
+                        v[3] = round_w256(w, 2 * b.Eb - 239);
+                    } else {
+                        v[3] = round_i128(dd, 2 * b.Eb - 94);
+                    }
                 }
             } else if constexpr (DT == 5) {
                 if (st.fast) {

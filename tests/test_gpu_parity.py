@@ -2,7 +2,7 @@
 
 Bit-exact bar: encoded containers are byte-identical, decoded arrays are
 bit-identical, profiler sums and correlations are identical binary64 values.
-Sizes span several tiles (8 blocks each) with ragged tails; edge cases cover
+Sizes span several tiles (16 blocks each) with ragged tails; edge cases cover
 empty/one-sample arrays, block sizes at both limits (multi-chunk blocks),
 adversarial float values (subnormals, huge exponents, zeros), corrupt
 streams, non-finite input and the bounded-wait timeout.
@@ -228,6 +228,26 @@ def test_profile_parity_adversarial_floats(dt):
     x = _data(dt, 256 * 9 + 3, rng, 2)
     _profile_parity(x, 256, list(A.DEFAULT_CANDIDATES), 0.9999)
     _profile_parity(x, 64, [0, 512, 3840], 0.9)
+
+
+@pytest.mark.parametrize("dt", [4, 5])
+def test_profile_parity_tiny_values(dt):
+    # unit-scale blocks with samples far below the block maximum: below the
+    # quantiser's reach at every power-of-two code, at depths both inside and
+    # beyond the profiler's fixed-point grids, and subnormals
+    rng = np.random.default_rng(60 + dt)
+    n = 256 * 40 + 5
+    x = rng.standard_normal(n)
+    depths = [25, 30, 47, 60, 90, 100, 126, 140]
+    for blk in range(0, 40, 3):
+        for i, dpt in enumerate(rng.choice(depths, 4)):
+            x[256 * blk + 7 * i + 1] = (-1.0) ** i * 2.0 ** -int(dpt) * (1 + rng.random())
+    x = x.astype(NP[dt])
+    fi = np.finfo(NP[dt])
+    x[256 * 5 + 3] = fi.smallest_subnormal * 3
+    x[256 * 9 + 100] = -fi.smallest_subnormal
+    _profile_parity(x, 256, list(A.DEFAULT_CANDIDATES), 0.9999)
+    _profile_parity(x, 1000, [0, 128, 1024, 2944], 0.99)
 
 
 def test_profile_parity_image_field():
