@@ -220,6 +220,73 @@ int apax_encode_test_stall(const void *x, int dtype, uint64_t n, const apax_para
                            apax_result *res, int64_t stall_tile, int64_t spin_cycles,
                            void *stream);
 
+/* ---------------------------------------------------------------- batches
+ * Many arrays in one launch (no counterpart in the paper, which codes one
+ * stream at a time): thousands of arrays of uneven length, mixed element
+ * types and per-array parameters are encoded by one persistent kernel whose
+ * CTAs take tiles of consecutive blocks from a global ticket.  The bytes of
+ * every container are exactly those apax_encode writes for the same array.
+ *
+ * Usage: size the workspace, build a plan (host call; validates every job
+ * with apax_encode's rules and copies the plan's tables into the workspace
+ * with a synchronous copy), then run it any number of times.  A run is one
+ * cudaMemsetAsync of the plan's counters plus one kernel launch, so it may
+ * be captured into a CUDA graph.  The jobs' buffers and the workspace must
+ * stay valid while the plan is used; one plan must not run twice at the
+ * same time (its counters live in the workspace). */
+typedef struct {
+    const void *x;              /* device: n samples of dtype */
+    int32_t dtype;              /* apax_dtype */
+    uint32_t reserved0;         /* 0 */
+    uint64_t n;
+    apax_params p;              /* block size, mode, rate or code of this array */
+    const uint32_t *code_dev;   /* device or NULL: fixed-quality code read on the
+                                   device at run time (e.g. &summary->recommended_code) */
+    void *out;                  /* device: the array's container (4-byte aligned) */
+    uint64_t out_capacity;      /* >= apax_encoded_size() of this array */
+    apax_result *res;           /* device: this array's status and container bytes */
+} apax_encode_job;
+
+typedef struct apax_batch apax_batch;   /* opaque host-side plan */
+
+/* Launch geometry of a plan: CTA size (teams of 8 threads: 64 or 128, i.e.
+ * 8 or 16 blocks per tile; teams of 32 for block sizes whose packets need
+ * them: 32..128) and persistent CTAs per SM (0 = the occupancy maximum). */
+typedef struct {
+    uint32_t threads;
+    uint32_t ctas_per_sm;
+} apax_batch_config;
+
+/* Workspace bytes for a batch of `count` jobs (host call). */
+int apax_batch_encode_workspace_size(const apax_encode_job *jobs, int count, uint64_t *bytes);
+
+/* Build a plan (host call, synchronous copy into `workspace`, which must be
+ * 256-byte aligned).  The geometry is the tuner's last choice for a batch of
+ * the same shape in this process, else a default. */
+int apax_batch_encode_create(const apax_encode_job *jobs, int count, void *workspace,
+                             uint64_t workspace_bytes, apax_batch **plan);
+
+/* Enqueue one run on `stream`: every job's container and result. */
+int apax_batch_run(apax_batch *plan, void *stream);
+
+/* Read or set the geometry (setting rewrites the plan's tables after a
+ * device synchronisation; APAX_ERR_INVALID_ARG for a geometry the plan
+ * cannot use). */
+int apax_batch_get_config(const apax_batch *plan, apax_batch_config *cfg);
+int apax_batch_set_config(apax_batch *plan, const apax_batch_config *cfg);
+
+/* Autotuner: runs the plan `reps` times under every allowed geometry (CTA
+ * size = blocks per tile and look-back granularity; CTAs per SM = tiles in
+ * flight per SM), keeps the fastest by CUDA-event time, and remembers it
+ * for later plans of the same shape in this process.  Synchronous; it
+ * performs real runs, so the jobs' outputs are written. */
+int apax_batch_tune(apax_batch *plan, int reps, void *stream);
+
+/* Tiles of the plan's current geometry (work items of one run). */
+uint64_t apax_batch_tiles(const apax_batch *plan);
+
+void apax_batch_destroy(apax_batch *plan);
+
 /* Human-readable text of a status code. */
 const char *apax_status_string(int status);
 

@@ -54,6 +54,17 @@ class Summary(ctypes.Structure):
                 ("n", ctypes.c_uint64)]
 
 
+class EncodeJob(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("dtype", ctypes.c_int32), ("reserved0", ctypes.c_uint32),
+                ("n", ctypes.c_uint64), ("p", Params), ("code_dev", ctypes.c_void_p),
+                ("out", ctypes.c_void_p), ("out_capacity", ctypes.c_uint64),
+                ("res", ctypes.c_void_p)]
+
+
+class BatchConfig(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32)]
+
+
 POINT_BYTES = ctypes.sizeof(Point)
 SUMMARY_BYTES = ctypes.sizeof(Summary)
 RESULT_BYTES = 16
@@ -64,7 +75,9 @@ EXPORTS = ("apax_encoded_size", "apax_workspace_size", "apax_encode", "apax_enco
            "apax_decode_workspace_size", "apax_decode", "apax_decode_blocks",
            "apax_profile_workspace_size", "apax_profile", "apax_derived_metrics",
            "apax_encode_test_stall", "apax_status_string", "apax_build_info",
-           "apax_encode_noalloc")
+           "apax_encode_noalloc", "apax_batch_encode_workspace_size", "apax_batch_encode_create",
+           "apax_batch_run", "apax_batch_get_config", "apax_batch_set_config", "apax_batch_tune",
+           "apax_batch_tiles", "apax_batch_destroy")
 NOALLOC_SCRATCH_BYTES = 256 << 10
 
 
@@ -94,6 +107,17 @@ def lib():
         L.apax_encode_test_stall.argtypes = [vp, i32, u64, pP, vp, u64, vp, u64, vp,
                                              ctypes.c_int64, ctypes.c_int64, vp]
         L.apax_encode_noalloc.argtypes = [vp, i32, u64, pP, vp, u64, vp, vp]
+        pJ, pC = ctypes.POINTER(EncodeJob), ctypes.POINTER(BatchConfig)
+        L.apax_batch_encode_workspace_size.argtypes = [pJ, i32, p64]
+        L.apax_batch_encode_create.argtypes = [pJ, i32, vp, u64, ctypes.POINTER(vp)]
+        L.apax_batch_run.argtypes = [vp, vp]
+        L.apax_batch_get_config.argtypes = [vp, pC]
+        L.apax_batch_set_config.argtypes = [vp, pC]
+        L.apax_batch_tune.argtypes = [vp, i32, vp]
+        L.apax_batch_tiles.argtypes = [vp]
+        L.apax_batch_tiles.restype = u64
+        L.apax_batch_destroy.argtypes = [vp]
+        L.apax_batch_destroy.restype = None
         L.apax_status_string.argtypes = [i32]
         L.apax_status_string.restype = ctypes.c_char_p
         L.apax_build_info.argtypes = []
@@ -231,6 +255,86 @@ def encode_test_stall(x: torch.Tensor, p: Params, stall_tile: int, spin_cycles: 
                                         res.data_ptr(), stall_tile, spin_cycles,
                                         _stream(None)), "encode_test_stall")
     return read_result(res)
+
+
+# ----------------------------------------------------------------- batches
+def encode_jobs(xs, ps, outs, results: torch.Tensor, code_devs=None):
+    """ctypes array of apax_encode_job for device tensors xs with params ps,
+    containers outs (uint8) and results[i] = bytes [16 i, 16 i + 16) of
+    `results`; code_devs[i] (optional) is a device uint32 tensor (or None)."""
+    k = len(xs)
+    arr = (EncodeJob * k)()
+    base = results.data_ptr()
+    for i, (x, p, o) in enumerate(zip(xs, ps, outs)):
+        xf = x.reshape(-1)
+        cd = None if code_devs is None or code_devs[i] is None else code_devs[i].data_ptr()
+        arr[i] = EncodeJob(xf.data_ptr(), _dtype_code(xf), 0, xf.numel(), p, cd, o.data_ptr(),
+                           o.numel(), base + RESULT_BYTES * i)
+    return arr
+
+
+def read_results(results: torch.Tensor, count: int):
+    v = results.view(torch.int64).reshape(-1, 2)[:count].cpu()
+    out = []
+    for st, nb in v.tolist():
+        st &= 0xffffffff
+        out.append(Result(st - (1 << 32) if st >= 1 << 31 else st, nb))
+    return out
+
+
+def batch_encode_workspace_size(jobs) -> int:
+    out = ctypes.c_uint64()
+    _check(lib().apax_batch_encode_workspace_size(jobs, len(jobs), ctypes.byref(out)),
+           "batch_encode_workspace_size")
+    return out.value
+
+
+class EncodeBatch:
+    """A plan encoding many arrays in one persistent launch (apax_batch_*).
+    `jobs` comes from encode_jobs(); the tensors behind it and `workspace`
+    (a uint8 device tensor, see batch_encode_workspace_size) must outlive
+    the plan."""
+
+    def __init__(self, jobs, workspace: torch.Tensor):
+        self.jobs = jobs
+        self.workspace = workspace
+        h = ctypes.c_void_p()
+        _check(lib().apax_batch_encode_create(jobs, len(jobs), workspace.data_ptr(),
+                                              workspace.numel(), ctypes.byref(h)),
+               "batch_encode_create")
+        self.handle = h
+
+    def run(self, stream=None):
+        _check(lib().apax_batch_run(self.handle, _stream(stream)), "batch_run")
+
+    def tune(self, reps: int = 3, stream=None):
+        _check(lib().apax_batch_tune(self.handle, reps, _stream(stream)), "batch_tune")
+
+    @property
+    def config(self):
+        c = BatchConfig()
+        _check(lib().apax_batch_get_config(self.handle, ctypes.byref(c)), "batch_get_config")
+        return (c.threads, c.ctas_per_sm)
+
+    @config.setter
+    def config(self, v):
+        c = BatchConfig(*v)
+        _check(lib().apax_batch_set_config(self.handle, ctypes.byref(c)), "batch_set_config")
+
+    @property
+    def tiles(self) -> int:
+        return lib().apax_batch_tiles(self.handle)
+
+    def close(self):
+        if self.handle:
+            lib().apax_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ----------------------------------------------------------------- decode

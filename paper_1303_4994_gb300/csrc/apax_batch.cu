@@ -1,0 +1,370 @@
+// apax_batch.cu -- batched codec: many arrays of mixed dtype, length and
+// parameters in one persistent launch, with a plan that lives in a
+// caller-owned workspace and an autotuner for its launch geometry.
+//
+// A plan is built once on the host (validation, per-array tile counts, the
+// descriptor table copied into the workspace).  Running it is one memset of
+// the plan's counters and one kernel launch on the caller's stream, so it
+// can be captured into a CUDA graph and replayed.
+#include <stdlib.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "apax_plan.h"
+
+using namespace apax;
+using namespace apax::host;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Launch geometries the tuner may pick for teams of 8 (blocks per tile =
+// threads / 8) and teams of 32 (one block per warp).
+struct Geo {
+    int ts, threads;
+};
+
+}  // namespace
+
+struct apax_batch {
+    int op;  // 0 encode
+    int count;
+    std::vector<EncArgs> jobs;     // per-array arguments, workspace pointers unset
+    std::vector<uint32_t> gp8, gp32;
+    uint32_t pkt_words, ebuf_words;
+    bool need32;                   // some packet only fits teams of 32
+    uint8_t *ws;
+    uint64_t ws_bytes;
+    // layout
+    EncArgs *d_jobs;
+    uint64_t *d_prefix;
+    uint8_t *d_zero;               // start of the region cleared per run
+    uint64_t zero_bytes;
+    uint64_t total_tiles;
+    apax_batch_config cfg;
+    int sms;
+    int dev;
+    std::string key;               // tuner cache key
+};
+
+namespace {
+
+std::mutex g_tune_mu;
+std::map<std::string, apax_batch_config> g_tune_cache;
+
+Geo geo_of(const apax_batch *b, const apax_batch_config &c)
+{
+    Geo g;
+    if (b->need32) {
+        g.ts = 32;
+        g.threads = (int)c.threads;
+    } else {
+        g.ts = 8;
+        g.threads = (int)c.threads;
+    }
+    return g;
+}
+
+size_t smem_of(const apax_batch *b, const Geo &g)
+{
+    return (size_t)(g.threads / g.ts) * (b->pkt_words + b->ebuf_words) * 4;
+}
+
+bool config_ok(const apax_batch *b, const apax_batch_config &c)
+{
+    if (b->need32) {
+        if (c.threads < 32 || c.threads > 128 || (c.threads % 32)) return false;
+    } else {
+        if (c.threads != 64 && c.threads != 128) return false;
+    }
+    Geo g = geo_of(b, c);
+    return smem_of(b, g) <= kEncSmemCap;
+}
+
+// Smallest tile of any allowed geometry (sizes the look-back arrays).
+int min_tile_blocks(const apax_batch *b) { return b->need32 ? 1 : 8; }
+
+// Workspace: [job table][tile prefix][ticket | done+status per job | tiles]
+struct Layout {
+    size_t jobs, prefix, zero, counters, tiles, total;
+};
+
+Layout layout_of(int count, const std::vector<EncArgs> &jobs, int min_tile)
+{
+    Layout L;
+    L.jobs = 0;
+    L.prefix = align_up(L.jobs + (size_t)count * sizeof(EncArgs), kAlign);
+    L.zero = align_up(L.prefix + (size_t)(count + 1) * 8, kAlign);
+    L.counters = L.zero + 64;  // the ticket and padding
+    size_t t = align_up(L.counters + (size_t)count * 16, kAlign);
+    L.tiles = t;
+    uint64_t words = 0;
+    for (const EncArgs &a : jobs)
+        if (a.mode == APAX_FIXED_QUALITY) words += a.nb ? (a.nb + min_tile - 1) / min_tile : 1;
+    L.total = align_up(t + words * 8, kAlign);
+    return L;
+}
+
+// Rebuild the device table for a geometry (synchronous; not on a hot path).
+int apply_config(apax_batch *b, const apax_batch_config &c)
+{
+    if (!config_ok(b, c)) return APAX_ERR_INVALID_ARG;
+    const Geo g = geo_of(b, c);
+    const int nteams = g.threads / g.ts;
+    const Layout L = layout_of(b->count, b->jobs, min_tile_blocks(b));
+    std::vector<EncArgs> tab(b->jobs);
+    std::vector<uint64_t> prefix((size_t)b->count + 1, 0);
+    uint64_t tiles_words = 0;
+    for (int i = 0; i < b->count; ++i) {
+        EncArgs &a = tab[i];
+        a.pkt_words = b->pkt_words;
+        a.ebuf_words = b->ebuf_words;
+        a.gp = (int)(g.ts == 8 ? b->gp8[i] : b->gp32[i]);
+        a.ntiles = a.nb ? (a.nb + nteams - 1) / nteams : 1;
+        a.ticket = nullptr;
+        a.done = (unsigned *)(b->ws + L.counters + 16 * (size_t)i);
+        a.status = (int *)(b->ws + L.counters + 16 * (size_t)i + 4);
+        if (a.mode == APAX_FIXED_QUALITY) {
+            a.tiles = (unsigned long long *)(b->ws + L.tiles + 8 * tiles_words);
+            tiles_words += a.ntiles;
+        } else {
+            a.tiles = nullptr;
+        }
+        prefix[i + 1] = prefix[i] + a.ntiles;
+    }
+    b->total_tiles = prefix[b->count];
+    b->d_jobs = (EncArgs *)(b->ws + L.jobs);
+    b->d_prefix = (uint64_t *)(b->ws + L.prefix);
+    b->d_zero = b->ws + L.zero;
+    b->zero_bytes = L.tiles + 8 * tiles_words - L.zero;
+    if (cudaMemcpy(b->d_jobs, tab.data(), tab.size() * sizeof(EncArgs), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(b->d_prefix, prefix.data(), prefix.size() * 8, cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+        return APAX_ERR_CUDA;
+    b->cfg = c;
+    if (b->cfg.ctas_per_sm == 0) {
+        const int occ = encode_batch_occupancy(g.ts, g.threads, smem_of(b, g));
+        b->cfg.ctas_per_sm = occ > 0 ? (uint32_t)occ : 1;
+    }
+    return APAX_OK;
+}
+
+apax_batch_config default_config(const apax_batch *b)
+{
+    apax_batch_config c;
+    c.threads = b->need32 ? 32 : 128;
+    if (b->need32) {
+        const size_t per = (size_t)(b->pkt_words + b->ebuf_words) * 4;
+        int w = 4;
+        while (w > 1 && (size_t)w * per > kEncSmemCap) --w;
+        c.threads = 32 * w;
+    }
+    c.ctas_per_sm = 0;
+    return c;
+}
+
+int validate_encode_jobs(const apax_encode_job *jobs, int count, std::vector<EncArgs> &out,
+                         std::vector<uint32_t> &gp8, std::vector<uint32_t> &gp32,
+                         uint32_t &pkt_words, uint32_t &ebuf_words, bool &need32)
+{
+    if (count <= 0 || !jobs) return APAX_ERR_INVALID_ARG;
+    out.resize(count);
+    gp8.resize(count);
+    gp32.resize(count);
+    pkt_words = 0;
+    ebuf_words = 0;
+    for (int i = 0; i < count; ++i) {
+        const apax_encode_job &j = jobs[i];
+        uint32_t pw, ew;
+        int st = fill_enc_args(j.x, j.dtype, j.n, &j.p, j.code_dev, j.out, j.out_capacity, j.res,
+                               out[i], pw, ew);
+        if (st) return st;
+        if (!j.res) return APAX_ERR_INVALID_ARG;
+        pkt_words = pw > pkt_words ? pw : pkt_words;
+        ebuf_words = ew > ebuf_words ? ew : ebuf_words;
+        const uint32_t G = j.p.block_size / 4;
+        gp8[i] = (G + 7) / 8;
+        gp32[i] = (G + 31) / 32;
+    }
+    need32 = 16ull * (pkt_words + ebuf_words) * 4 > kEncSmemCap;
+    return APAX_OK;
+}
+
+std::string make_key(const apax_batch *b)
+{
+    // arrays, total samples (log2 bucket), dtype/mode mix, largest packet
+    uint64_t n = 0;
+    unsigned mix = 0;
+    for (const EncArgs &a : b->jobs) {
+        n += a.n;
+        mix |= 1u << (2 * a.dtype + a.mode);
+    }
+    int lg = 0;
+    while ((n >> lg) > 1) ++lg;
+    char buf[128];
+    snprintf(buf, sizeof buf, "enc:%d:%d:%x:%u:%u:%d", b->count, lg, mix, b->pkt_words,
+             b->ebuf_words, b->dev);
+    return buf;
+}
+
+}  // namespace
+
+extern "C" {
+
+int apax_batch_encode_workspace_size(const apax_encode_job *jobs, int count, uint64_t *bytes)
+{
+    if (!bytes) return APAX_ERR_INVALID_ARG;
+    std::vector<EncArgs> v;
+    std::vector<uint32_t> g8, g32;
+    uint32_t pw, ew;
+    bool n32;
+    int st = validate_encode_jobs(jobs, count, v, g8, g32, pw, ew, n32);
+    if (st) return st;
+    *bytes = layout_of(count, v, n32 ? 1 : 8).total;
+    return APAX_OK;
+}
+
+int apax_batch_encode_create(const apax_encode_job *jobs, int count, void *workspace,
+                             uint64_t workspace_bytes, apax_batch **plan)
+{
+    if (!plan) return APAX_ERR_INVALID_ARG;
+    *plan = nullptr;
+    apax_batch *b = new apax_batch();
+    b->op = 0;
+    b->count = count;
+    int st = validate_encode_jobs(jobs, count, b->jobs, b->gp8, b->gp32, b->pkt_words,
+                                  b->ebuf_words, b->need32);
+    if (st) {
+        delete b;
+        return st;
+    }
+    const Layout L = layout_of(count, b->jobs, min_tile_blocks(b));
+    if (!workspace || ((uintptr_t)workspace % kAlign)) {
+        delete b;
+        return APAX_ERR_INVALID_ARG;
+    }
+    if (workspace_bytes < L.total) {
+        delete b;
+        return APAX_ERR_CAPACITY;
+    }
+    b->ws = (uint8_t *)workspace;
+    b->ws_bytes = workspace_bytes;
+    if (cudaGetDevice(&b->dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->dev) != cudaSuccess) {
+        delete b;
+        return APAX_ERR_CUDA;
+    }
+    b->key = make_key(b);
+    apax_batch_config c = default_config(b);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(b->key);
+        if (it != g_tune_cache.end()) c = it->second;
+    }
+    st = apply_config(b, c);
+    if (st) {
+        delete b;
+        return st;
+    }
+    *plan = b;
+    return APAX_OK;
+}
+
+int apax_batch_run(apax_batch *b, void *stream)
+{
+    if (!b) return APAX_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int st = cuda_fail(cudaMemsetAsync(b->d_zero, 0, b->zero_bytes, s));
+    if (st) return st;
+    const Geo g = geo_of(b, b->cfg);
+    EncBatchArgs ba;
+    ba.jobs = b->d_jobs;
+    ba.tile_prefix = b->d_prefix;
+    ba.count = b->count;
+    ba.total_tiles = b->total_tiles;
+    ba.ticket = (unsigned long long *)b->d_zero;
+    const uint64_t want = (uint64_t)b->sms * b->cfg.ctas_per_sm;
+    const unsigned ctas = (unsigned)(want < b->total_tiles ? want : b->total_tiles);
+    return cuda_fail(launch_encode_batch(ba, g.ts, g.threads, smem_of(b, g), ctas, s));
+}
+
+int apax_batch_get_config(const apax_batch *b, apax_batch_config *c)
+{
+    if (!b || !c) return APAX_ERR_INVALID_ARG;
+    *c = b->cfg;
+    return APAX_OK;
+}
+
+int apax_batch_set_config(apax_batch *b, const apax_batch_config *c)
+{
+    if (!b || !c) return APAX_ERR_INVALID_ARG;
+    if (cudaDeviceSynchronize() != cudaSuccess) return APAX_ERR_CUDA;
+    return apply_config(b, *c);
+}
+
+int apax_batch_tune(apax_batch *b, int reps, void *stream)
+{
+    if (!b || reps < 1) return APAX_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<apax_batch_config> cands;
+    const int thr8[2] = {64, 128};
+    for (int t = 0; t < (b->need32 ? 4 : 2); ++t) {
+        apax_batch_config c;
+        c.threads = b->need32 ? 32u * (t + 1) : (uint32_t)thr8[t];
+        if (!config_ok(b, c)) continue;
+        const Geo g = geo_of(b, c);
+        const int occ = encode_batch_occupancy(g.ts, g.threads, smem_of(b, g));
+        for (int k = 1; k <= occ; k = k < 2 ? k + 1 : k * 2) {
+            c.ctas_per_sm = (uint32_t)k;
+            cands.push_back(c);
+        }
+        if (occ > 2 && (occ & (occ - 1))) {
+            c.ctas_per_sm = (uint32_t)occ;
+            cands.push_back(c);
+        }
+    }
+    if (cands.empty()) return APAX_ERR_INVALID_ARG;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return APAX_ERR_CUDA;
+    float best = 0.f;
+    apax_batch_config bestc = b->cfg;
+    int st = APAX_OK;
+    for (const apax_batch_config &c : cands) {
+        if ((st = cuda_fail(cudaStreamSynchronize(s))) != APAX_OK) break;
+        if ((st = apply_config(b, c)) != APAX_OK) break;
+        if ((st = apax_batch_run(b, s)) != APAX_OK) break;  // warm-up
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && st == APAX_OK; ++r) st = apax_batch_run(b, s);
+        cudaEventRecord(e1, s);
+        if (st || (st = cuda_fail(cudaEventSynchronize(e1))) != APAX_OK) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (best == 0.f || ms < best) {
+            best = ms;
+            bestc = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    st = apply_config(b, bestc);
+    if (st) return st;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[b->key] = b->cfg;
+    return APAX_OK;
+}
+
+uint64_t apax_batch_tiles(const apax_batch *b) { return b ? b->total_tiles : 0; }
+
+void apax_batch_destroy(apax_batch *b) { delete b; }
+
+}  // extern "C"

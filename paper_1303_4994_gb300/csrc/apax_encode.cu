@@ -118,13 +118,13 @@ struct NibWriter {
     }
 };
 
-// ---------------------------------------------------------------- kernel
+// ---------------------------------------------------------------- tile body
+// One tile (nteams consecutive blocks) of the array described by `a`.
+// Called by every thread of the CTA; `smem` holds the teams' packet images.
 template <int DT, int TS, int MODE>
-__global__ void __launch_bounds__(128) k_encode(EncArgs a)
+__device__ __forceinline__ void encode_tile(const EncArgs &a, uint64_t tile, uint32_t *smem)
 {
-    extern __shared__ uint32_t smem[];
-    __shared__ uint64_t s_tile;
-    __shared__ uint32_t s_words[16];
+    __shared__ uint32_t s_words[32];
     __shared__ uint64_t s_base;
     using T = DT_<DT>;
     using raw = typename T::raw;
@@ -134,9 +134,6 @@ __global__ void __launch_bounds__(128) k_encode(EncArgs a)
     const int nteams = blockDim.x / TS;
     const int gp = a.gp;
 
-    if (threadIdx.x == 0) s_tile = MODE == 1 ? (uint64_t)atomicAdd(a.ticket, 1u) : blockIdx.x;
-    __syncthreads();
-    const uint64_t tile = s_tile;
     const uint64_t j = tile * (uint64_t)nteams + (uint64_t)team;
     int code = (int)a.code;
     if (a.code_dev) code = (int)*a.code_dev;
@@ -327,7 +324,8 @@ __global__ void __launch_bounds__(128) k_encode(EncArgs a)
         }
     }
 
-    // completion: the last CTA to finish writes the payload size and result
+    // completion: the CTA that finishes the array's last tile writes the
+    // payload size and the result
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -351,6 +349,84 @@ __global__ void __launch_bounds__(128) k_encode(EncArgs a)
     }
 }
 
+// ---------------------------------------------------------------- kernels
+// One array: fixed quality takes tiles by ticket (launch order, which the
+// look-back relies on), fixed rate by CTA index.
+template <int DT, int TS, int MODE>
+__global__ void __launch_bounds__(128) k_encode(EncArgs a)
+{
+    extern __shared__ uint32_t smem[];
+    __shared__ uint64_t s_tile;
+    if (threadIdx.x == 0) s_tile = MODE == 1 ? (uint64_t)atomicAdd(a.ticket, 1u) : blockIdx.x;
+    __syncthreads();
+    encode_tile<DT, TS, MODE>(a, s_tile, smem);
+}
+
+template <int DT, int TS, int MODE>
+__device__ __noinline__ void encode_tile_call(const EncArgs &a, uint64_t tile, uint32_t *smem)
+{
+    encode_tile<DT, TS, MODE>(a, tile, smem);
+}
+
+template <int TS>
+__device__ __forceinline__ void encode_tile_any(const EncArgs &a, uint64_t tile, uint32_t *smem)
+{
+    const int k = 2 * a.dtype + a.mode;
+    switch (k) {
+    case 2: encode_tile_call<1, TS, 0>(a, tile, smem); break;
+    case 3: encode_tile_call<1, TS, 1>(a, tile, smem); break;
+    case 4: encode_tile_call<2, TS, 0>(a, tile, smem); break;
+    case 5: encode_tile_call<2, TS, 1>(a, tile, smem); break;
+    case 6: encode_tile_call<3, TS, 0>(a, tile, smem); break;
+    case 7: encode_tile_call<3, TS, 1>(a, tile, smem); break;
+    case 8: encode_tile_call<4, TS, 0>(a, tile, smem); break;
+    case 9: encode_tile_call<4, TS, 1>(a, tile, smem); break;
+    case 10: encode_tile_call<5, TS, 0>(a, tile, smem); break;
+    default: encode_tile_call<5, TS, 1>(a, tile, smem); break;
+    }
+}
+
+// Many arrays in one persistent launch: CTAs take global tile tickets in
+// order (so each array's tiles start in order, as its look-back needs),
+// find the owning array by binary search over the tile prefix, and run
+// that array's tile body.
+template <int TS>
+__global__ void __launch_bounds__(128) k_encode_batch(EncBatchArgs ba)
+{
+    extern __shared__ uint32_t smem[];
+    __shared__ uint64_t s_tile;
+    __shared__ int s_job;
+    __shared__ __align__(16) EncArgs s_args;
+    while (true) {
+        if (threadIdx.x == 0) {
+            const uint64_t g = atomicAdd(ba.ticket, 1ull);
+            int lo = 0, hi = ba.count;  // jobs[lo] owns g: prefix[lo] <= g < prefix[lo + 1]
+            if (g < ba.total_tiles) {
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (ba.tile_prefix[mid] <= g) lo = mid;
+                    else hi = mid;
+                }
+                s_tile = g - ba.tile_prefix[lo];
+            } else {
+                s_tile = ~0ull;
+            }
+            s_job = lo;
+        }
+        __syncthreads();
+        if (s_tile == ~0ull) break;
+        {
+            // the job's descriptor into shared memory
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(ba.jobs + s_job);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(&s_args);
+            for (int i = threadIdx.x; i < (int)(sizeof(EncArgs) / 4); i += blockDim.x) dst[i] = src[i];
+        }
+        __syncthreads();
+        encode_tile_any<TS>(s_args, s_tile, smem);
+        __syncthreads();
+    }
+}
+
 template <int DT, int TS>
 static cudaError_t launch_ts(const EncArgs &a, int threads, size_t smem, cudaStream_t s)
 {
@@ -365,6 +441,26 @@ template <int DT>
 static cudaError_t launch_dt(const EncArgs &a, int ts, int threads, size_t smem, cudaStream_t s)
 {
     return ts == 8 ? launch_ts<DT, 8>(a, threads, smem, s) : launch_ts<DT, 32>(a, threads, smem, s);
+}
+
+cudaError_t launch_encode_batch(const EncBatchArgs &b, int ts, int threads, size_t smem,
+                               unsigned ctas, cudaStream_t s)
+{
+    auto k = ts == 8 ? k_encode_batch<8> : k_encode_batch<32>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (ctas) k<<<ctas, threads, smem, s>>>(b);
+    return cudaGetLastError();
+}
+
+int encode_batch_occupancy(int ts, int threads, size_t smem)
+{
+    int nb = 0;
+    auto k = ts == 8 ? k_encode_batch<8> : k_encode_batch<32>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, smem) != cudaSuccess) return 0;
+    return nb;
 }
 
 cudaError_t launch_encode(const EncArgs &a, int ts, int threads, size_t smem, cudaStream_t s)

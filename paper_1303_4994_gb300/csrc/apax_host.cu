@@ -5,125 +5,33 @@
 
 #include "apax_team.cuh"
 #include "apax_kernels.h"
+#include "apax_plan.h"
 
 using namespace apax;
 
+using namespace apax::host;
+
 namespace {
 
-struct Fmt {
-    int size, W, F, H;
-};
+}  // namespace
 
-int fmt_of(int dtype, Fmt &f)
-{
-    switch (dtype) {
-    case APAX_I8: f = {1, 8, 0, 32}; return APAX_OK;
-    case APAX_I16: f = {2, 16, 0, 32}; return APAX_OK;
-    case APAX_I32: f = {4, 32, 0, 32}; return APAX_OK;
-    case APAX_F32: f = {4, 32, 1, 48}; return APAX_OK;
-    case APAX_F64: f = {8, 32, 1, 48}; return APAX_OK;
-    default: return APAX_ERR_DTYPE;
-    }
-}
+namespace apax {
+namespace host {
 
-bool block_size_ok(uint32_t N) { return N >= 64 && N <= 16384 && (N % 4) == 0; }
-
-uint64_t pad32(uint64_t bits) { return 4 * ((bits + 31) / 32); }
-
-uint64_t minpacket(const Fmt &f, uint64_t L)
-{
-    uint64_t G = (L + 3) / 4;
-    return pad32((uint64_t)f.H + 8 + 4 * ((G - 1 + 1) / 2));
-}
-
-uint64_t budget(const Fmt &f, uint64_t L, uint32_t num, uint32_t den)
-{
-    uint64_t b = (L * (uint64_t)f.size * den / (4ull * num)) * 4;
-    uint64_t mp = minpacket(f, L);
-    return b > mp ? b : mp;
-}
-
-uint64_t table_bytes(uint64_t nb) { return ((4 * nb) + 7) / 8 * 8; }
-
-int check(int dtype, const apax_params *p, Fmt &f)
-{
-    if (!p) return APAX_ERR_INVALID_ARG;
-    int st = fmt_of(dtype, f);
-    if (st) return st;
-    if (!block_size_ok(p->block_size)) return APAX_ERR_BLOCK_SIZE;
-    if (p->mode == APAX_FIXED_RATE) {
-        if (p->rate_num == 0 || p->rate_den == 0) return APAX_ERR_RATE;
-        uint64_t B = ((uint64_t)p->block_size * f.size * p->rate_den / (4ull * p->rate_num)) * 4;
-        if (B < minpacket(f, p->block_size) || B >= (1u << 18)) return APAX_ERR_RATE;
-    } else if (p->mode == APAX_FIXED_QUALITY) {
-        if (p->atten_code > 4095) return APAX_ERR_INVALID_ARG;
-    } else {
-        return APAX_ERR_INVALID_ARG;
-    }
-    return APAX_OK;
-}
-
-// Encoder launch plan.  A team of TS threads owns a block; its shared
-// memory holds the block's packet image and exponent bytes.  Teams of 8
-// (16 per 128-thread CTA) when that fits, else teams of 32 (one per warp).
-struct Plan {
-    int ts, threads;
-    uint32_t pkt_words, ebuf_words;
-    int gp;
-    size_t smem;
-    uint64_t ntiles;
-};
-
-// The shared packet buffer holds the largest possible packet, or the whole
-// fixed-rate budget when that is larger (packets are padded to it).
-Plan plan_encode(const Fmt &f, uint32_t N, uint64_t nb, uint64_t fr_budget_bytes)
-{
-    Plan pl;
-    pl.pkt_words = max_packet_words(f.H, f.W, N);
-    if (fr_budget_bytes / 4 > pl.pkt_words) pl.pkt_words = (uint32_t)(fr_budget_bytes / 4);
-    pl.ebuf_words = ((N / 4) + 3) / 4;
-    const size_t per = (size_t)(pl.pkt_words + pl.ebuf_words) * 4;
-    const size_t cap = 200 * 1024;
-    if (16 * per <= cap) {
-        pl.ts = 8;
-        pl.threads = 128;
-    } else {
-        pl.ts = 32;
-        int warps = 4;
-        while (warps > 1 && (size_t)warps * per > cap) --warps;
-        pl.threads = 32 * warps;
-    }
-    const int nteams = pl.threads / pl.ts;
-    const int G = (int)(N / 4);
-    pl.gp = (G + pl.ts - 1) / pl.ts;
-    pl.smem = (size_t)nteams * per;
-    pl.ntiles = nb ? (nb + nteams - 1) / nteams : 1;
-    return pl;
-}
-
-constexpr uint64_t kWsHead = 64;  // ticket, done, status (+ padding)
-
-int cuda_fail(cudaError_t e) { return e == cudaSuccess ? APAX_OK : APAX_ERR_CUDA; }
-
-int encode_impl(const void *x, int dtype, uint64_t n, const apax_params *p,
-                const uint32_t *code_dev, void *out, uint64_t cap, void *ws, uint64_t wsb,
-                apax_result *res, int64_t stall, int64_t spin, void *stream)
+int fill_enc_args(const void *x, int dtype, uint64_t n, const apax_params *p,
+                  const uint32_t *code_dev, void *out, uint64_t cap, apax_result *res, EncArgs &a,
+                  uint32_t &pkt_words, uint32_t &ebuf_words)
 {
     Fmt f;
     int st = check(dtype, p, f);
     if (st) return st;
-    if ((!x && n) || !out || !ws) return APAX_ERR_INVALID_ARG;
+    if ((!x && n) || !out) return APAX_ERR_INVALID_ARG;
     // the container is written as 32-bit words; inputs at element alignment
-    if (((uintptr_t)out & 3) || ((uintptr_t)ws & 7) || ((uintptr_t)x % f.size))
-        return APAX_ERR_INVALID_ARG;
-    uint64_t need_ws;
-    apax_workspace_size(dtype, n, p, &need_ws);
-    if (wsb < need_ws) return APAX_ERR_CAPACITY;
+    if (((uintptr_t)out & 3) || ((uintptr_t)x % f.size)) return APAX_ERR_INVALID_ARG;
     const uint32_t N = p->block_size;
     const uint64_t nb = (n + N - 1) / N;
     const uint64_t B = p->mode == APAX_FIXED_RATE ? budget(f, N, p->rate_num, p->rate_den) : 0;
-    const Plan pl = plan_encode(f, N, nb, B);
-    EncArgs a;
+    team_words(f, N, B, pkt_words, ebuf_words);
     memset(&a, 0, sizeof a);
     a.x = x;
     a.n = n;
@@ -135,17 +43,13 @@ int encode_impl(const void *x, int dtype, uint64_t n, const apax_params *p,
     a.code_dev = code_dev;
     a.out = (uint8_t *)out;
     a.cap = cap;
-    a.pkt_words = pl.pkt_words;
-    a.ebuf_words = pl.ebuf_words;
-    a.gp = pl.gp;
-    a.ntiles = pl.ntiles;
     a.res = res;
-    a.spin_limit = spin;
-    a.test_stall_tile = stall;
+    a.spin_limit = 1ll << 31;
+    a.test_stall_tile = -1;
     if (p->mode == APAX_FIXED_RATE) {
         a.rate_num = p->rate_num;
         a.rate_den = p->rate_den;
-        a.B = (uint32_t)budget(f, N, p->rate_num, p->rate_den);
+        a.B = (uint32_t)B;
         uint64_t total;
         apax_encoded_size(dtype, n, p, &total);
         if (cap < total) return APAX_ERR_CAPACITY;
@@ -155,6 +59,35 @@ int encode_impl(const void *x, int dtype, uint64_t n, const apax_params *p,
         a.poff = 40 + table_bytes(nb);
         if (cap < a.poff) return APAX_ERR_CAPACITY;
     }
+    return APAX_OK;
+}
+
+}  // namespace host
+}  // namespace apax
+
+namespace {
+
+int encode_impl(const void *x, int dtype, uint64_t n, const apax_params *p,
+                const uint32_t *code_dev, void *out, uint64_t cap, void *ws, uint64_t wsb,
+                apax_result *res, int64_t stall, int64_t spin, void *stream)
+{
+    EncArgs a;
+    uint32_t pw, ew;
+    int st = fill_enc_args(x, dtype, n, p, code_dev, out, cap, res, a, pw, ew);
+    if (st) return st;
+    if (!ws || ((uintptr_t)ws & 7)) return APAX_ERR_INVALID_ARG;
+    uint64_t need_ws;
+    apax_workspace_size(dtype, n, p, &need_ws);
+    if (wsb < need_ws) return APAX_ERR_CAPACITY;
+    int ts, threads;
+    default_geometry((size_t)(pw + ew) * 4, ts, threads);
+    const Plan pl = plan_geometry(a.N, a.nb, pw, ew, ts, threads);
+    a.pkt_words = pl.pkt_words;
+    a.ebuf_words = pl.ebuf_words;
+    a.gp = pl.gp;
+    a.ntiles = pl.ntiles;
+    a.spin_limit = spin;
+    a.test_stall_tile = stall;
     uint8_t *w = (uint8_t *)ws;
     a.ticket = (unsigned *)(w + 0);
     a.done = (unsigned *)(w + 4);

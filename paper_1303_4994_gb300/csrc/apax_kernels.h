@@ -37,6 +37,16 @@ struct EncArgs {
     apax_result *res;
 };
 
+// Many arrays in one launch: jobs[i] owns global tiles
+// [tile_prefix[i], tile_prefix[i + 1]).
+struct EncBatchArgs {
+    const EncArgs *jobs;
+    const uint64_t *tile_prefix;  // count + 1 entries
+    int count;
+    uint64_t total_tiles;
+    unsigned long long *ticket;
+};
+
 struct DecArgs {
     const uint8_t *in;
     uint64_t in_bytes;
@@ -73,6 +83,9 @@ struct ProfArgs {
 };
 
 cudaError_t launch_encode(const EncArgs &a, int ts, int threads, size_t smem, cudaStream_t s);
+cudaError_t launch_encode_batch(const EncBatchArgs &b, int ts, int threads, size_t smem,
+                               unsigned ctas, cudaStream_t s);
+int encode_batch_occupancy(int ts, int threads, size_t smem);  // CTAs per SM
 cudaError_t launch_decode(const DecArgs &a, cudaStream_t s);
 cudaError_t launch_profile(const ProfArgs &a, cudaStream_t s);
 

@@ -1,0 +1,144 @@
+// apax_plan.h -- host-side validation, container sizes and launch planning
+// shared by the single-array and batched entry points (internal).
+#pragma once
+
+#include <stdint.h>
+#include <stddef.h>
+
+#include "apax_team.cuh"
+#include "apax_kernels.h"
+
+namespace apax {
+namespace host {
+
+struct Fmt {
+    int size, W, F, H;
+};
+
+inline int fmt_of(int dtype, Fmt &f)
+{
+    switch (dtype) {
+    case APAX_I8: f = {1, 8, 0, 32}; return APAX_OK;
+    case APAX_I16: f = {2, 16, 0, 32}; return APAX_OK;
+    case APAX_I32: f = {4, 32, 0, 32}; return APAX_OK;
+    case APAX_F32: f = {4, 32, 1, 48}; return APAX_OK;
+    case APAX_F64: f = {8, 32, 1, 48}; return APAX_OK;
+    default: return APAX_ERR_DTYPE;
+    }
+}
+
+inline bool block_size_ok(uint32_t N) { return N >= 64 && N <= 16384 && (N % 4) == 0; }
+
+inline uint64_t pad32(uint64_t bits) { return 4 * ((bits + 31) / 32); }
+
+inline uint64_t minpacket(const Fmt &f, uint64_t L)
+{
+    uint64_t G = (L + 3) / 4;
+    return pad32((uint64_t)f.H + 8 + 4 * ((G - 1 + 1) / 2));
+}
+
+inline uint64_t budget(const Fmt &f, uint64_t L, uint32_t num, uint32_t den)
+{
+    uint64_t b = (L * (uint64_t)f.size * den / (4ull * num)) * 4;
+    uint64_t mp = minpacket(f, L);
+    return b > mp ? b : mp;
+}
+
+inline uint64_t table_bytes(uint64_t nb) { return ((4 * nb) + 7) / 8 * 8; }
+
+inline int check(int dtype, const apax_params *p, Fmt &f)
+{
+    if (!p) return APAX_ERR_INVALID_ARG;
+    int st = fmt_of(dtype, f);
+    if (st) return st;
+    if (!block_size_ok(p->block_size)) return APAX_ERR_BLOCK_SIZE;
+    if (p->mode == APAX_FIXED_RATE) {
+        if (p->rate_num == 0 || p->rate_den == 0) return APAX_ERR_RATE;
+        uint64_t B = ((uint64_t)p->block_size * f.size * p->rate_den / (4ull * p->rate_num)) * 4;
+        if (B < minpacket(f, p->block_size) || B >= (1u << 18)) return APAX_ERR_RATE;
+    } else if (p->mode == APAX_FIXED_QUALITY) {
+        if (p->atten_code > 4095) return APAX_ERR_INVALID_ARG;
+    } else {
+        return APAX_ERR_INVALID_ARG;
+    }
+    return APAX_OK;
+}
+
+// Encoder launch plan.  A team of TS threads owns a block; its shared
+// memory holds the block's packet image and exponent bytes.  Teams of 8
+// (16 per 128-thread CTA) when that fits, else teams of 32 (one per warp).
+struct Plan {
+    int ts, threads;
+    uint32_t pkt_words, ebuf_words;
+    int gp;
+    size_t smem;
+    uint64_t ntiles;
+};
+
+// Shared-memory words of one team: the largest possible packet, or the
+// whole fixed-rate budget when that is larger (packets are padded to it),
+// then the exponent bytes.
+inline void team_words(const Fmt &f, uint32_t N, uint64_t fr_budget_bytes, uint32_t &pkt_words,
+                       uint32_t &ebuf_words)
+{
+    pkt_words = max_packet_words(f.H, f.W, N);
+    if (fr_budget_bytes / 4 > pkt_words) pkt_words = (uint32_t)(fr_budget_bytes / 4);
+    ebuf_words = ((N / 4) + 3) / 4;
+}
+
+constexpr size_t kEncSmemCap = 200 * 1024;
+
+// Geometry for a given team size and CTA size.
+inline Plan plan_geometry(uint32_t N, uint64_t nb, uint32_t pkt_words, uint32_t ebuf_words, int ts,
+                          int threads)
+{
+    Plan pl;
+    pl.ts = ts;
+    pl.threads = threads;
+    pl.pkt_words = pkt_words;
+    pl.ebuf_words = ebuf_words;
+    const int nteams = threads / ts;
+    const int G = (int)(N / 4);
+    pl.gp = (G + ts - 1) / ts;
+    pl.smem = (size_t)nteams * (pkt_words + ebuf_words) * 4;
+    pl.ntiles = nb ? (nb + nteams - 1) / nteams : 1;
+    return pl;
+}
+
+// Teams of 8 (16 per 128-thread CTA) when their packets fit, else teams of
+// 32 (one per warp, as many warps as fit).
+inline void default_geometry(size_t per_team_bytes, int &ts, int &threads)
+{
+    if (16 * per_team_bytes <= kEncSmemCap) {
+        ts = 8;
+        threads = 128;
+    } else {
+        ts = 32;
+        int warps = 4;
+        while (warps > 1 && (size_t)warps * per_team_bytes > kEncSmemCap) --warps;
+        threads = 32 * warps;
+    }
+}
+
+inline Plan plan_encode(const Fmt &f, uint32_t N, uint64_t nb, uint64_t fr_budget_bytes)
+{
+    uint32_t pw, ew;
+    team_words(f, N, fr_budget_bytes, pw, ew);
+    int ts, threads;
+    default_geometry((size_t)(pw + ew) * 4, ts, threads);
+    return plan_geometry(N, nb, pw, ew, ts, threads);
+}
+
+constexpr uint64_t kWsHead = 64;  // ticket, done, status (+ padding)
+
+// Validate one encode call and fill its per-array arguments (everything
+// but the team geometry and the workspace pointers).
+int fill_enc_args(const void *x, int dtype, uint64_t n, const apax_params *p,
+                  const uint32_t *code_dev, void *out, uint64_t cap, apax_result *res, EncArgs &a,
+                  uint32_t &pkt_words, uint32_t &ebuf_words);
+
+inline int cuda_fail(cudaError_t e) { return e == cudaSuccess ? APAX_OK : APAX_ERR_CUDA; }
+
+
+}  // namespace host
+}  // namespace apax

@@ -97,3 +97,34 @@ def test_profile_argument_checks(lib):
     assert lib.apax_profile_workspace_size(4, 1000, 256, 16, ctypes.byref(out)) == 0
     assert out.value > 0
     assert lib.apax_profile_workspace_size(4, 1000, 256, 33, ctypes.byref(out)) == -1
+
+
+def _job(dt=4, n=1000, p=None, x=0x10000, out=0x20000, cap=1 << 20, res=0x30000):
+    p = p or A.params(256, A.FIXED_QUALITY, (1, 1), 0)
+    return A.EncodeJob(x, dt, 0, n, p, None, out, cap, res)
+
+
+def _batch_ws(jobs):
+    arr = (A.EncodeJob * len(jobs))(*jobs)
+    out = ctypes.c_uint64()
+    st = A.lib().apax_batch_encode_workspace_size(arr, len(jobs), ctypes.byref(out))
+    return st, out.value
+
+
+def test_batch_argument_checks(lib):
+    # host-side validation of every job, with apax_encode's rules
+    st, ws = _batch_ws([_job(), _job(dt=2, n=0), _job(dt=5, n=77777)])
+    assert st == 0 and ws > 0 and ws % 256 == 0
+    assert _batch_ws([_job(p=A.params(66, 1))])[0] == -2
+    assert _batch_ws([_job(), _job(dt=9)])[0] == -3
+    assert _batch_ws([_job(p=A.params(256, A.FIXED_RATE, (1000, 1)))])[0] == -4
+    assert _batch_ws([_job(cap=40)])[0] == -5
+    assert _batch_ws([_job(res=0)])[0] == -1
+    assert _batch_ws([_job(x=0x10002)])[0] == -1   # misaligned float32 input
+    arr = (A.EncodeJob * 1)(_job())
+    out = ctypes.c_uint64()
+    assert A.lib().apax_batch_encode_workspace_size(arr, 0, ctypes.byref(out)) == -1
+    # fixed-rate jobs need no look-back words; fixed-quality ones grow with tiles
+    fr = _batch_ws([_job(n=1 << 20, p=A.params(256, A.FIXED_RATE, (4, 1)), cap=1 << 22)])[1]
+    fq = _batch_ws([_job(n=1 << 20, cap=1 << 23)])[1]
+    assert fq > fr
