@@ -250,8 +250,9 @@ typedef struct {
 typedef struct apax_batch apax_batch;   /* opaque host-side plan */
 
 /* Launch geometry of a plan: CTA size (teams of 8 threads: 64 or 128, i.e.
- * 8 or 16 blocks per tile; teams of 32 for block sizes whose packets need
- * them: 32..128) and persistent CTAs per SM (0 = the occupancy maximum). */
+ * 8 or 16 blocks per tile; teams of 32 -- one block per warp -- when a
+ * block size needs them: 32..128) and persistent CTAs per SM (0 = the
+ * occupancy maximum). */
 typedef struct {
     uint32_t threads;
     uint32_t ctas_per_sm;
@@ -266,7 +267,50 @@ int apax_batch_encode_workspace_size(const apax_encode_job *jobs, int count, uin
 int apax_batch_encode_create(const apax_encode_job *jobs, int count, void *workspace,
                              uint64_t workspace_bytes, apax_batch **plan);
 
-/* Enqueue one run on `stream`: every job's container and result. */
+/* One container to decode in a batch.  `block_size` is the block size the
+ * container was encoded with (the plan sizes its tiles from it; a container
+ * whose header says otherwise is reported as APAX_ERR_CORRUPT). */
+typedef struct {
+    const void *in;             /* device: container (4-byte aligned) */
+    uint64_t in_bytes;
+    void *y;                    /* device: n elements of dtype */
+    int32_t dtype;
+    uint32_t block_size;
+    uint64_t n;
+    apax_result *res;           /* device: this container's status; bytes = n */
+} apax_decode_job;
+
+/* Workspace bytes and plan of a decode batch (host calls; the same rules
+ * as the encode batch; apax_decode's checks per job). */
+int apax_batch_decode_workspace_size(const apax_decode_job *jobs, int count, uint64_t *bytes);
+int apax_batch_decode_create(const apax_decode_job *jobs, int count, void *workspace,
+                             uint64_t workspace_bytes, apax_batch **plan);
+
+/* One array to profile in a batch: apax_profile's arguments. */
+typedef struct {
+    const void *x;                  /* device: n samples of dtype */
+    int32_t dtype;
+    uint32_t block_size;
+    uint64_t n;
+    const uint16_t *candidates;     /* host (read when the plan is built), or NULL
+                                       with ncand = APAX_PROFILE_DEFAULT_CANDIDATES */
+    int32_t ncand;
+    uint32_t reserved0;
+    double target;
+    apax_profile_point *points;     /* device: ncand points */
+    apax_profile_summary *summary;  /* device */
+} apax_profile_job;
+
+/* Workspace bytes and plan of a profile batch: every array's sweep in one
+ * persistent launch (runs of 16 blocks as work items; the CTA finishing an
+ * array's last run adds up its fan-in-16 tree, in the same order as
+ * apax_profile, and writes its points and summary).  CTA size is fixed at
+ * 128; the tuner picks CTAs per SM. */
+int apax_batch_profile_workspace_size(const apax_profile_job *jobs, int count, uint64_t *bytes);
+int apax_batch_profile_create(const apax_profile_job *jobs, int count, void *workspace,
+                              uint64_t workspace_bytes, apax_batch **plan);
+
+/* Enqueue one run on `stream`: every job's output and result. */
 int apax_batch_run(apax_batch *plan, void *stream);
 
 /* Read or set the geometry (setting rewrites the plan's tables after a

@@ -61,6 +61,19 @@ class EncodeJob(ctypes.Structure):
                 ("res", ctypes.c_void_p)]
 
 
+class DecodeJob(ctypes.Structure):
+    _fields_ = [("in_", ctypes.c_void_p), ("in_bytes", ctypes.c_uint64), ("y", ctypes.c_void_p),
+                ("dtype", ctypes.c_int32), ("block_size", ctypes.c_uint32), ("n", ctypes.c_uint64),
+                ("res", ctypes.c_void_p)]
+
+
+class ProfileJob(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("dtype", ctypes.c_int32), ("block_size", ctypes.c_uint32),
+                ("n", ctypes.c_uint64), ("candidates", ctypes.c_void_p), ("ncand", ctypes.c_int32),
+                ("reserved0", ctypes.c_uint32), ("target", ctypes.c_double),
+                ("points", ctypes.c_void_p), ("summary", ctypes.c_void_p)]
+
+
 class BatchConfig(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32)]
 
@@ -77,7 +90,9 @@ EXPORTS = ("apax_encoded_size", "apax_workspace_size", "apax_encode", "apax_enco
            "apax_encode_test_stall", "apax_status_string", "apax_build_info",
            "apax_encode_noalloc", "apax_batch_encode_workspace_size", "apax_batch_encode_create",
            "apax_batch_run", "apax_batch_get_config", "apax_batch_set_config", "apax_batch_tune",
-           "apax_batch_tiles", "apax_batch_destroy")
+           "apax_batch_tiles", "apax_batch_destroy", "apax_batch_decode_workspace_size",
+           "apax_batch_decode_create", "apax_batch_profile_workspace_size",
+           "apax_batch_profile_create")
 NOALLOC_SCRATCH_BYTES = 256 << 10
 
 
@@ -110,6 +125,11 @@ def lib():
         pJ, pC = ctypes.POINTER(EncodeJob), ctypes.POINTER(BatchConfig)
         L.apax_batch_encode_workspace_size.argtypes = [pJ, i32, p64]
         L.apax_batch_encode_create.argtypes = [pJ, i32, vp, u64, ctypes.POINTER(vp)]
+        pD, pPJ = ctypes.POINTER(DecodeJob), ctypes.POINTER(ProfileJob)
+        L.apax_batch_profile_workspace_size.argtypes = [pPJ, i32, p64]
+        L.apax_batch_profile_create.argtypes = [pPJ, i32, vp, u64, ctypes.POINTER(vp)]
+        L.apax_batch_decode_workspace_size.argtypes = [pD, i32, p64]
+        L.apax_batch_decode_create.argtypes = [pD, i32, vp, u64, ctypes.POINTER(vp)]
         L.apax_batch_run.argtypes = [vp, vp]
         L.apax_batch_get_config.argtypes = [vp, pC]
         L.apax_batch_set_config.argtypes = [vp, pC]
@@ -282,6 +302,50 @@ def read_results(results: torch.Tensor, count: int):
     return out
 
 
+def decode_jobs(containers, ys, block_sizes, results: torch.Tensor):
+    """ctypes array of apax_decode_job: containers (uint8 device tensors) into
+    ys (device tensors of the original dtype and length)."""
+    k = len(containers)
+    arr = (DecodeJob * k)()
+    base = results.data_ptr()
+    for i, (c, y, N) in enumerate(zip(containers, ys, block_sizes)):
+        yf = y.reshape(-1)
+        arr[i] = DecodeJob(c.data_ptr(), c.numel(), yf.data_ptr(), _dtype_code(yf), N, yf.numel(),
+                           base + RESULT_BYTES * i)
+    return arr
+
+
+def profile_jobs(xs, block_sizes, candidates, targets, points, summaries):
+    """ctypes array of apax_profile_job; candidates[i] is a list of codes (kept
+    alive on the returned array), points[i] / summaries[i] device uint8
+    tensors (see profile_buffers)."""
+    k = len(xs)
+    arr = (ProfileJob * k)()
+    arr._keep = []
+    for i in range(k):
+        xf = xs[i].reshape(-1)
+        c = (ctypes.c_uint16 * len(candidates[i]))(*candidates[i])
+        arr._keep.append(c)
+        arr[i] = ProfileJob(xf.data_ptr(), _dtype_code(xf), block_sizes[i], xf.numel(),
+                            ctypes.cast(c, ctypes.c_void_p), len(candidates[i]), 0, targets[i],
+                            points[i].data_ptr(), summaries[i].data_ptr())
+    return arr
+
+
+def batch_profile_workspace_size(jobs) -> int:
+    out = ctypes.c_uint64()
+    _check(lib().apax_batch_profile_workspace_size(jobs, len(jobs), ctypes.byref(out)),
+           "batch_profile_workspace_size")
+    return out.value
+
+
+def batch_decode_workspace_size(jobs) -> int:
+    out = ctypes.c_uint64()
+    _check(lib().apax_batch_decode_workspace_size(jobs, len(jobs), ctypes.byref(out)),
+           "batch_decode_workspace_size")
+    return out.value
+
+
 def batch_encode_workspace_size(jobs) -> int:
     out = ctypes.c_uint64()
     _check(lib().apax_batch_encode_workspace_size(jobs, len(jobs), ctypes.byref(out)),
@@ -289,19 +353,28 @@ def batch_encode_workspace_size(jobs) -> int:
     return out.value
 
 
-class EncodeBatch:
-    """A plan encoding many arrays in one persistent launch (apax_batch_*).
-    `jobs` comes from encode_jobs(); the tensors behind it and `workspace`
-    (a uint8 device tensor, see batch_encode_workspace_size) must outlive
-    the plan."""
+class Batch:
+    """A plan running many arrays in one persistent launch (apax_batch_*).
+    `jobs` comes from encode_jobs() or decode_jobs(); the tensors behind it
+    and `workspace` (a 256-byte aligned uint8 device tensor, see
+    batch_*_workspace_size) must outlive the plan."""
 
     def __init__(self, jobs, workspace: torch.Tensor):
         self.jobs = jobs
         self.workspace = workspace
         h = ctypes.c_void_p()
-        _check(lib().apax_batch_encode_create(jobs, len(jobs), workspace.data_ptr(),
-                                              workspace.numel(), ctypes.byref(h)),
-               "batch_encode_create")
+        if isinstance(jobs[0], ProfileJob):
+            _check(lib().apax_batch_profile_create(jobs, len(jobs), workspace.data_ptr(),
+                                                   workspace.numel(), ctypes.byref(h)),
+                   "batch_profile_create")
+        elif isinstance(jobs[0], DecodeJob):
+            _check(lib().apax_batch_decode_create(jobs, len(jobs), workspace.data_ptr(),
+                                                  workspace.numel(), ctypes.byref(h)),
+                   "batch_decode_create")
+        else:
+            _check(lib().apax_batch_encode_create(jobs, len(jobs), workspace.data_ptr(),
+                                                  workspace.numel(), ctypes.byref(h)),
+                   "batch_encode_create")
         self.handle = h
 
     def run(self, stream=None):
@@ -335,6 +408,15 @@ class EncodeBatch:
             self.close()
         except Exception:
             pass
+
+
+EncodeBatch = DecodeBatch = ProfileBatch = Batch
+
+
+def aligned_workspace(nbytes: int, device="cuda") -> torch.Tensor:
+    """A uint8 device tensor of nbytes starting on a 256-byte boundary."""
+    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+    return ws[(-ws.data_ptr()) % 256:][:nbytes]
 
 
 # ----------------------------------------------------------------- decode

@@ -34,9 +34,17 @@ struct Geo {
 }  // namespace
 
 struct apax_batch {
-    int op;  // 0 encode
+    int op;  // 0 encode, 1 decode, 2 profile
     int count;
-    std::vector<EncArgs> jobs;     // per-array arguments, workspace pointers unset
+    std::vector<EncArgs> jobs;     // encode: per-array arguments, workspace pointers unset
+    std::vector<DecArgs> djobs;    // decode: per-container arguments
+    std::vector<uint32_t> dN;      // decode: declared block sizes
+    std::vector<ProfArgs> pjobs;   // profile: per-array arguments
+    ProfArgs *d_pjobs;
+    int max_ncand;
+    DecArgs *d_djobs;
+    uint64_t *d_tiles_of;
+    uint32_t *d_bsize;
     std::vector<uint32_t> gp8, gp32;
     uint32_t pkt_words, ebuf_words;
     bool need32;                   // some packet only fits teams of 32
@@ -112,9 +120,14 @@ Layout layout_of(int count, const std::vector<EncArgs> &jobs, int min_tile)
     return L;
 }
 
+int apply_decode_config(apax_batch *b, const apax_batch_config &c);
+int apply_profile_config(apax_batch *b, const apax_batch_config &c);
+
 // Rebuild the device table for a geometry (synchronous; not on a hot path).
 int apply_config(apax_batch *b, const apax_batch_config &c)
 {
+    if (b->op == 1) return apply_decode_config(b, c);
+    if (b->op == 2) return apply_profile_config(b, c);
     if (!config_ok(b, c)) return APAX_ERR_INVALID_ARG;
     const Geo g = geo_of(b, c);
     const int nteams = g.threads / g.ts;
@@ -160,6 +173,11 @@ int apply_config(apax_batch *b, const apax_batch_config &c)
 apax_batch_config default_config(const apax_batch *b)
 {
     apax_batch_config c;
+    if (b->op == 1) {
+        c.threads = 128;
+        c.ctas_per_sm = 0;
+        return c;
+    }
     c.threads = b->need32 ? 32 : 128;
     if (b->need32) {
         const size_t per = (size_t)(b->pkt_words + b->ebuf_words) * 4;
@@ -198,6 +216,182 @@ int validate_encode_jobs(const apax_encode_job *jobs, int count, std::vector<Enc
     return APAX_OK;
 }
 
+// ---- decode plans
+// Workspace: [job table][tile prefix][tiles per job][block sizes]
+//            [ticket | done+status per job]
+struct DLayout {
+    size_t jobs, prefix, tiles_of, bsize, zero, counters, total;
+};
+
+DLayout dlayout_of(int count)
+{
+    DLayout L;
+    L.jobs = 0;
+    L.prefix = align_up((size_t)count * sizeof(DecArgs), kAlign);
+    L.tiles_of = align_up(L.prefix + (size_t)(count + 1) * 8, kAlign);
+    L.bsize = align_up(L.tiles_of + (size_t)count * 8, kAlign);
+    L.zero = align_up(L.bsize + (size_t)count * 4, kAlign);
+    L.counters = L.zero + 64;
+    L.total = align_up(L.counters + (size_t)count * 16, kAlign);
+    return L;
+}
+
+int validate_decode_jobs(const apax_decode_job *jobs, int count, std::vector<DecArgs> &out,
+                         std::vector<uint32_t> &bs, bool &need32)
+{
+    if (count <= 0 || !jobs) return APAX_ERR_INVALID_ARG;
+    out.resize(count);
+    bs.resize(count);
+    need32 = false;
+    for (int i = 0; i < count; ++i) {
+        const apax_decode_job &j = jobs[i];
+        Fmt f;
+        int st = fmt_of(j.dtype, f);
+        if (st) return st;
+        if (!block_size_ok(j.block_size)) return APAX_ERR_BLOCK_SIZE;
+        if ((!j.in && j.in_bytes) || (!j.y && j.n) || !j.res) return APAX_ERR_INVALID_ARG;
+        if (((uintptr_t)j.in & 3) || ((uintptr_t)j.y % f.size)) return APAX_ERR_INVALID_ARG;
+        DecArgs &a = out[i];
+        memset(&a, 0, sizeof a);
+        a.in = (const uint8_t *)j.in;
+        a.in_bytes = j.in_bytes;
+        a.y = j.y;
+        a.dtype = j.dtype;
+        a.n = j.n;
+        a.ranged = false;
+        a.res = j.res;
+        bs[i] = j.block_size;
+        if (j.block_size / 4 > 1024) need32 = true;
+    }
+    return APAX_OK;
+}
+
+int apply_decode_config(apax_batch *b, const apax_batch_config &c)
+{
+    if (b->need32 ? (c.threads < 32 || c.threads > 128 || (c.threads % 32))
+                  : (c.threads != 64 && c.threads != 128))
+        return APAX_ERR_INVALID_ARG;
+    const int ts = b->need32 ? 32 : 8;
+    const int nteams = (int)c.threads / ts;
+    const DLayout L = dlayout_of(b->count);
+    std::vector<DecArgs> tab(b->djobs);
+    std::vector<uint64_t> prefix((size_t)b->count + 1, 0), tiles((size_t)b->count, 0);
+    for (int i = 0; i < b->count; ++i) {
+        DecArgs &a = tab[i];
+        const uint64_t nb = (a.n + b->dN[i] - 1) / b->dN[i];
+        tiles[i] = nb ? (nb + nteams - 1) / nteams : 1;
+        a.done = (unsigned *)(b->ws + L.counters + 16 * (size_t)i);
+        a.status = (int *)(b->ws + L.counters + 16 * (size_t)i + 4);
+        prefix[i + 1] = prefix[i] + tiles[i];
+    }
+    b->total_tiles = prefix[b->count];
+    b->d_djobs = (DecArgs *)(b->ws + L.jobs);
+    b->d_prefix = (uint64_t *)(b->ws + L.prefix);
+    b->d_tiles_of = (uint64_t *)(b->ws + L.tiles_of);
+    b->d_bsize = (uint32_t *)(b->ws + L.bsize);
+    b->d_zero = b->ws + L.zero;
+    b->zero_bytes = L.total - L.zero;
+    if (cudaMemcpy(b->d_djobs, tab.data(), tab.size() * sizeof(DecArgs), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(b->d_prefix, prefix.data(), prefix.size() * 8, cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(b->d_tiles_of, tiles.data(), tiles.size() * 8, cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(b->d_bsize, b->dN.data(), b->dN.size() * 4, cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+        return APAX_ERR_CUDA;
+    b->cfg = c;
+    if (b->cfg.ctas_per_sm == 0) {
+        const int occ = decode_batch_occupancy(ts, (int)c.threads);
+        b->cfg.ctas_per_sm = occ > 0 ? (uint32_t)occ : 1;
+    }
+    return APAX_OK;
+}
+
+// ---- profile plans (runs of 16 blocks: the tree's level-1 nodes)
+// Workspace: [job table][run prefix][ticket | done+status per job |
+//            candidate bytes per job][run sums and tree scratch per job]
+struct PLayout {
+    size_t jobs, prefix, zero, counters, bytes, sums, total;
+    std::vector<size_t> sums_of;
+};
+
+uint64_t prof_sums_words(const ProfArgs &a)
+{
+    const uint64_t Qn = 2 + 4 * (uint64_t)a.ncand;
+    return Qn * (a.nruns ? a.nruns : 1) + Qn * 2 * (((a.nruns + 15) / 16) + 1);
+}
+
+PLayout playout_of(const std::vector<ProfArgs> &jobs)
+{
+    const size_t count = jobs.size();
+    PLayout L;
+    L.jobs = 0;
+    L.prefix = align_up(count * sizeof(ProfArgs), kAlign);
+    L.zero = align_up(L.prefix + (count + 1) * 8, kAlign);
+    L.counters = L.zero + 64;
+    L.bytes = align_up(L.counters + count * 16, kAlign);
+    L.sums = align_up(L.bytes + count * 8 * 32, kAlign);
+    size_t off = L.sums;
+    L.sums_of.resize(count);
+    for (size_t i = 0; i < count; ++i) {
+        L.sums_of[i] = off;
+        off = align_up(off + 8 * prof_sums_words(jobs[i]), 16);
+    }
+    L.total = align_up(off, kAlign);
+    return L;
+}
+
+int validate_profile_jobs(const apax_profile_job *jobs, int count, std::vector<ProfArgs> &out,
+                          int &max_ncand)
+{
+    if (count <= 0 || !jobs) return APAX_ERR_INVALID_ARG;
+    out.resize(count);
+    max_ncand = 1;
+    for (int i = 0; i < count; ++i) {
+        const apax_profile_job &j = jobs[i];
+        int st = fill_prof_args(j.x, j.dtype, j.n, j.block_size, j.candidates, j.ncand, j.target,
+                                j.points, j.summary, out[i]);
+        if (st) return st;
+        if (j.ncand > max_ncand) max_ncand = j.ncand;
+    }
+    return APAX_OK;
+}
+
+int apply_profile_config(apax_batch *b, const apax_batch_config &c)
+{
+    if (c.threads != 128) return APAX_ERR_INVALID_ARG;
+    const PLayout L = playout_of(b->pjobs);
+    std::vector<ProfArgs> tab(b->pjobs);
+    std::vector<uint64_t> prefix((size_t)b->count + 1, 0);
+    for (int i = 0; i < b->count; ++i) {
+        ProfArgs &a = tab[i];
+        a.done = (unsigned *)(b->ws + L.counters + 16 * (size_t)i);
+        a.status = (int *)(b->ws + L.counters + 16 * (size_t)i + 4);
+        a.bytes = (unsigned long long *)(b->ws + L.bytes + 256 * (size_t)i);
+        a.run_sums = (double *)(b->ws + L.sums_of[i]);
+        const uint64_t Qn = 2 + 4 * (uint64_t)a.ncand;
+        a.scratch = a.run_sums + Qn * (a.nruns ? a.nruns : 1);
+        prefix[i + 1] = prefix[i] + (a.nruns ? a.nruns : 1);
+    }
+    b->total_tiles = prefix[b->count];
+    b->d_pjobs = (ProfArgs *)(b->ws + L.jobs);
+    b->d_prefix = (uint64_t *)(b->ws + L.prefix);
+    b->d_zero = b->ws + L.zero;
+    b->zero_bytes = L.sums - L.zero;
+    if (cudaMemcpy(b->d_pjobs, tab.data(), tab.size() * sizeof(ProfArgs), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(b->d_prefix, prefix.data(), prefix.size() * 8, cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+        return APAX_ERR_CUDA;
+    b->cfg = c;
+    if (b->cfg.ctas_per_sm == 0) {
+        const int occ = profile_batch_occupancy(b->max_ncand);
+        b->cfg.ctas_per_sm = occ > 0 ? (uint32_t)occ : 1;
+    }
+    return APAX_OK;
+}
+
 std::string make_key(const apax_batch *b)
 {
     // arrays, total samples (log2 bucket), dtype/mode mix, largest packet
@@ -207,11 +401,20 @@ std::string make_key(const apax_batch *b)
         n += a.n;
         mix |= 1u << (2 * a.dtype + a.mode);
     }
+    for (const DecArgs &a : b->djobs) {
+        n += a.n;
+        mix |= 1u << (16 + a.dtype);
+    }
+    for (const ProfArgs &a : b->pjobs) {
+        n += a.n;
+        mix |= 1u << (24 + a.dtype);
+    }
     int lg = 0;
     while ((n >> lg) > 1) ++lg;
     char buf[128];
-    snprintf(buf, sizeof buf, "enc:%d:%d:%x:%u:%u:%d", b->count, lg, mix, b->pkt_words,
-             b->ebuf_words, b->dev);
+    static const char *ops[3] = {"enc", "dec", "prof"};
+    snprintf(buf, sizeof buf, "%s:%d:%d:%x:%u:%u:%d:%d", ops[b->op], b->count, lg, mix,
+             b->pkt_words, b->ebuf_words, (int)b->need32, b->dev);
     return buf;
 }
 
@@ -278,12 +481,136 @@ int apax_batch_encode_create(const apax_encode_job *jobs, int count, void *works
     return APAX_OK;
 }
 
+int apax_batch_decode_workspace_size(const apax_decode_job *jobs, int count, uint64_t *bytes)
+{
+    if (!bytes) return APAX_ERR_INVALID_ARG;
+    std::vector<DecArgs> v;
+    std::vector<uint32_t> bs;
+    bool n32;
+    int st = validate_decode_jobs(jobs, count, v, bs, n32);
+    if (st) return st;
+    *bytes = dlayout_of(count).total;
+    return APAX_OK;
+}
+
+int apax_batch_decode_create(const apax_decode_job *jobs, int count, void *workspace,
+                             uint64_t workspace_bytes, apax_batch **plan)
+{
+    if (!plan) return APAX_ERR_INVALID_ARG;
+    *plan = nullptr;
+    apax_batch *b = new apax_batch();
+    b->op = 1;
+    b->count = count;
+    b->pkt_words = b->ebuf_words = 0;
+    int st = validate_decode_jobs(jobs, count, b->djobs, b->dN, b->need32);
+    if (!st && (!workspace || ((uintptr_t)workspace % kAlign))) st = APAX_ERR_INVALID_ARG;
+    if (!st && workspace_bytes < dlayout_of(count).total) st = APAX_ERR_CAPACITY;
+    if (!st && (cudaGetDevice(&b->dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->dev) !=
+                    cudaSuccess))
+        st = APAX_ERR_CUDA;
+    if (st) {
+        delete b;
+        return st;
+    }
+    b->ws = (uint8_t *)workspace;
+    b->ws_bytes = workspace_bytes;
+    b->key = make_key(b);
+    apax_batch_config c = default_config(b);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(b->key);
+        if (it != g_tune_cache.end()) c = it->second;
+    }
+    st = apply_config(b, c);
+    if (st) {
+        delete b;
+        return st;
+    }
+    *plan = b;
+    return APAX_OK;
+}
+
+int apax_batch_profile_workspace_size(const apax_profile_job *jobs, int count, uint64_t *bytes)
+{
+    if (!bytes) return APAX_ERR_INVALID_ARG;
+    std::vector<ProfArgs> v;
+    int mx;
+    int st = validate_profile_jobs(jobs, count, v, mx);
+    if (st) return st;
+    *bytes = playout_of(v).total;
+    return APAX_OK;
+}
+
+int apax_batch_profile_create(const apax_profile_job *jobs, int count, void *workspace,
+                              uint64_t workspace_bytes, apax_batch **plan)
+{
+    if (!plan) return APAX_ERR_INVALID_ARG;
+    *plan = nullptr;
+    apax_batch *b = new apax_batch();
+    b->op = 2;
+    b->count = count;
+    b->pkt_words = b->ebuf_words = 0;
+    b->need32 = false;
+    int st = validate_profile_jobs(jobs, count, b->pjobs, b->max_ncand);
+    if (!st && (!workspace || ((uintptr_t)workspace % kAlign))) st = APAX_ERR_INVALID_ARG;
+    if (!st && workspace_bytes < playout_of(b->pjobs).total) st = APAX_ERR_CAPACITY;
+    if (!st && (cudaGetDevice(&b->dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->dev) !=
+                    cudaSuccess))
+        st = APAX_ERR_CUDA;
+    if (st) {
+        delete b;
+        return st;
+    }
+    b->ws = (uint8_t *)workspace;
+    b->ws_bytes = workspace_bytes;
+    b->key = make_key(b);
+    apax_batch_config c;
+    c.threads = 128;
+    c.ctas_per_sm = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(b->key);
+        if (it != g_tune_cache.end()) c = it->second;
+    }
+    st = apply_config(b, c);
+    if (st) {
+        delete b;
+        return st;
+    }
+    *plan = b;
+    return APAX_OK;
+}
+
 int apax_batch_run(apax_batch *b, void *stream)
 {
     if (!b) return APAX_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     int st = cuda_fail(cudaMemsetAsync(b->d_zero, 0, b->zero_bytes, s));
     if (st) return st;
+    const uint64_t want = (uint64_t)b->sms * b->cfg.ctas_per_sm;
+    const unsigned ctas = (unsigned)(want < b->total_tiles ? want : b->total_tiles);
+    if (b->op == 2) {
+        ProfBatchArgs pa;
+        pa.jobs = b->d_pjobs;
+        pa.run_prefix = b->d_prefix;
+        pa.count = b->count;
+        pa.total_runs = b->total_tiles;
+        pa.ticket = (unsigned long long *)b->d_zero;
+        return cuda_fail(launch_profile_batch(pa, b->max_ncand, ctas, s));
+    }
+    if (b->op == 1) {
+        DecBatchArgs da;
+        da.jobs = b->d_djobs;
+        da.tile_prefix = b->d_prefix;
+        da.tiles_of = b->d_tiles_of;
+        da.block_size = b->d_bsize;
+        da.count = b->count;
+        da.total_tiles = b->total_tiles;
+        da.ticket = (unsigned long long *)b->d_zero;
+        return cuda_fail(launch_decode_batch(da, b->need32 ? 32 : 8, (int)b->cfg.threads, ctas, s));
+    }
     const Geo g = geo_of(b, b->cfg);
     EncBatchArgs ba;
     ba.jobs = b->d_jobs;
@@ -291,8 +618,6 @@ int apax_batch_run(apax_batch *b, void *stream)
     ba.count = b->count;
     ba.total_tiles = b->total_tiles;
     ba.ticket = (unsigned long long *)b->d_zero;
-    const uint64_t want = (uint64_t)b->sms * b->cfg.ctas_per_sm;
-    const unsigned ctas = (unsigned)(want < b->total_tiles ? want : b->total_tiles);
     return cuda_fail(launch_encode_batch(ba, g.ts, g.threads, smem_of(b, g), ctas, s));
 }
 
@@ -316,12 +641,19 @@ int apax_batch_tune(apax_batch *b, int reps, void *stream)
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<apax_batch_config> cands;
     const int thr8[2] = {64, 128};
-    for (int t = 0; t < (b->need32 ? 4 : 2); ++t) {
+    for (int t = 0; t < (b->op == 2 ? 1 : (b->need32 ? 4 : 2)); ++t) {
         apax_batch_config c;
-        c.threads = b->need32 ? 32u * (t + 1) : (uint32_t)thr8[t];
-        if (!config_ok(b, c)) continue;
-        const Geo g = geo_of(b, c);
-        const int occ = encode_batch_occupancy(g.ts, g.threads, smem_of(b, g));
+        c.threads = b->op == 2 ? 128u : (b->need32 ? 32u * (t + 1) : (uint32_t)thr8[t]);
+        int occ;
+        if (b->op == 2) {
+            occ = profile_batch_occupancy(b->max_ncand);
+        } else if (b->op == 1) {
+            occ = decode_batch_occupancy(b->need32 ? 32 : 8, (int)c.threads);
+        } else {
+            if (!config_ok(b, c)) continue;
+            const Geo g = geo_of(b, c);
+            occ = encode_batch_occupancy(g.ts, g.threads, smem_of(b, g));
+        }
         for (int k = 1; k <= occ; k = k < 2 ? k + 1 : k * 2) {
             c.ctas_per_sm = (uint32_t)k;
             cands.push_back(c);

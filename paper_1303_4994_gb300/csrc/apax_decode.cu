@@ -305,13 +305,60 @@ struct Dequant {
     }
 };
 
-// Teams of TS threads with EB bytes of exponent buffer each: (8, 1024) for
-// block sizes up to 4096, (32, 4096) above.  Each launch decodes only the
-// containers of its size class, so both can be enqueued without knowing N.
-template <int DT, int TS, int EB>
-__global__ void __launch_bounds__(128) k_decode(DecArgs a)
+// Container header fields (40 bytes, little endian; see the encoder).
+struct DecHdr {
+    uint32_t N, B;
+    uint64_t n, payload, poff, nb;
+    int mode;
+    int err;  // 0, or the status a malformed or mismatched header gives
+};
+
+__device__ __forceinline__ DecHdr read_header(const DecArgs &a)
 {
-    extern __shared__ uint8_t dsm[];
+    DecHdr h;
+    h.N = h.B = 0;
+    h.n = h.payload = h.poff = h.nb = 0;
+    h.mode = 0;
+    h.err = -9;
+    const uint8_t *in = a.in;
+    if (!(in && a.in_bytes >= 40 && in[0] == 'A' && in[1] == 'P' && in[2] == 'X' && in[3] == '1' &&
+          in[4] == 1))
+        return h;
+    auto le = [&](int o, int k) {
+        uint64_t v = 0;
+        for (int i = 0; i < k; ++i) v |= (uint64_t)in[o + i] << (8 * i);
+        return v;
+    };
+    h.mode = in[6];
+    h.N = (uint32_t)le(8, 4);
+    h.B = (uint32_t)le(16, 4);
+    h.n = le(20, 8);
+    h.payload = le(28, 8);
+    if (in[5] != a.dtype || h.n != a.n) {
+        h.err = -1;
+        return h;
+    }
+    if (h.N < 64 || h.N > 16384 || (h.N & 3) || (h.mode != 0 && h.mode != 1)) return h;
+    h.nb = (h.n + h.N - 1) / h.N;
+    h.poff = 40 + (h.mode == 1 ? ((4 * h.nb + 7) / 8) * 8 : 0);
+    if (h.poff > a.in_bytes || h.payload > a.in_bytes - h.poff) return h;
+    if (h.mode == 0 && ((h.B & 3) || h.B == 0)) return h;
+    if (a.ranged && (a.b1 > h.nb || a.b0 > a.b1)) {
+        h.err = -1;
+        return h;
+    }
+    h.err = 0;
+    return h;
+}
+
+// One tile: the CTA's teams decode blocks jb + tile * nteams + team of the
+// array (jb = the first block of the requested range).  Teams of TS threads
+// with EB bytes of exponent buffer each: (8, 1024) for block sizes up to
+// 4096, (32, 4096) above.
+template <int DT, int TS, int EB>
+__device__ __forceinline__ void decode_tile(const DecArgs &a, const DecHdr &hd, uint64_t tile,
+                                            uint8_t *dsm)
+{
     using T = DT_<DT>;
     using raw = typename T::raw;
     using lt = typename LaneT<DT>::t;
@@ -319,176 +366,164 @@ __global__ void __launch_bounds__(128) k_decode(DecArgs a)
     const int team = threadIdx.x / TS, t = tlane<TS>();
     const int nteams = blockDim.x / TS;
     uint8_t *ebuf = dsm + (size_t)team * EB;
-    constexpr bool LARGE = EB > 1024;
-
-    // container header (checked by every thread)
     const uint8_t *in = a.in;
-    bool ok = in && a.in_bytes >= 40 && in[0] == 'A' && in[1] == 'P' && in[2] == 'X' &&
-              in[3] == '1' && in[4] == 1;
-    int err = -9;
-    uint32_t N = 0, B = 0;
-    uint64_t n = 0, payload = 0, poff = 0, nb = 0;
-    int mode = 0;
-    if (ok) {
-        auto le = [&](int o, int k) {
-            uint64_t v = 0;
-            for (int i = 0; i < k; ++i) v |= (uint64_t)in[o + i] << (8 * i);
-            return v;
-        };
-        mode = in[6];
-        N = (uint32_t)le(8, 4);
-        B = (uint32_t)le(16, 4);
-        n = le(20, 8);
-        payload = le(28, 8);
-        if (in[5] != a.dtype || n != a.n) {
-            ok = false;
-            err = -1;
-        } else if (N < 64 || N > 16384 || (N & 3) || (mode != 0 && mode != 1)) {
-            ok = false;
-        } else {
-            nb = (n + N - 1) / N;
-            poff = 40 + (mode == 1 ? ((4 * nb + 7) / 8) * 8 : 0);
-            if (poff > a.in_bytes || payload > a.in_bytes - poff) ok = false;
-            if (mode == 0 && ((B & 3) || B == 0)) ok = false;
-            if (a.ranged && (a.b1 > nb || a.b0 > a.b1)) {
-                ok = false;
-                err = -1;
+    const uint32_t N = hd.N, B = hd.B;
+    const uint64_t n = hd.n, payload = hd.payload, poff = hd.poff, nb = hd.nb;
+    const int mode = hd.mode;
+    const int GN = (int)(N / 4), gp = (GN + TS - 1) / TS;
+    const uint64_t jb = a.ranged ? a.b0 : 0, je = a.ranged ? a.b1 : nb;
+    const uint32_t *tab = reinterpret_cast<const uint32_t *>(in + 40);
+    {
+        const uint64_t j = jb + tile * (uint64_t)nteams + (uint64_t)team;
+        const bool active = j < je;
+        int L = 0, G = 0;
+        bool bad = false;
+        PktReader pr;
+        pr.w = reinterpret_cast<const uint32_t *>(in + poff);
+        pr.nwords = 0;
+        if (active) {
+            const uint64_t start = mode == 1 ? 4ull * (uint64_t)__ldg(tab + j) : j * (uint64_t)B;
+            const uint64_t off = j * (uint64_t)N;
+            L = (int)((n - off) < N ? (n - off) : N);
+            G = (L + 3) >> 2;
+            bad = start >= payload || (start & 3);
+            if (!bad) {
+                pr.w = reinterpret_cast<const uint32_t *>(in + poff + start);
+                const uint64_t aw = (payload - start) >> 2;
+                pr.nwords = (uint32_t)(aw > 0xffffffffull ? 0xffffffffull : aw);
             }
         }
-    }
-    // the size class this launch serves (header errors: the small launch)
-    const bool mine = ok ? ((N / 4 > 1024) == LARGE) : !LARGE;
-    if (!mine) {
-        // nothing to do in this launch
-    } else if (!ok) {
-        if (threadIdx.x == 0) set_status(a.status, err);
-    } else {
-        const int GN = (int)(N / 4), gp = (GN + TS - 1) / TS;
-        const uint64_t jb = a.ranged ? a.b0 : 0, je = a.ranged ? a.b1 : nb;
-        const uint32_t *tab = reinterpret_cast<const uint32_t *>(in + 40);
-        constexpr int WT = 32 / TS;  // teams per warp
-        const uint64_t warp_g = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-        const uint64_t stride = (uint64_t)gridDim.x * nteams;
-        // warp-uniform trip count: the teams of a warp share shuffles
-        for (uint64_t base = jb + warp_g * WT; base < je; base += stride) {
-            const uint64_t j = base + (uint64_t)(team % WT);
-            const bool active = j < je;
-            int L = 0, G = 0;
-            bool bad = false;
-            PktReader pr;
-            pr.w = reinterpret_cast<const uint32_t *>(in + poff);
-            pr.nwords = 0;
-            if (active) {
-                const uint64_t start = mode == 1 ? 4ull * (uint64_t)__ldg(tab + j) : j * (uint64_t)B;
-                const uint64_t off = j * (uint64_t)N;
-                L = (int)((n - off) < N ? (n - off) : N);
-                G = (L + 3) >> 2;
-                bad = start >= payload || (start & 3);
-                if (!bad) {
-                    pr.w = reinterpret_cast<const uint32_t *>(in + poff + start);
-                    const uint64_t aw = (payload - start) >> 2;
-                    pr.nwords = (uint32_t)(aw > 0xffffffffull ? 0xffffffffull : aw);
-                }
-            }
-            bool oob = false;
-            const uint32_t h0 = active && !bad ? pr.get(0, oob) : 0;
-            const int s = h0 & 3, code = (h0 >> 2) & 4095;
-            const uint32_t plen = h0 >> 14;
-            if (active) {
-                bad |= oob || s == 3 || plen < 4 || (plen & 3) || (uint64_t)plen > 4ull * pr.nwords;
-                if (mode == 0 && j + 1 < nb && plen != B) bad = true;
-            }
-            int Eb = 0;
-            if (active && !bad) {
-                pr.nwords = plen >> 2;
-                if (T::F) Eb = (int)(int16_t)(pr.get(1, oob) & 0xffffu);
-            }
-            bad = team_sum<TS>((int)bad) > 0;
-            if (active && bad && t == 0) set_status(a.status, -9);
-            const bool go0 = active && !bad;
-            const int Gt = go0 ? G : 0;
-            const int g0 = t * gp, g1 = min(g0 + gp, Gt);
-            const int nib = parse_tokens<TS>(pr, H, Gt, W, ebuf, g0, g1);
-            const bool go = go0 && nib >= 0;
-            if (go0 && nib < 0 && t == 0) set_status(a.status, -9);
-            // mantissa bit offset of my groups
-            int mysum = 0;
-            if (go)
-                for (int g = g0; g < g1; ++g) mysum += ebuf[g];
-            const int incl4 = team_incl_scan<TS>(4 * mysum);
-            const int total4 = tshfl<TS>(incl4, TS - 1);
-            if (go && t == 0 && (uint64_t)H + 4ull * (uint64_t)nib + (uint64_t)total4 > 8ull * plen)
-                set_status(a.status, -9);
-            const uint32_t bit0 = (uint32_t)H + 4u * (uint32_t)(go ? nib : 0) + (uint32_t)(incl4 - 4 * mysum);
-            const Dequant<DT> DQ(code, Eb);
-            raw *yb = reinterpret_cast<raw *>(a.y) +
-                      (a.ranged ? (j - a.b0) * (uint64_t)N : j * (uint64_t)N);
-            const int lim = min(L, 4 * g1);  // my samples end here
-            const int ge = go ? g1 : g0;      // my groups [g0, ge)
-            // totals of my samples for the team scan: S = sum w, D = sum of
-            // prefixes of w, len = count; w = u except u_0 of an S2 block
-            uint32_t S = 0, D = 0, u0 = 0;
-            int len = 0;
-            FieldReader fr;
-            if (s != 0) {
-                fr.init(&pr, bit0);
-#pragma unroll 1
-                for (int g = g0; g < ge; ++g) {
-                    const int e = ebuf[g];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int32_t uv = fr.get(e, oob);
-                        const int idx = 4 * g + i;
-                        if (idx == 0) u0 = (uint32_t)uv;
-                        S += (s == 2 && idx == 0) ? 0u : (uint32_t)uv;
-                        D += S;
-                    }
-                }
-                len = 4 * (ge - g0);
-            }
-            // team scan of (S, D, len): A then B -> (SA+SB, DA+DB+lenB*SA, lenA+lenB)
-            uint32_t sS = S, sD = D;
-            int sl = len;
-#pragma unroll
-            for (int d = 1; d < TS; d <<= 1) {
-                const uint32_t oS = tshfl_up<TS>(sS, d), oD = tshfl_up<TS>(sD, d);
-                const int ol = tshfl_up<TS>(sl, d);
-                if (t >= d) {
-                    sD = oD + sD + (uint32_t)sl * oS;
-                    sS = oS + sS;
-                    sl = ol + sl;
-                }
-            }
-            uint32_t runS = tshfl_up<TS>(sS, 1), runD = tshfl_up<TS>(sD, 1);
-            if (t == 0) runS = runD = 0;
-            const uint32_t u0b = tshfl<TS>(u0, 0);
-            // values: inverse derivatives, dequantised, stored 4 at a time
+        bool oob = false;
+        const uint32_t h0 = active && !bad ? pr.get(0, oob) : 0;
+        const int s = h0 & 3, code = (h0 >> 2) & 4095;
+        const uint32_t plen = h0 >> 14;
+        if (active) {
+            bad |= oob || s == 3 || plen < 4 || (plen & 3) || (uint64_t)plen > 4ull * pr.nwords;
+            if (mode == 0 && j + 1 < nb && plen != B) bad = true;
+        }
+        int Eb = 0;
+        if (active && !bad) {
+            pr.nwords = plen >> 2;
+            if (T::F) Eb = (int)(int16_t)(pr.get(1, oob) & 0xffffu);
+        }
+        bad = team_sum<TS>((int)bad) > 0;
+        if (active && bad && t == 0) set_status(a.status, -9);
+        const bool go0 = active && !bad;
+        const int Gt = go0 ? G : 0;
+        const int g0 = t * gp, g1 = min(g0 + gp, Gt);
+        const int nib = parse_tokens<TS>(pr, H, Gt, W, ebuf, g0, g1);
+        const bool go = go0 && nib >= 0;
+        if (go0 && nib < 0 && t == 0) set_status(a.status, -9);
+        // mantissa bit offset of my groups
+        int mysum = 0;
+        if (go)
+            for (int g = g0; g < g1; ++g) mysum += ebuf[g];
+        const int incl4 = team_incl_scan<TS>(4 * mysum);
+        const int total4 = tshfl<TS>(incl4, TS - 1);
+        if (go && t == 0 && (uint64_t)H + 4ull * (uint64_t)nib + (uint64_t)total4 > 8ull * plen)
+            set_status(a.status, -9);
+        const uint32_t bit0 = (uint32_t)H + 4u * (uint32_t)(go ? nib : 0) + (uint32_t)(incl4 - 4 * mysum);
+        const Dequant<DT> DQ(code, Eb);
+        raw *yb = reinterpret_cast<raw *>(a.y) +
+                  (a.ranged ? (j - a.b0) * (uint64_t)N : j * (uint64_t)N);
+        const int lim = min(L, 4 * g1);  // my samples end here
+        const int ge = go ? g1 : g0;      // my groups [g0, ge)
+        // totals of my samples for the team scan: S = sum w, D = sum of
+        // prefixes of w, len = count; w = u except u_0 of an S2 block
+        uint32_t S = 0, D = 0, u0 = 0;
+        int len = 0;
+        FieldReader fr;
+        if (s != 0) {
             fr.init(&pr, bit0);
 #pragma unroll 1
             for (int g = g0; g < ge; ++g) {
                 const int e = ebuf[g];
-                lt out[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const int32_t uv = fr.get(e, oob);
                     const int idx = 4 * g + i;
-                    uint32_t q;
-                    if (s == 0) {
-                        q = (uint32_t)uv;
-                    } else if (s == 1) {
-                        runS += (uint32_t)uv;
-                        q = runS;
-                    } else {
-                        runS += idx == 0 ? 0u : (uint32_t)uv;
-                        runD += runS;
-                        q = u0b + runD;
-                    }
-                    out[i] = DQ(sext_w(q, W));
+                    if (idx == 0) u0 = (uint32_t)uv;
+                    S += (s == 2 && idx == 0) ? 0u : (uint32_t)uv;
+                    D += S;
                 }
-                store4<DT>(yb, 4 * g, lim, out);
             }
-            const int any_oob = team_sum<TS>((int)(go && oob));
-            if (go && any_oob > 0 && t == 0) set_status(a.status, -9);
+            len = 4 * (ge - g0);
+        }
+        // team scan of (S, D, len): A then B -> (SA+SB, DA+DB+lenB*SA, lenA+lenB)
+        uint32_t sS = S, sD = D;
+        int sl = len;
+#pragma unroll
+        for (int d = 1; d < TS; d <<= 1) {
+            const uint32_t oS = tshfl_up<TS>(sS, d), oD = tshfl_up<TS>(sD, d);
+            const int ol = tshfl_up<TS>(sl, d);
+            if (t >= d) {
+                sD = oD + sD + (uint32_t)sl * oS;
+                sS = oS + sS;
+                sl = ol + sl;
+            }
+        }
+        uint32_t runS = tshfl_up<TS>(sS, 1), runD = tshfl_up<TS>(sD, 1);
+        if (t == 0) runS = runD = 0;
+        const uint32_t u0b = tshfl<TS>(u0, 0);
+        // values: inverse derivatives, dequantised, stored 4 at a time
+        fr.init(&pr, bit0);
+#pragma unroll 1
+        for (int g = g0; g < ge; ++g) {
+            const int e = ebuf[g];
+            lt out[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int32_t uv = fr.get(e, oob);
+                const int idx = 4 * g + i;
+                uint32_t q;
+                if (s == 0) {
+                    q = (uint32_t)uv;
+                } else if (s == 1) {
+                    runS += (uint32_t)uv;
+                    q = runS;
+                } else {
+                    runS += idx == 0 ? 0u : (uint32_t)uv;
+                    runD += runS;
+                    q = u0b + runD;
+                }
+                out[i] = DQ(sext_w(q, W));
+            }
+            store4<DT>(yb, 4 * g, lim, out);
+        }
+        const int any_oob = team_sum<TS>((int)(go && oob));
+        if (go && any_oob > 0 && t == 0) set_status(a.status, -9);
+    }
+}
+
+// Size class of a container: teams of 32 for blocks above 4096 samples
+// (header errors are reported by the small class).
+template <int EB>
+__device__ __forceinline__ bool my_class(const DecHdr &h)
+{
+    constexpr bool LARGE = EB > 1024;
+    return h.err == 0 ? ((h.N / 4 > 1024) == LARGE) : !LARGE;
+}
+
+// One array: CTAs stride over tiles of the requested block range.  Both
+// size classes are enqueued; each decodes only the containers of its class.
+template <int DT, int TS, int EB>
+__global__ void __launch_bounds__(128) k_decode(DecArgs a)
+{
+    extern __shared__ uint8_t dsm[];
+    __shared__ DecHdr s_h;
+    if (threadIdx.x == 0) s_h = read_header(a);
+    __syncthreads();
+    const DecHdr hd = s_h;
+    constexpr bool LARGE = EB > 1024;
+    if (my_class<EB>(hd)) {
+        if (hd.err) {
+            if (threadIdx.x == 0) set_status(a.status, hd.err);
+        } else {
+            const int nteams = blockDim.x / TS;
+            const uint64_t jb = a.ranged ? a.b0 : 0, je = a.ranged ? a.b1 : hd.nb;
+            const uint64_t ntiles = (je - jb + nteams - 1) / nteams;
+            for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+                decode_tile<DT, TS, EB>(a, hd, tile, dsm);
         }
     }
     __syncthreads();
@@ -496,7 +531,7 @@ __global__ void __launch_bounds__(128) k_decode(DecArgs a)
         __threadfence();
         unsigned *done = LARGE ? a.done + 1 : a.done;
         const unsigned prev = atomicAdd(done, 1u);
-        if (prev == gridDim.x - 1 && mine) {
+        if (prev == gridDim.x - 1 && my_class<EB>(hd)) {
             __threadfence();
             volatile int *st = a.status;
             if (a.res) {
@@ -504,6 +539,83 @@ __global__ void __launch_bounds__(128) k_decode(DecArgs a)
                 a.res->status = *st;
             }
         }
+    }
+}
+
+template <int DT, int TS, int EB>
+__device__ __noinline__ void decode_tile_call(const DecArgs &a, const DecHdr &hd, uint64_t tile,
+                                              uint8_t *dsm)
+{
+    decode_tile<DT, TS, EB>(a, hd, tile, dsm);
+}
+
+// Many arrays in one persistent launch: global tile tickets, owning array
+// by binary search, per-array completion.  The plan sizes each array's tiles
+// from its declared block size; a container whose header disagrees is
+// reported as corrupt.
+template <int TS, int EB>
+__global__ void __launch_bounds__(128) k_decode_batch(DecBatchArgs ba)
+{
+    extern __shared__ uint8_t dsm[];
+    __shared__ uint64_t s_tile;
+    __shared__ int s_job;
+    __shared__ __align__(16) DecArgs s_args;
+    __shared__ DecHdr s_h;
+    while (true) {
+        if (threadIdx.x == 0) {
+            const uint64_t g = atomicAdd(ba.ticket, 1ull);
+            int lo = 0, hi = ba.count;
+            if (g < ba.total_tiles) {
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (ba.tile_prefix[mid] <= g) lo = mid;
+                    else hi = mid;
+                }
+                s_tile = g - ba.tile_prefix[lo];
+            } else {
+                s_tile = ~0ull;
+            }
+            s_job = lo;
+        }
+        __syncthreads();
+        if (s_tile == ~0ull) break;
+        {
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(ba.jobs + s_job);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(&s_args);
+            for (int i = threadIdx.x; i < (int)(sizeof(DecArgs) / 4); i += blockDim.x) dst[i] = src[i];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            DecHdr h = read_header(s_args);
+            if (h.err == 0 && h.N != ba.block_size[s_job]) h.err = -9;
+            s_h = h;
+            if (h.err) set_status(s_args.status, h.err);
+        }
+        __syncthreads();
+        const DecHdr hd = s_h;
+        if (hd.err == 0) {
+            switch (s_args.dtype) {
+            case 1: decode_tile_call<1, TS, EB>(s_args, hd, s_tile, dsm); break;
+            case 2: decode_tile_call<2, TS, EB>(s_args, hd, s_tile, dsm); break;
+            case 3: decode_tile_call<3, TS, EB>(s_args, hd, s_tile, dsm); break;
+            case 4: decode_tile_call<4, TS, EB>(s_args, hd, s_tile, dsm); break;
+            default: decode_tile_call<5, TS, EB>(s_args, hd, s_tile, dsm); break;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const unsigned prev = atomicAdd(s_args.done, 1u);
+            if (prev == ba.tiles_of[s_job] - 1) {
+                __threadfence();
+                volatile int *st = s_args.status;
+                if (s_args.res) {
+                    s_args.res->bytes = s_args.n;
+                    s_args.res->status = *st;
+                }
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -528,6 +640,28 @@ static cudaError_t launch_dt(const DecArgs &a, cudaStream_t s)
 }
 
 }  // namespace
+
+cudaError_t launch_decode_batch(const DecBatchArgs &b, int ts, int threads, unsigned ctas,
+                               cudaStream_t s)
+{
+    const size_t smem = (size_t)(threads / ts) * (ts == 8 ? 1024 : 4096);
+    auto k = ts == 8 ? k_decode_batch<8, 1024> : k_decode_batch<32, 4096>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (ctas) k<<<ctas, threads, smem, s>>>(b);
+    return cudaGetLastError();
+}
+
+int decode_batch_occupancy(int ts, int threads)
+{
+    const size_t smem = (size_t)(threads / ts) * (ts == 8 ? 1024 : 4096);
+    auto k = ts == 8 ? k_decode_batch<8, 1024> : k_decode_batch<32, 4096>;
+    int nb = 0;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, smem) != cudaSuccess) return 0;
+    return nb;
+}
 
 cudaError_t launch_decode(const DecArgs &a, cudaStream_t s)
 {

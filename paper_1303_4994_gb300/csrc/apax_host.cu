@@ -62,6 +62,46 @@ int fill_enc_args(const void *x, int dtype, uint64_t n, const apax_params *p,
     return APAX_OK;
 }
 
+int fill_prof_args(const void *x, int dtype, uint64_t n, uint32_t block_size,
+                   const uint16_t *candidates, int ncand, double target,
+                   apax_profile_point *points, apax_profile_summary *summary, ProfArgs &a)
+{
+    Fmt f;
+    int st = fmt_of(dtype, f);
+    if (st) return st;
+    if (!block_size_ok(block_size)) return APAX_ERR_BLOCK_SIZE;
+    uint16_t def[16];
+    if (!candidates) {
+        if (ncand != APAX_PROFILE_DEFAULT_CANDIDATES) return APAX_ERR_INVALID_ARG;
+        for (int i = 0; i < 16; ++i) def[i] = (uint16_t)(256 * i);
+        candidates = def;
+    }
+    if (ncand < 1 || ncand > 32 || (!x && n) || !points || !summary) return APAX_ERR_INVALID_ARG;
+    if (((uintptr_t)x % f.size) || ((uintptr_t)points & 7) || ((uintptr_t)summary & 7))
+        return APAX_ERR_INVALID_ARG;
+    for (int i = 0; i < ncand; ++i) {
+        // power-of-two attenuations only (m = 0), strictly increasing
+        if (candidates[i] > 4095 || (candidates[i] & 127)) return APAX_ERR_INVALID_ARG;
+        if (i && candidates[i] <= candidates[i - 1]) return APAX_ERR_INVALID_ARG;
+    }
+    if (!(target == target)) return APAX_ERR_INVALID_ARG;
+    const uint64_t nb = (n + block_size - 1) / block_size;
+    memset(&a, 0, sizeof a);
+    a.x = x;
+    a.n = n;
+    a.N = block_size;
+    a.nb = nb;
+    a.dtype = dtype;
+    a.ncand = ncand;
+    for (int i = 0; i < ncand; ++i) a.codes[i] = candidates[i];
+    a.nruns = (nb + 15) / 16;
+    a.gp = (int)((block_size / 4 + 7) / 8);  // teams of 8 threads
+    a.target = target;
+    a.points = points;
+    a.summary = summary;
+    return APAX_OK;
+}
+
 }  // namespace host
 }  // namespace apax
 
@@ -272,43 +312,14 @@ int apax_profile(const void *x, int dtype, uint64_t n, uint32_t block_size,
                  uint64_t workspace_bytes, apax_profile_point *points,
                  apax_profile_summary *summary, void *stream)
 {
-    Fmt f;
-    int st = fmt_of(dtype, f);
+    ProfArgs a;
+    int st = fill_prof_args(x, dtype, n, block_size, candidates, ncand, target, points, summary, a);
     if (st) return st;
-    if (!block_size_ok(block_size)) return APAX_ERR_BLOCK_SIZE;
-    uint16_t def[16];
-    if (!candidates) {
-        if (ncand != APAX_PROFILE_DEFAULT_CANDIDATES) return APAX_ERR_INVALID_ARG;
-        for (int i = 0; i < 16; ++i) def[i] = (uint16_t)(256 * i);
-        candidates = def;
-    }
-    if (ncand < 1 || ncand > 32 || (!x && n) || !points || !summary || !workspace)
-        return APAX_ERR_INVALID_ARG;
-    if (((uintptr_t)workspace & 15) || ((uintptr_t)x % f.size) || ((uintptr_t)points & 7) ||
-        ((uintptr_t)summary & 7))
-        return APAX_ERR_INVALID_ARG;
-    for (int i = 0; i < ncand; ++i) {
-        // power-of-two attenuations only (m = 0), strictly increasing
-        if (candidates[i] > 4095 || (candidates[i] & 127)) return APAX_ERR_INVALID_ARG;
-        if (i && candidates[i] <= candidates[i - 1]) return APAX_ERR_INVALID_ARG;
-    }
-    if (!(target == target)) return APAX_ERR_INVALID_ARG;
+    if (!workspace || ((uintptr_t)workspace & 15)) return APAX_ERR_INVALID_ARG;
     uint64_t need;
     st = apax_profile_workspace_size(dtype, n, block_size, ncand, &need);
     if (st) return st;
     if (workspace_bytes < need) return APAX_ERR_CAPACITY;
-    const uint64_t nb = (n + block_size - 1) / block_size;
-    ProfArgs a;
-    memset(&a, 0, sizeof a);
-    a.x = x;
-    a.n = n;
-    a.N = block_size;
-    a.nb = nb;
-    a.dtype = dtype;
-    a.ncand = ncand;
-    for (int i = 0; i < ncand; ++i) a.codes[i] = candidates[i];
-    a.nruns = (nb + 15) / 16;
-    a.gp = (int)((block_size / 4 + 7) / 8);  // teams of 8 threads
     uint8_t *w = (uint8_t *)workspace;
     a.done = (unsigned *)(w + 4);
     a.status = (int *)(w + 8);
@@ -316,9 +327,6 @@ int apax_profile(const void *x, int dtype, uint64_t n, uint32_t block_size,
     const uint64_t Qn = 2 + 4 * (uint64_t)ncand;
     a.run_sums = (double *)(w + kWsHead + 8 * 32);
     a.scratch = a.run_sums + Qn * (a.nruns ? a.nruns : 1);
-    a.target = target;
-    a.points = points;
-    a.summary = summary;
     cudaStream_t s = (cudaStream_t)stream;
     st = cuda_fail(cudaMemsetAsync(workspace, 0, kWsHead + 8 * 32, s));
     if (st) return st;

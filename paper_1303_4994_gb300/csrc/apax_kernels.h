@@ -61,6 +61,18 @@ struct DecArgs {
     apax_result *res;
 };
 
+// Many containers in one launch: jobs[i] owns global tiles
+// [tile_prefix[i], tile_prefix[i + 1]) of its declared block size.
+struct DecBatchArgs {
+    const DecArgs *jobs;
+    const uint64_t *tile_prefix;  // count + 1 entries
+    const uint64_t *tiles_of;     // tiles per job
+    const uint32_t *block_size;   // declared block size per job
+    int count;
+    uint64_t total_tiles;
+    unsigned long long *ticket;
+};
+
 struct ProfArgs {
     const void *x;
     uint64_t n;
@@ -87,7 +99,23 @@ cudaError_t launch_encode_batch(const EncBatchArgs &b, int ts, int threads, size
                                unsigned ctas, cudaStream_t s);
 int encode_batch_occupancy(int ts, int threads, size_t smem);  // CTAs per SM
 cudaError_t launch_decode(const DecArgs &a, cudaStream_t s);
+cudaError_t launch_decode_batch(const DecBatchArgs &b, int ts, int threads, unsigned ctas,
+                               cudaStream_t s);
+int decode_batch_occupancy(int ts, int threads);
 cudaError_t launch_profile(const ProfArgs &a, cudaStream_t s);
+
+// Many arrays' profiler sweeps in one launch: jobs[i] owns global runs
+// [run_prefix[i], run_prefix[i + 1]) (at least one, to finalise empty arrays).
+struct ProfBatchArgs {
+    const ProfArgs *jobs;
+    const uint64_t *run_prefix;
+    int count;
+    uint64_t total_runs;
+    unsigned long long *ticket;
+};
+cudaError_t launch_profile_batch(const ProfBatchArgs &b, int max_ncand, unsigned ctas,
+                                 cudaStream_t s);
+int profile_batch_occupancy(int max_ncand);
 
 // apax_encode with an already-sized workspace supplied by another entry point.
 int encode_with_workspace(const void *x, int dtype, uint64_t n, const apax_params *p, void *out,

@@ -137,6 +137,12 @@ int fill_enc_args(const void *x, int dtype, uint64_t n, const apax_params *p,
                   const uint32_t *code_dev, void *out, uint64_t cap, apax_result *res, EncArgs &a,
                   uint32_t &pkt_words, uint32_t &ebuf_words);
 
+// Validate one profile call and fill its arguments (all but the workspace
+// pointers).
+int fill_prof_args(const void *x, int dtype, uint64_t n, uint32_t block_size,
+                   const uint16_t *candidates, int ncand, double target,
+                   apax_profile_point *points, apax_profile_summary *summary, ProfArgs &a);
+
 inline int cuda_fail(cudaError_t e) { return e == cudaSuccess ? APAX_OK : APAX_ERR_CUDA; }
 
 

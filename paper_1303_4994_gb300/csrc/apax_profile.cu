@@ -170,14 +170,15 @@ __device__ void fallback_team(const TBlock<DT> &b, int code, bool want_block,
     }
 }
 
+// One run (kRun consecutive blocks, a level-1 node of the summation tree):
+// the CTA's teams take one block each and write the run's partial sums.
 template <int DT>
-__global__ void __launch_bounds__(128) k_profile(ProfArgs a)
+__device__ __forceinline__ void profile_run(const ProfArgs &a, uint64_t run, uint8_t *psm)
 {
     using T = DT_<DT>;
     using raw = typename T::raw;
     using lt = typename LaneT<DT>::t;
     constexpr int W = T::W, H = T::H;
-    extern __shared__ __align__(16) uint8_t psm[];
     const int team = threadIdx.x / TS, t = tlane<TS>();
     const int nteams = blockDim.x / TS;  // = kRun
     const int nc = a.ncand;
@@ -190,7 +191,7 @@ __global__ void __launch_bounds__(128) k_profile(ProfArgs a)
     __shared__ uint64_t s_txx[kRun][4];  // f32: sum x^2 of the tiny samples (side grid)
 
     const int gp = a.gp;
-    const uint64_t j = (uint64_t)blockIdx.x * nteams + team;
+    const uint64_t j = run * nteams + team;
     const raw *x = reinterpret_cast<const raw *>(a.x);
     int s;
     {
@@ -513,7 +514,7 @@ __global__ void __launch_bounds__(128) k_profile(ProfArgs a)
         double acc = 0.0;
         for (int tm = 0; tm < nteams; ++tm)
             if (s_ok[tm]) acc = __dadd_rn(acc, bv[(size_t)tm * Qn + q]);
-        a.run_sums[(uint64_t)blockIdx.x * Qn + q] = acc;
+        a.run_sums[run * Qn + q] = acc;
     }
     for (int ci = threadIdx.x; ci < nc; ci += blockDim.x) {
         unsigned long long by = 0;
@@ -524,6 +525,13 @@ __global__ void __launch_bounds__(128) k_profile(ProfArgs a)
             }
         atomicAdd(a.bytes + ci, by);
     }
+}
+
+template <int DT>
+__global__ void __launch_bounds__(128) k_profile(ProfArgs a)
+{
+    extern __shared__ __align__(16) uint8_t psm[];
+    profile_run<DT>(a, blockIdx.x, psm);
 }
 
 // One level of the fan-in-16 tree: out[m][q] = in[16m][q] + ... (in order).
@@ -551,15 +559,16 @@ __device__ double corr_r(double sxx, double sxy, double syy)
     return __ddiv_rn(__ddiv_rn(sxy, __dsqrt_rn(sxx)), __dsqrt_rn(syy));
 }
 
-__global__ void k_finalize(ProfArgs a, const double *tot, uint64_t container_fixed)
+// Points and summary from the sums of the whole array (threads 0..31).
+__device__ void finalize_points(const ProfArgs &a, const double *tot, uint64_t container_fixed,
+                                double *s_r)
 {
     const int nc = a.ncand;
-    __shared__ double s_r[32];
     const int i = threadIdx.x;
     if (i < nc) {
         apax_profile_point p;
         p.code = a.codes[i];
-        p.bytes = container_fixed + a.bytes[i];
+        p.bytes = container_fixed + *(volatile unsigned long long *)(a.bytes + i);
         p.sx = tot[0];
         p.sxx = tot[1];
         p.sy = tot[2 + 4 * i];
@@ -579,12 +588,119 @@ __global__ void k_finalize(ProfArgs a, const double *tot, uint64_t container_fix
             else break;
         }
         apax_profile_summary sm;
-        sm.status = *a.status;
+        sm.status = *(volatile int *)a.status;
         sm.recommended = rec < 0 ? 0 : rec;
         sm.recommended_code = a.codes[rec < 0 ? 0 : rec];
         sm.flags = rec < 0 ? 1u : 0u;
         sm.n = a.n;
         *a.summary = sm;
+    }
+}
+
+__global__ void k_finalize(ProfArgs a, const double *tot, uint64_t container_fixed)
+{
+    __shared__ double s_r[32];
+    finalize_points(a, tot, container_fixed, s_r);
+}
+
+// The whole fan-in-16 tree over the array's run sums and the finalisation,
+// by one CTA (after every run of the array is written).  Same additions in
+// the same order as the k_tree levels.
+__device__ void tree_finalize_cta(const ProfArgs &a, double *s_r)
+{
+    const int Qn = 2 + 4 * a.ncand;
+    uint64_t cnt = a.nruns;
+    const double *in = a.run_sums;
+    double *bufs[2] = {a.scratch, a.scratch + ((a.nruns + 15) / 16 + 1) * (uint64_t)Qn};
+    int pi = 0;
+    if (cnt == 0) {
+        for (int q = threadIdx.x; q < Qn; q += blockDim.x) __stcg(a.scratch + q, 0.0);
+        in = a.scratch;
+    }
+    while (cnt > 1) {
+        const uint64_t nodes = (cnt + 15) / 16;
+        for (uint64_t m = threadIdx.x; m < nodes * (uint64_t)Qn; m += blockDim.x) {
+            const uint64_t node = m / Qn, q = m % Qn;
+            const uint64_t a0 = node * 16, a1 = min(a0 + 16, cnt);
+            double sum = __ldcg(in + a0 * Qn + q);
+            for (uint64_t i = a0 + 1; i < a1; ++i) sum = __dadd_rn(sum, __ldcg(in + i * Qn + q));
+            __stcg(bufs[pi] + node * Qn + q, sum);
+        }
+        __syncthreads();
+        in = bufs[pi];
+        pi ^= 1;
+        cnt = nodes;
+    }
+    __syncthreads();
+    // the totals into shared memory (at most 2 + 4 * 32 values)
+    __shared__ double s_tot[2 + 4 * 32];
+    for (int q = threadIdx.x; q < Qn; q += blockDim.x) s_tot[q] = __ldcg(in + q);
+    __syncthreads();
+    const uint64_t fixed = 40 + ((4 * a.nb + 7) / 8) * 8;
+    finalize_points(a, s_tot, fixed, s_r);
+}
+
+template <int DT>
+__device__ __noinline__ void profile_run_call(const ProfArgs &a, uint64_t run, uint8_t *psm)
+{
+    profile_run<DT>(a, run, psm);
+}
+
+// Many arrays' profiler sweeps in one persistent launch: global run
+// tickets, owning array by binary search; the CTA that completes an array's
+// last run adds up its tree and writes its points and summary.
+__global__ void __launch_bounds__(128) k_profile_batch(ProfBatchArgs ba)
+{
+    extern __shared__ __align__(16) uint8_t psm[];
+    __shared__ uint64_t s_run;
+    __shared__ int s_job, s_last;
+    __shared__ __align__(16) ProfArgs s_args;
+    __shared__ double s_r[32];
+    while (true) {
+        if (threadIdx.x == 0) {
+            const uint64_t g = atomicAdd(ba.ticket, 1ull);
+            int lo = 0, hi = ba.count;
+            if (g < ba.total_runs) {
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (ba.run_prefix[mid] <= g) lo = mid;
+                    else hi = mid;
+                }
+                s_run = g - ba.run_prefix[lo];
+            } else {
+                s_run = ~0ull;
+            }
+            s_job = lo;
+        }
+        __syncthreads();
+        if (s_run == ~0ull) break;
+        {
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(ba.jobs + s_job);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(&s_args);
+            for (int i = threadIdx.x; i < (int)(sizeof(ProfArgs) / 4); i += blockDim.x) dst[i] = src[i];
+        }
+        __syncthreads();
+        if (s_args.nruns) {
+            switch (s_args.dtype) {
+            case 1: profile_run_call<1>(s_args, s_run, psm); break;
+            case 2: profile_run_call<2>(s_args, s_run, psm); break;
+            case 3: profile_run_call<3>(s_args, s_run, psm); break;
+            case 4: profile_run_call<4>(s_args, s_run, psm); break;
+            default: profile_run_call<5>(s_args, s_run, psm); break;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const uint64_t units = s_args.nruns ? s_args.nruns : 1;
+            s_last = atomicAdd(s_args.done, 1u) == units - 1;
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            tree_finalize_cta(s_args, s_r);
+        }
+        __syncthreads();
     }
 }
 
@@ -603,6 +719,38 @@ cudaError_t launch_prof_dt(const ProfArgs &a, cudaStream_t s)
 }
 
 }  // namespace
+
+size_t profile_smem(int ncand, bool any_float, int dtype_max_nd)
+{
+    const int Qn = 2 + 4 * ncand;
+    (void)any_float;
+    return (size_t)kRun * ncand * sizeof(CandStage) + (size_t)kRun * Qn * 8 +
+           (size_t)6 * dtype_max_nd * 8;
+}
+
+cudaError_t launch_profile_batch(const ProfBatchArgs &b, int max_ncand, unsigned ctas,
+                                 cudaStream_t s)
+{
+    const size_t smem = profile_smem(max_ncand, true, PS<5>::ND);
+    cudaError_t e = cudaFuncSetAttribute(k_profile_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    if (ctas) k_profile_batch<<<ctas, TS * kRun, smem, s>>>(b);
+    return cudaGetLastError();
+}
+
+int profile_batch_occupancy(int max_ncand)
+{
+    const size_t smem = profile_smem(max_ncand, true, PS<5>::ND);
+    int nb = 0;
+    if (cudaFuncSetAttribute(k_profile_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_profile_batch, TS * kRun, smem) !=
+        cudaSuccess)
+        return 0;
+    return nb;
+}
 
 cudaError_t launch_profile(const ProfArgs &a, cudaStream_t s)
 {

@@ -166,3 +166,102 @@ def test_batch_encode_graph_replay_and_device_code():
     g.replay()
     torch.cuda.synchronize()
     _check(outs, results, want)
+
+
+UINT = {1: np.uint8, 2: np.uint16, 3: np.uint32, 4: np.uint32, 5: np.uint64}
+
+
+def _decode_batch(containers, arrays, ps, block_sizes=None):
+    ys = [torch.full((a.size,), 7, dtype=torch.from_numpy(a[:0]).dtype, device="cuda")
+          for a in arrays]
+    results = torch.zeros(16 * len(ys), dtype=torch.uint8, device="cuda")
+    bs = block_sizes or [p.block_size for p in ps]
+    jobs = A.decode_jobs(containers, ys, bs, results)
+    ws = A.aligned_workspace(A.batch_decode_workspace_size(jobs))
+    return ys, results, A.Batch(jobs, ws)
+
+
+@pytest.mark.parametrize("big", [False, True])
+def test_batch_decode_matches_oracle(big):
+    arrays, ps = _mixed_batch(5 + big, 40, big_blocks=big)
+    want = _want(arrays, ps)
+    containers = [torch.from_numpy(np.frombuffer(w, dtype=np.uint8).copy()).cuda() for w in want]
+    ys, results, plan = _decode_batch(containers, arrays, ps)
+    for cfg in [None, (64, 1), (128, 2)] if not big else [None, (32, 2), (128, 1)]:
+        if cfg is not None:
+            plan.config = cfg
+        results.zero_()
+        for y in ys:
+            y.fill_(7)
+        plan.run()
+        torch.cuda.synchronize()
+        rs = A.read_results(results, len(ys))
+        for i, (a, w, y, r) in enumerate(zip(arrays, want, ys, rs)):
+            assert r.status == 0 and r.bytes == a.size, (i, r)
+            yo = O.decode(w, a.dtype, a.size)
+            np.testing.assert_array_equal(y.cpu().numpy().view(UINT[A.TORCH_CODE[y.dtype]]),
+                                          yo.view(UINT[A.TORCH_CODE[y.dtype]]))
+    plan.tune(reps=1)
+    plan.close()
+
+
+def test_batch_decode_reports_per_container_errors():
+    arrays, ps = _mixed_batch(8, 10)
+    want = _want(arrays, ps)
+    containers = [torch.from_numpy(np.frombuffer(w, dtype=np.uint8).copy()).cuda() for w in want]
+    bs = [p.block_size for p in ps]
+    bad = 6  # declared block size differs from the container's
+    bs[bad] = 128 if bs[bad] != 128 else 64
+    containers[7] = containers[7][:20].contiguous()  # truncated header
+    ys, results, plan = _decode_batch(containers, arrays, ps, block_sizes=bs)
+    plan.run()
+    torch.cuda.synchronize()
+    rs = A.read_results(results, len(ys))
+    for i, (a, w, y, r) in enumerate(zip(arrays, want, ys, rs)):
+        if i == bad:
+            assert r.status == -9
+        elif i == 7:
+            assert r.status == -9
+        else:
+            assert r.status == 0, (i, r)
+            yo = O.decode(w, a.dtype, a.size)
+            np.testing.assert_array_equal(y.cpu().numpy().view(UINT[A.TORCH_CODE[y.dtype]]),
+                                          yo.view(UINT[A.TORCH_CODE[y.dtype]]))
+
+
+def test_batch_profile_matches_oracle():
+    import struct
+    rng = np.random.default_rng(11)
+    arrays, Ns, cands, targets = [], [], [], []
+    specs = [(4, 0), (2, 1), (5, 300), (4, 256 * 16 * 3 + 5), (1, 4000), (3, 9000),
+             (4, 70000), (5, 33333), (2, 256 * 16)]
+    for dt, n in specs:
+        arrays.append(_array(rng, dt, n))
+        Ns.append(int(rng.choice([64, 256, 1000])))
+        k = int(rng.integers(1, 17))
+        cands.append(sorted(set(int(c) * 128 for c in rng.choice(32, k, replace=False))))
+        targets.append(float(rng.choice([0.9, 0.999, 0.99999])))
+    xs = [torch.from_numpy(a).cuda() for a in arrays]
+    pts = [torch.zeros(A.POINT_BYTES * len(c), dtype=torch.uint8, device="cuda") for c in cands]
+    sums = [torch.zeros(A.SUMMARY_BYTES, dtype=torch.uint8, device="cuda") for _ in cands]
+    jobs = A.profile_jobs(xs, Ns, cands, targets, pts, sums)
+    ws = A.aligned_workspace(A.batch_profile_workspace_size(jobs))
+    plan = A.Batch(jobs, ws)
+    for rep in range(2):
+        for p in pts + sums:
+            p.zero_()
+        plan.run()
+        torch.cuda.synchronize()
+        for i, a in enumerate(arrays):
+            po, rec, missed = O.profile(a, N=Ns[i], candidates=cands[i], target=targets[i])
+            got = A.read_points(pts[i], len(cands[i]))
+            sm = A.read_summary(sums[i])
+            assert sm.status == 0 and sm.n == a.size
+            for o, g in zip(po, got):
+                assert o.code == g.code and o.bytes == g.bytes, (i, o.code, o.bytes, g.bytes)
+                for f in ("sx", "sy", "sxx", "sxy", "syy", "sdd", "r"):
+                    assert struct.pack("<d", getattr(o, f)) == struct.pack("<d", getattr(g, f)), \
+                        (i, f, getattr(o, f), getattr(g, f))
+            assert sm.recommended == rec and bool(sm.flags & 1) == missed
+        if rep == 0:
+            plan.tune(reps=1)
