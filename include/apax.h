@@ -248,6 +248,7 @@ typedef struct {
 } apax_encode_job;
 
 typedef struct apax_batch apax_batch;   /* opaque host-side plan */
+typedef struct apax_server apax_server; /* opaque request server */
 
 /* Launch geometry of a plan: CTA size (teams of 8 threads: 64 or 128, i.e.
  * 8 or 16 blocks per tile; teams of 32 -- one block per warp -- when a
@@ -330,6 +331,69 @@ int apax_batch_tune(apax_batch *plan, int reps, void *stream);
 uint64_t apax_batch_tiles(const apax_batch *plan);
 
 void apax_batch_destroy(apax_batch *plan);
+
+/* ---------------------------------------------------------------- serving
+ * A request server with continuous batching (no counterpart in the paper).
+ * Requests queue on the host; every apax_server_poll retires finished steps
+ * and admits queued requests, first come first served, while a step slot is
+ * free and the device arena has room for their outputs and workspace; the
+ * admitted requests run as one step (one batched encode launch and one
+ * batched decode launch on the slot's stream).  Steps on different slots
+ * overlap on the device.  The arena is caller-owned device memory and its
+ * size is the admission cap; the server allocates pinned host memory for
+ * its job-table staging and results.  Every output is byte-identical to the
+ * single-array call on the same request.  Host calls on one server must
+ * not run concurrently. */
+enum { APAX_OP_ENCODE = 0, APAX_OP_DECODE = 1 };
+
+typedef struct {
+    void *arena;                /* device, 256-byte aligned */
+    uint64_t arena_bytes;       /* admission cap */
+    uint32_t slots;             /* steps in flight at once (1..64) */
+    uint32_t max_batch;         /* requests per step (1..65536) */
+} apax_server_config;
+
+typedef struct {
+    uint64_t id;                /* caller's tag, returned in the completion */
+    int32_t op;                 /* APAX_OP_ENCODE / APAX_OP_DECODE */
+    int32_t dtype;
+    uint64_t n;                 /* elements */
+    apax_params p;              /* encode: all fields; decode: block_size */
+    const void *in;             /* device: samples (encode) or container (decode) */
+    uint64_t in_bytes;          /* decode: container bytes */
+    void *out;                  /* device output, or NULL: allocated from the arena
+                                   (give it back with apax_server_release) */
+    uint64_t out_capacity;
+    double t_arrival;           /* seconds on the server clock, or 0: submit time */
+} apax_request;
+
+typedef struct {
+    uint64_t id;
+    int32_t op;
+    int32_t status;             /* apax_result status of the request */
+    uint64_t bytes;             /* container bytes (encode) or elements (decode) */
+    void *out;                  /* where the output is */
+    double t_arrival, t_submit, t_launch, t_done;  /* server clock, seconds */
+} apax_completion;
+
+typedef struct {
+    uint64_t queued, inflight, busy_slots;
+    uint64_t arena_used, arena_peak;
+    uint64_t steps, admitted, completed, undelivered;
+} apax_server_stats_t;
+
+int apax_server_create(const apax_server_config *cfg, apax_server **srv);
+/* Queue a request (host checks of the single-array call; a request that
+ * could never fit the arena returns APAX_ERR_CAPACITY). */
+int apax_server_submit(apax_server *srv, const apax_request *req);
+/* Retire finished steps, admit queued requests, and return up to max_out
+ * completions (never waits for the device). */
+int apax_server_poll(apax_server *srv, apax_completion *out, int max_out, int *n_out);
+/* Give a server-allocated output back to the arena. */
+int apax_server_release(apax_server *srv, void *out);
+int apax_server_stats(const apax_server *srv, apax_server_stats_t *stats);
+/* Waits for the steps in flight, then frees the server's host resources. */
+void apax_server_destroy(apax_server *srv);
 
 /* Human-readable text of a status code. */
 const char *apax_status_string(int status);

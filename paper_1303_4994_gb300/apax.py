@@ -74,6 +74,31 @@ class ProfileJob(ctypes.Structure):
                 ("points", ctypes.c_void_p), ("summary", ctypes.c_void_p)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("arena", ctypes.c_void_p), ("arena_bytes", ctypes.c_uint64),
+                ("slots", ctypes.c_uint32), ("max_batch", ctypes.c_uint32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("op", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("n", ctypes.c_uint64), ("p", Params), ("in_", ctypes.c_void_p),
+                ("in_bytes", ctypes.c_uint64), ("out", ctypes.c_void_p),
+                ("out_capacity", ctypes.c_uint64), ("t_arrival", ctypes.c_double)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("op", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("bytes", ctypes.c_uint64), ("out", ctypes.c_void_p),
+                ("t_arrival", ctypes.c_double), ("t_submit", ctypes.c_double),
+                ("t_launch", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in ("queued", "inflight", "busy_slots", "arena_used",
+                                                "arena_peak", "steps", "admitted", "completed",
+                                                "undelivered")]
+
+
 class BatchConfig(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32)]
 
@@ -92,7 +117,9 @@ EXPORTS = ("apax_encoded_size", "apax_workspace_size", "apax_encode", "apax_enco
            "apax_batch_run", "apax_batch_get_config", "apax_batch_set_config", "apax_batch_tune",
            "apax_batch_tiles", "apax_batch_destroy", "apax_batch_decode_workspace_size",
            "apax_batch_decode_create", "apax_batch_profile_workspace_size",
-           "apax_batch_profile_create")
+           "apax_batch_profile_create", "apax_server_create", "apax_server_submit",
+           "apax_server_poll", "apax_server_release", "apax_server_stats", "apax_server_destroy")
+OP_ENCODE, OP_DECODE = 0, 1
 NOALLOC_SCRATCH_BYTES = 256 << 10
 
 
@@ -138,6 +165,13 @@ def lib():
         L.apax_batch_tiles.restype = u64
         L.apax_batch_destroy.argtypes = [vp]
         L.apax_batch_destroy.restype = None
+        L.apax_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
+        L.apax_server_submit.argtypes = [vp, ctypes.POINTER(Request)]
+        L.apax_server_poll.argtypes = [vp, ctypes.POINTER(Completion), i32, ctypes.POINTER(i32)]
+        L.apax_server_release.argtypes = [vp, vp]
+        L.apax_server_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+        L.apax_server_destroy.argtypes = [vp]
+        L.apax_server_destroy.restype = None
         L.apax_status_string.argtypes = [i32]
         L.apax_status_string.restype = ctypes.c_char_p
         L.apax_build_info.argtypes = []
@@ -417,6 +451,68 @@ def aligned_workspace(nbytes: int, device="cuda") -> torch.Tensor:
     """A uint8 device tensor of nbytes starting on a 256-byte boundary."""
     ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
     return ws[(-ws.data_ptr()) % 256:][:nbytes]
+
+
+# ----------------------------------------------------------------- serving
+class Server:
+    """Request server with continuous batching (apax_server_*).  `arena` is a
+    256-byte aligned uint8 device tensor: the admission cap and the memory
+    outputs the server allocates come from."""
+
+    def __init__(self, arena: torch.Tensor, slots: int = 4, max_batch: int = 256):
+        self.arena = arena
+        cfg = ServerConfig(arena.data_ptr(), arena.numel(), slots, max_batch)
+        h = ctypes.c_void_p()
+        _check(lib().apax_server_create(ctypes.byref(cfg), ctypes.byref(h)), "server_create")
+        self.handle = h
+        self._buf = (Completion * 1024)()
+
+    def submit_encode(self, rid: int, x: torch.Tensor, p: Params, out: torch.Tensor | None = None,
+                      t_arrival: float = 0.0):
+        xf = x.reshape(-1)
+        r = Request(rid, OP_ENCODE, _dtype_code(xf), xf.numel(), p, xf.data_ptr(), 0,
+                    out.data_ptr() if out is not None else None,
+                    out.numel() if out is not None else 0, t_arrival)
+        _check(lib().apax_server_submit(self.handle, ctypes.byref(r)), "server_submit")
+
+    def submit_decode(self, rid: int, container: torch.Tensor, dtype: torch.dtype, n: int,
+                      block_size: int, out: torch.Tensor | None = None, t_arrival: float = 0.0):
+        p = params(block_size)
+        r = Request(rid, OP_DECODE, TORCH_CODE[dtype], n, p, container.data_ptr(),
+                    container.numel(), out.data_ptr() if out is not None else None,
+                    out.numel() * out.element_size() if out is not None else 0, t_arrival)
+        _check(lib().apax_server_submit(self.handle, ctypes.byref(r)), "server_submit")
+
+    def poll(self):
+        k = ctypes.c_int()
+        _check(lib().apax_server_poll(self.handle, self._buf, len(self._buf), ctypes.byref(k)),
+               "server_poll")
+        return [Completion.from_buffer_copy(self._buf[i]) for i in range(k.value)]
+
+    def output(self, c: Completion, nbytes: int) -> torch.Tensor:
+        """The bytes of a server-allocated output, as a view into the arena."""
+        off = c.out - self.arena.data_ptr()
+        assert 0 <= off and off + nbytes <= self.arena.numel()
+        return self.arena[off:off + nbytes]
+
+    def release(self, out_ptr: int):
+        _check(lib().apax_server_release(self.handle, out_ptr), "server_release")
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().apax_server_stats(self.handle, ctypes.byref(st)), "server_stats")
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if self.handle:
+            lib().apax_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ----------------------------------------------------------------- decode

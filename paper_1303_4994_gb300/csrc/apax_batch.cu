@@ -60,12 +60,28 @@ struct apax_batch {
     int sms;
     int dev;
     std::string key;               // tuner cache key
+    // table upload: synchronous (plans), or from pinned staging on a stream
+    uint8_t *pinned;
+    uint64_t pinned_bytes, pinned_used;
+    cudaStream_t up_stream;
 };
 
 namespace {
 
 std::mutex g_tune_mu;
 std::map<std::string, apax_batch_config> g_tune_cache;
+
+// Copy one table into the workspace.
+bool upload(apax_batch *b, void *dst, const void *src, size_t bytes)
+{
+    if (!b->pinned) return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+    const size_t off = align_up(b->pinned_used, 16);
+    if (off + bytes > b->pinned_bytes) return false;
+    memcpy(b->pinned + off, src, bytes);
+    b->pinned_used = off + bytes;
+    return cudaMemcpyAsync(dst, b->pinned + off, bytes, cudaMemcpyHostToDevice, b->up_stream) ==
+           cudaSuccess;
+}
 
 Geo geo_of(const apax_batch *b, const apax_batch_config &c)
 {
@@ -157,10 +173,8 @@ int apply_config(apax_batch *b, const apax_batch_config &c)
     b->d_prefix = (uint64_t *)(b->ws + L.prefix);
     b->d_zero = b->ws + L.zero;
     b->zero_bytes = L.tiles + 8 * tiles_words - L.zero;
-    if (cudaMemcpy(b->d_jobs, tab.data(), tab.size() * sizeof(EncArgs), cudaMemcpyHostToDevice) !=
-            cudaSuccess ||
-        cudaMemcpy(b->d_prefix, prefix.data(), prefix.size() * 8, cudaMemcpyHostToDevice) !=
-            cudaSuccess)
+    if (!upload(b, b->d_jobs, tab.data(), tab.size() * sizeof(EncArgs)) ||
+        !upload(b, b->d_prefix, prefix.data(), prefix.size() * 8))
         return APAX_ERR_CUDA;
     b->cfg = c;
     if (b->cfg.ctas_per_sm == 0) {
@@ -173,7 +187,7 @@ int apply_config(apax_batch *b, const apax_batch_config &c)
 apax_batch_config default_config(const apax_batch *b)
 {
     apax_batch_config c;
-    if (b->op == 1) {
+    if (b->op != 0) {
         c.threads = 128;
         c.ctas_per_sm = 0;
         return c;
@@ -291,14 +305,10 @@ int apply_decode_config(apax_batch *b, const apax_batch_config &c)
     b->d_bsize = (uint32_t *)(b->ws + L.bsize);
     b->d_zero = b->ws + L.zero;
     b->zero_bytes = L.total - L.zero;
-    if (cudaMemcpy(b->d_djobs, tab.data(), tab.size() * sizeof(DecArgs), cudaMemcpyHostToDevice) !=
-            cudaSuccess ||
-        cudaMemcpy(b->d_prefix, prefix.data(), prefix.size() * 8, cudaMemcpyHostToDevice) !=
-            cudaSuccess ||
-        cudaMemcpy(b->d_tiles_of, tiles.data(), tiles.size() * 8, cudaMemcpyHostToDevice) !=
-            cudaSuccess ||
-        cudaMemcpy(b->d_bsize, b->dN.data(), b->dN.size() * 4, cudaMemcpyHostToDevice) !=
-            cudaSuccess)
+    if (!upload(b, b->d_djobs, tab.data(), tab.size() * sizeof(DecArgs)) ||
+        !upload(b, b->d_prefix, prefix.data(), prefix.size() * 8) ||
+        !upload(b, b->d_tiles_of, tiles.data(), tiles.size() * 8) ||
+        !upload(b, b->d_bsize, b->dN.data(), b->dN.size() * 4))
         return APAX_ERR_CUDA;
     b->cfg = c;
     if (b->cfg.ctas_per_sm == 0) {
@@ -379,10 +389,8 @@ int apply_profile_config(apax_batch *b, const apax_batch_config &c)
     b->d_prefix = (uint64_t *)(b->ws + L.prefix);
     b->d_zero = b->ws + L.zero;
     b->zero_bytes = L.sums - L.zero;
-    if (cudaMemcpy(b->d_pjobs, tab.data(), tab.size() * sizeof(ProfArgs), cudaMemcpyHostToDevice) !=
-            cudaSuccess ||
-        cudaMemcpy(b->d_prefix, prefix.data(), prefix.size() * 8, cudaMemcpyHostToDevice) !=
-            cudaSuccess)
+    if (!upload(b, b->d_pjobs, tab.data(), tab.size() * sizeof(ProfArgs)) ||
+        !upload(b, b->d_prefix, prefix.data(), prefix.size() * 8))
         return APAX_ERR_CUDA;
     b->cfg = c;
     if (b->cfg.ctas_per_sm == 0) {
@@ -420,6 +428,77 @@ std::string make_key(const apax_batch *b)
 
 }  // namespace
 
+namespace apax {
+namespace host {
+
+int batch_create(int op, const void *jobs, int count, void *workspace, uint64_t workspace_bytes,
+                 uint8_t *pinned, uint64_t pinned_bytes, cudaStream_t stream, bool use_tuned,
+                 apax_batch **plan)
+{
+    if (!plan) return APAX_ERR_INVALID_ARG;
+    *plan = nullptr;
+    apax_batch *b = new apax_batch();
+    b->op = op;
+    b->count = count;
+    b->pkt_words = b->ebuf_words = 0;
+    b->need32 = false;
+    b->pinned = pinned;
+    b->pinned_bytes = pinned_bytes;
+    b->pinned_used = 0;
+    b->up_stream = stream;
+    int st;
+    uint64_t need = 0;
+    if (op == 0) {
+        st = validate_encode_jobs((const apax_encode_job *)jobs, count, b->jobs, b->gp8, b->gp32,
+                                  b->pkt_words, b->ebuf_words, b->need32);
+        if (!st) need = layout_of(count, b->jobs, min_tile_blocks(b)).total;
+    } else if (op == 1) {
+        st = validate_decode_jobs((const apax_decode_job *)jobs, count, b->djobs, b->dN, b->need32);
+        if (!st) need = dlayout_of(count).total;
+    } else {
+        st = validate_profile_jobs((const apax_profile_job *)jobs, count, b->pjobs, b->max_ncand);
+        if (!st) need = playout_of(b->pjobs).total;
+    }
+    if (!st && (!workspace || ((uintptr_t)workspace % kAlign))) st = APAX_ERR_INVALID_ARG;
+    if (!st && workspace_bytes < need) st = APAX_ERR_CAPACITY;
+    if (!st && (cudaGetDevice(&b->dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->dev) !=
+                    cudaSuccess))
+        st = APAX_ERR_CUDA;
+    if (st) {
+        delete b;
+        return st;
+    }
+    b->ws = (uint8_t *)workspace;
+    b->ws_bytes = workspace_bytes;
+    b->key = make_key(b);
+    apax_batch_config c = default_config(b);
+    if (use_tuned) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(b->key);
+        if (it != g_tune_cache.end()) c = it->second;
+    }
+    st = apply_config(b, c);
+    if (st) {
+        delete b;
+        return st;
+    }
+    *plan = b;
+    return APAX_OK;
+}
+
+uint64_t batch_workspace_bytes(int op, const void *jobs, int count)
+{
+    uint64_t v = 0;
+    int st = op == 0 ? apax_batch_encode_workspace_size((const apax_encode_job *)jobs, count, &v)
+           : op == 1 ? apax_batch_decode_workspace_size((const apax_decode_job *)jobs, count, &v)
+                     : apax_batch_profile_workspace_size((const apax_profile_job *)jobs, count, &v);
+    return st ? 0 : v;
+}
+
+}  // namespace host
+}  // namespace apax
+
 extern "C" {
 
 int apax_batch_encode_workspace_size(const apax_encode_job *jobs, int count, uint64_t *bytes)
@@ -438,47 +517,8 @@ int apax_batch_encode_workspace_size(const apax_encode_job *jobs, int count, uin
 int apax_batch_encode_create(const apax_encode_job *jobs, int count, void *workspace,
                              uint64_t workspace_bytes, apax_batch **plan)
 {
-    if (!plan) return APAX_ERR_INVALID_ARG;
-    *plan = nullptr;
-    apax_batch *b = new apax_batch();
-    b->op = 0;
-    b->count = count;
-    int st = validate_encode_jobs(jobs, count, b->jobs, b->gp8, b->gp32, b->pkt_words,
-                                  b->ebuf_words, b->need32);
-    if (st) {
-        delete b;
-        return st;
-    }
-    const Layout L = layout_of(count, b->jobs, min_tile_blocks(b));
-    if (!workspace || ((uintptr_t)workspace % kAlign)) {
-        delete b;
-        return APAX_ERR_INVALID_ARG;
-    }
-    if (workspace_bytes < L.total) {
-        delete b;
-        return APAX_ERR_CAPACITY;
-    }
-    b->ws = (uint8_t *)workspace;
-    b->ws_bytes = workspace_bytes;
-    if (cudaGetDevice(&b->dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->dev) != cudaSuccess) {
-        delete b;
-        return APAX_ERR_CUDA;
-    }
-    b->key = make_key(b);
-    apax_batch_config c = default_config(b);
-    {
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = g_tune_cache.find(b->key);
-        if (it != g_tune_cache.end()) c = it->second;
-    }
-    st = apply_config(b, c);
-    if (st) {
-        delete b;
-        return st;
-    }
-    *plan = b;
-    return APAX_OK;
+    return apax::host::batch_create(0, jobs, count, workspace, workspace_bytes, nullptr, 0, nullptr,
+                                    true, plan);
 }
 
 int apax_batch_decode_workspace_size(const apax_decode_job *jobs, int count, uint64_t *bytes)
@@ -496,39 +536,8 @@ int apax_batch_decode_workspace_size(const apax_decode_job *jobs, int count, uin
 int apax_batch_decode_create(const apax_decode_job *jobs, int count, void *workspace,
                              uint64_t workspace_bytes, apax_batch **plan)
 {
-    if (!plan) return APAX_ERR_INVALID_ARG;
-    *plan = nullptr;
-    apax_batch *b = new apax_batch();
-    b->op = 1;
-    b->count = count;
-    b->pkt_words = b->ebuf_words = 0;
-    int st = validate_decode_jobs(jobs, count, b->djobs, b->dN, b->need32);
-    if (!st && (!workspace || ((uintptr_t)workspace % kAlign))) st = APAX_ERR_INVALID_ARG;
-    if (!st && workspace_bytes < dlayout_of(count).total) st = APAX_ERR_CAPACITY;
-    if (!st && (cudaGetDevice(&b->dev) != cudaSuccess ||
-                cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->dev) !=
-                    cudaSuccess))
-        st = APAX_ERR_CUDA;
-    if (st) {
-        delete b;
-        return st;
-    }
-    b->ws = (uint8_t *)workspace;
-    b->ws_bytes = workspace_bytes;
-    b->key = make_key(b);
-    apax_batch_config c = default_config(b);
-    {
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = g_tune_cache.find(b->key);
-        if (it != g_tune_cache.end()) c = it->second;
-    }
-    st = apply_config(b, c);
-    if (st) {
-        delete b;
-        return st;
-    }
-    *plan = b;
-    return APAX_OK;
+    return apax::host::batch_create(1, jobs, count, workspace, workspace_bytes, nullptr, 0, nullptr,
+                                    true, plan);
 }
 
 int apax_batch_profile_workspace_size(const apax_profile_job *jobs, int count, uint64_t *bytes)
@@ -545,42 +554,8 @@ int apax_batch_profile_workspace_size(const apax_profile_job *jobs, int count, u
 int apax_batch_profile_create(const apax_profile_job *jobs, int count, void *workspace,
                               uint64_t workspace_bytes, apax_batch **plan)
 {
-    if (!plan) return APAX_ERR_INVALID_ARG;
-    *plan = nullptr;
-    apax_batch *b = new apax_batch();
-    b->op = 2;
-    b->count = count;
-    b->pkt_words = b->ebuf_words = 0;
-    b->need32 = false;
-    int st = validate_profile_jobs(jobs, count, b->pjobs, b->max_ncand);
-    if (!st && (!workspace || ((uintptr_t)workspace % kAlign))) st = APAX_ERR_INVALID_ARG;
-    if (!st && workspace_bytes < playout_of(b->pjobs).total) st = APAX_ERR_CAPACITY;
-    if (!st && (cudaGetDevice(&b->dev) != cudaSuccess ||
-                cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->dev) !=
-                    cudaSuccess))
-        st = APAX_ERR_CUDA;
-    if (st) {
-        delete b;
-        return st;
-    }
-    b->ws = (uint8_t *)workspace;
-    b->ws_bytes = workspace_bytes;
-    b->key = make_key(b);
-    apax_batch_config c;
-    c.threads = 128;
-    c.ctas_per_sm = 0;
-    {
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = g_tune_cache.find(b->key);
-        if (it != g_tune_cache.end()) c = it->second;
-    }
-    st = apply_config(b, c);
-    if (st) {
-        delete b;
-        return st;
-    }
-    *plan = b;
-    return APAX_OK;
+    return apax::host::batch_create(2, jobs, count, workspace, workspace_bytes, nullptr, 0, nullptr,
+                                    true, plan);
 }
 
 int apax_batch_run(apax_batch *b, void *stream)

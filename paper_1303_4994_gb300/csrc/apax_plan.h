@@ -143,6 +143,15 @@ int fill_prof_args(const void *x, int dtype, uint64_t n, uint32_t block_size,
                    const uint16_t *candidates, int ncand, double target,
                    apax_profile_point *points, apax_profile_summary *summary, ProfArgs &a);
 
+// Batch plans (apax_batch.cu).  op: 0 encode, 1 decode, 2 profile; jobs
+// points at apax_encode_job / apax_decode_job / apax_profile_job.  With
+// `pinned` the plan's tables are copied from that pinned host staging on
+// `stream` (asynchronously) instead of with a synchronous copy.
+int batch_create(int op, const void *jobs, int count, void *workspace, uint64_t workspace_bytes,
+                 uint8_t *pinned, uint64_t pinned_bytes, cudaStream_t stream, bool use_tuned,
+                 apax_batch **plan);
+uint64_t batch_workspace_bytes(int op, const void *jobs, int count);  // 0 on error
+
 inline int cuda_fail(cudaError_t e) { return e == cudaSuccess ? APAX_OK : APAX_ERR_CUDA; }
 
 
