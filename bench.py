@@ -8,9 +8,20 @@ float32 4096x4096 k^-3 random field.  `value` is GB/s of uncompressed data
 through the step; encode, decode and profile are also timed on their own.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--workload field|batched|serving]
 
 With N > 1 (torchrun), every rank codes its own array (weak scaling, no
 data-path collective); rank 0 prints max-over-ranks timing.
+
+Other workloads (one GPU):
+  batched  8,192 arrays (4 KB..64 MB, int16/int32/float32/float64, fixed
+           rates 2:1..6:1, 56.6 GB): one persistent launch each for encode,
+           decode and the profiler sweep, against the plain per-array loop.
+  serving  Poisson arrivals (2,000 requests/s, 50/50 encode/decode, 64 KB..
+           256 MB of float32 field slices at a fixed quality or int16 traces
+           at 4:1) through the request server with a 64 GB admission cap:
+           open-loop p50/p99 latency, then a closed-loop replay of the same
+           trace against the plain per-request path.
 """
 from __future__ import annotations
 
@@ -306,6 +317,250 @@ def run_reference(args, rank, world):
                     "d2h_bytes_per_step": 0}}
 
 
+def _tree_levels(n):
+    c, lv = (n // N_BLOCK + 15) // 16, 0
+    while c > 1:
+        c, lv = (c + 15) // 16, lv + 1
+    return lv
+
+
+def _wrapped(master, off, n):
+    import torch
+    M = master.numel()
+    pos, parts, need = off % M, [], n
+    while need > 0:
+        take = min(need, M - pos)
+        parts.append(master[pos:pos + take])
+        need -= take
+        pos = 0
+    return torch.cat(parts) if len(parts) > 1 else parts[0].clone()
+
+
+def run_batched(args):
+    import torch
+
+    from paper_1303_4994_gb300 import apax as A
+    from paper_1303_4994_gb300 import build as B
+    from paper_1303_4994_gb300 import synth
+
+    B.build()
+    A.lib()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    specs = synth.batch_specs(args.arrays)
+    masters = {k: torch.from_numpy(v).to(dev) for k, v in synth.batch_masters().items()}
+    xs = [_wrapped(masters[dt], off, n) for dt, n, _, off in specs]
+    ps = [A.params(N_BLOCK, A.FIXED_RATE, rate, 0) for _, _, rate, _ in specs]
+    total = sum(x.numel() * x.element_size() for x in xs)
+    caps = [A.encoded_size(A.TORCH_CODE[x.dtype], x.numel(), p) for x, p in zip(xs, ps)]
+    outs = [torch.empty(c, dtype=torch.uint8, device=dev) for c in caps]
+    outs_plain = [torch.empty(c, dtype=torch.uint8, device=dev) for c in caps]
+    ys = [torch.empty_like(x) for x in xs]
+    k = len(xs)
+    res = torch.zeros(16 * k, dtype=torch.uint8, device=dev)
+    dres = torch.zeros(16 * k, dtype=torch.uint8, device=dev)
+    ejobs = A.encode_jobs(xs, ps, outs, res)
+    djobs = A.decode_jobs(outs, ys, [N_BLOCK] * k, dres)
+    eplan = A.Batch(ejobs, A.aligned_workspace(A.batch_encode_workspace_size(ejobs)))
+    dplan = A.Batch(djobs, A.aligned_workspace(A.batch_decode_workspace_size(djobs)))
+    # profiler sweep of every array (16 codes) in one launch
+    nc = 16
+    pts = [torch.zeros(A.POINT_BYTES * nc, dtype=torch.uint8, device=dev) for _ in xs]
+    sums = [torch.zeros(A.SUMMARY_BYTES, dtype=torch.uint8, device=dev) for _ in xs]
+    pjobs = A.profile_jobs(xs, [N_BLOCK] * k, [list(A.DEFAULT_CANDIDATES)] * k, [TARGET] * k,
+                           pts, sums)
+    pplan = A.Batch(pjobs, A.aligned_workspace(A.batch_profile_workspace_size(pjobs)))
+    for plan in (eplan, dplan, pplan):
+        plan.tune(reps=1, stream=stream)
+    wsz = max(A.workspace_size(A.TORCH_CODE[x.dtype], x.numel(), p) for x, p in zip(xs, ps))
+    ws = torch.empty(wsz, dtype=torch.uint8, device=dev)
+    dws = torch.empty(A.decode_workspace_size(), dtype=torch.uint8, device=dev)
+    pws = torch.empty(max(A.profile_workspace_size(A.TORCH_CODE[x.dtype], x.numel(), N_BLOCK, nc)
+                          for x in xs), dtype=torch.uint8, device=dev)
+    r1 = A.new_result(dev)
+
+    def plain_enc():
+        for x, p, o in zip(xs, ps, outs_plain):
+            A.encode_into(x, p, o, ws, r1, stream)
+
+    def plain_dec():
+        for o, y in zip(outs_plain, ys):
+            A.decode_into(o, y, dws, r1, stream)
+
+    def plain_prof():
+        for x, pt, sm in zip(xs, pts, sums):
+            A.profile_into(x, N_BLOCK, list(A.DEFAULT_CANDIDATES), TARGET, pws, pt, sm, stream)
+
+    def timed(fn, reps):
+        ts = []
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.mean(ts))
+
+    runs = {"batched_encode": lambda: eplan.run(stream), "plain_encode": plain_enc,
+            "batched_decode": lambda: dplan.run(stream), "plain_decode": plain_dec,
+            "batched_profile": lambda: pplan.run(stream), "plain_profile": plain_prof}
+    for fn in runs.values():
+        for _ in range(max(args.warmup, 3)):
+            fn()
+    torch.cuda.synchronize()
+    with Clocks(0) as clk:
+        ms = {name: timed(fn, args.steps) for name, fn in runs.items()}
+    # the batched containers are the plain loop's, byte for byte
+    eplan.run(stream)
+    plain_enc()
+    torch.cuda.synchronize()
+    same = all(torch.equal(a, b) for a, b in zip(outs, outs_plain))
+    st = A.read_results(res, k)
+    assert all(r.status == 0 for r in st)
+    comp = sum(r.bytes for r in st)
+    gbs = {name: total / t / 1e6 for name, t in ms.items()}
+    peak, peak_kind = _peaks()
+    step_ms = ms["batched_encode"] + ms["batched_decode"]
+    return {
+        "metric": METRIC, "value": round(total / step_ms / 1e6, 3), "unit": "GB/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(step_ms, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "mixed",
+        "data": "synthetic",
+        "config": {"workload": f"batched: {k} arrays 4 KB..64 MB, int16/int32/float32/float64, "
+                               "fixed rate 2:1/3:1/4:1/6:1, N=256 (seed 3)",
+                   "bytes": total, "l2": "inputs larger than L2"},
+        "ratio": round(total / comp, 4),
+        "gbs": {n: round(v, 2) for n, v in gbs.items()},
+        "ms": {n: round(v, 3) for n, v in ms.items()},
+        "batched_vs_plain": {op: round(ms["plain_" + op] / ms["batched_" + op], 3)
+                             for op in ("encode", "decode", "profile")},
+        "containers_identical_to_plain": bool(same),
+        "configs_tuned": {"encode": eplan.config, "decode": dplan.config, "profile": pplan.config},
+        "roofline": {"bound": "hbm", "kernel": "batched decode",
+                     "achieved": (total + comp) / ms["batched_decode"] / 1e6, "peak": peak,
+                     "unit": "GB/s",
+                     "frac": (total + comp) / ms["batched_decode"] / 1e6 / peak,
+                     "traffic": None, "peak_source": f"{peak_kind} hbm_gbs"},
+        "gpu_launches": args.steps * (3 + k + 2 * k + sum(2 + _tree_levels(x.numel()) for x in xs)),
+        "clocks": clk.summary(),
+    }
+
+
+def run_serving(args):
+    import torch
+
+    from paper_1303_4994_gb300 import apax as A
+    from paper_1303_4994_gb300 import build as B
+    from paper_1303_4994_gb300 import synth
+
+    B.build()
+    A.lib()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    trace = synth.serving_trace(args.serve_seconds)
+    # device-resident payload pools (float32 field, int16 trace), 4 GB each
+    field = torch.from_numpy(synth.grf2d(4096, 4096, seed=1).reshape(-1)).to(dev)
+    pool = {"float32": field.repeat(16),
+            "int16": torch.from_numpy(synth.sensor_trace(1 << 25, seed=0)).to(dev).repeat(64)}
+    # the profiler's choice for the field (fixed quality at r >= 0.9999)
+    pts, summ = A.profile(field, N_BLOCK, A.DEFAULT_CANDIDATES, TARGET)
+    code = int(summ.recommended_code)
+    params = {"float32": A.params(N_BLOCK, A.FIXED_QUALITY, (1, 1), code),
+              "int16": A.params(N_BLOCK, A.FIXED_RATE, (4, 1), 0)}
+    # decode requests use pre-encoded containers at 64 log-spaced sizes
+    sizes = np.unique(np.exp(np.linspace(np.log(64 << 10), np.log(256 << 20), 64)).astype(np.int64))
+    pre = {}
+    for dt in ("float32", "int16"):
+        es = 4 if dt == "float32" else 2
+        for nb in sizes:
+            n = int(nb) // es
+            pre[(dt, int(nb))] = (A.encode(pool[dt][:n], N_BLOCK, params[dt].mode,
+                                           (params[dt].rate_num, params[dt].rate_den),
+                                           params[dt].atten_code), n)
+    reqs = []
+    for t, op, dt, nb, off in trace:
+        es = 4 if dt == "float32" else 2
+        if op == "encode":
+            n = nb // es
+            o = off % (pool[dt].numel() - n)
+            reqs.append((t, op, dt, pool[dt][o:o + n], n, nb))
+        else:
+            j = int(np.clip(np.searchsorted(sizes, nb), 0, len(sizes) - 1))
+            c, n = pre[(dt, int(sizes[j]))]
+            reqs.append((t, op, dt, c, n, n * es))
+    arena = A.aligned_workspace(64 << 30)
+    torch.cuda.synchronize()
+
+    def serve(open_loop, depth):
+        srv = A.Server(arena, slots=4, max_batch=256)
+        lat, done_bytes, first, last = [], 0, None, 0.0
+        i, outstanding = 0, 0
+        t0 = time.perf_counter()
+        while i < len(reqs) or outstanding:
+            now = time.perf_counter() - t0
+            while i < len(reqs) and (reqs[i][0] <= now if open_loop else outstanding < depth):
+                t, op, dt, buf, n, nb = reqs[i]
+                if op == "encode":
+                    srv.submit_encode(i, buf, params[dt])
+                else:
+                    srv.submit_decode(i, buf, getattr(torch, dt), n, N_BLOCK)
+                i += 1
+                outstanding += 1
+            for c in srv.poll():
+                assert c.status == 0, c.status
+                outstanding -= 1
+                lat.append(c.t_done - c.t_submit)
+                done_bytes += reqs[c.id][5]
+                first = c.t_submit if first is None else min(first, c.t_submit)
+                last = max(last, c.t_done)
+                srv.release(c.out)
+        st = srv.stats()
+        srv.close()
+        return lat, done_bytes / (last - first) / 1e9, st
+
+    lat, gbs_open, st_open = serve(True, 0)
+    lat_c, gbs_closed, st_closed = serve(False, 1024)
+    # the plain per-request path: one call per request, one stream
+    ws = torch.empty(max(A.workspace_size(A.TORCH_CODE[getattr(torch, dt)], r[4], params[dt])
+                         for r in reqs for dt in [r[2]]), dtype=torch.uint8, device=dev)
+    dws = torch.empty(A.decode_workspace_size(), dtype=torch.uint8, device=dev)
+    r1 = A.new_result(dev)
+    out_e = torch.empty(max(A.encoded_size(A.TORCH_CODE[getattr(torch, r[2])], r[4], params[r[2]])
+                            for r in reqs), dtype=torch.uint8, device=dev)
+    out_d = torch.empty(max(r[5] for r in reqs), dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for t, op, dt, buf, n, nb in reqs:
+        if op == "encode":
+            A.encode_into(buf, params[dt], out_e, ws, r1, stream)
+        else:
+            A.decode_into(buf, out_d[:nb].view(getattr(torch, dt)), dws, r1, stream)
+    torch.cuda.synchronize()
+    plain_gbs = sum(r[5] for r in reqs) / (time.perf_counter() - t0) / 1e9
+    total = sum(r[5] for r in reqs)
+    return {
+        "metric": METRIC, "value": round(gbs_closed, 3), "unit": "GB/s", "n_gpus": 1,
+        "steps": 1, "warmup": 0, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "mixed", "data": "synthetic",
+        "config": {"workload": f"serving: Poisson 2000 req/s for {args.serve_seconds} s, 50/50 "
+                               "encode/decode, 64 KB..256 MB float32 (fixed quality, code "
+                               f"{code}) / int16 (4:1), 64 GB admission cap (seed 4)",
+                   "requests": len(reqs), "bytes": total, "slots": 4, "max_batch": 256},
+        "open_loop": {"gbs": round(gbs_open, 3), "offered_gbs": round(total / args.serve_seconds / 1e9, 3),
+                      "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
+                      "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3),
+                      "steps": st_open["steps"], "arena_peak_gb": round(st_open["arena_peak"] / 1e9, 3)},
+        "closed_loop": {"gbs": round(gbs_closed, 3),
+                        "p50_ms": round(float(np.percentile(lat_c, 50)) * 1e3, 3),
+                        "p99_ms": round(float(np.percentile(lat_c, 99)) * 1e3, 3),
+                        "steps": st_closed["steps"]},
+        "plain_per_request_gbs": round(plain_gbs, 3),
+        "served_vs_plain": round(gbs_closed / plain_gbs, 3),
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -313,7 +568,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="field", choices=["field", "batched", "serving"])
+    ap.add_argument("--arrays", type=int, default=8192)
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
     args = ap.parse_args()
+    if args.workload != "field" and args.impl == "ours":
+        import torch
+        torch.cuda.set_device(0)
+        line = run_batched(args) if args.workload == "batched" else run_serving(args)
+        print(json.dumps(line))
+        return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))

@@ -82,3 +82,61 @@ IMAGE_F32 = dict(name="float32 4096x4096 k^-3 field, profile 16 codes at r>=0.99
                  shape=(4096, 4096), block_size=256, target=0.9999)
 FIELD_F64 = dict(name="float64 512^3 k^-4 field with 4 blobs, profile at r>=0.99999, fixed quality",
                  n=512, block_size=256, target=0.99999)
+
+
+# ---------------------------------------------------------------- many arrays
+# Batched workload: `count` arrays with lengths log-uniform over 4 KB..64 MB
+# in bytes (rounded down to the element size), element types uniform over
+# int16 / int32 / float32 / float64, fixed rates uniform over 2:1, 3:1, 4:1,
+# 6:1.  Contents are wrapped slices, at seeded offsets, of one master signal
+# per type (the sensor trace for the integers -- int32 with amplitudes
+# summing to 2^27 and noise 8 * 2^16 -- the k^-3 field for float32 and the
+# k^-4 field for float64), so the whole batch can be built on the device
+# from four masters.
+BATCH_DTYPES = ("int16", "int32", "float32", "float64")
+BATCH_RATES = ((2, 1), (3, 1), (4, 1), (6, 1))
+
+
+def batch_specs(count: int = 8192, seed: int = 3, lo_bytes: int = 4096,
+                hi_bytes: int = 64 << 20):
+    """[(dtype name, elements, (num, den), master offset)] of the batch."""
+    rng = np.random.default_rng(seed)
+    nbytes = np.exp(rng.uniform(np.log(lo_bytes), np.log(hi_bytes), count))
+    kinds = rng.integers(0, 4, count)
+    rates = rng.integers(0, 4, count)
+    offs = rng.integers(0, 1 << 40, count)
+    size = {"int16": 2, "int32": 4, "float32": 4, "float64": 8}
+    out = []
+    for b, k, r, o in zip(nbytes, kinds, rates, offs):
+        dt = BATCH_DTYPES[int(k)]
+        out.append((dt, int(b) // size[dt], BATCH_RATES[int(r)], int(o)))
+    return out
+
+
+def batch_masters(n16: int = 1 << 25, field3d_n: int = 256):
+    """Master signals of the batched and serving workloads."""
+    return {
+        "int16": sensor_trace(n16, seed=3),
+        "int32": sensor_trace(n16 // 2, seed=4, amp_sum=2.0 ** 27, sigma=8.0 * 2 ** 16,
+                              dtype=np.int32),
+        "float32": grf2d(4096, 4096, seed=1).reshape(-1),
+        "float64": field3d(field3d_n, seed=2).reshape(-1),
+    }
+
+
+# ---------------------------------------------------------------- request trace
+def serving_trace(seconds: float = 60.0, rate: float = 2000.0, seed: int = 4,
+                  lo_bytes: int = 64 << 10, hi_bytes: int = 256 << 20):
+    """Poisson arrivals: [(t, op 'encode'|'decode', 'float32'|'int16', bytes,
+    pool offset)] with payload sizes log-uniform over lo..hi bytes."""
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= seconds:
+            break
+        op = "encode" if rng.random() < 0.5 else "decode"
+        dt = "float32" if rng.random() < 0.5 else "int16"
+        nb = int(np.exp(rng.uniform(np.log(lo_bytes), np.log(hi_bytes))))
+        out.append((t, op, dt, nb, int(rng.integers(0, 1 << 40))))
+    return out
