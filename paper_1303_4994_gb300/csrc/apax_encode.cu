@@ -148,7 +148,7 @@ __device__ __forceinline__ void encode_tile(const EncArgs &a, uint64_t tile, uin
         TBlock<DT> pv;
         open_team_block<DT, TS>(pv, x, a.n, a.N, a.nb, j == 0 ? 0 : j - 1, gp);
         uint32_t bb[3];
-        team_eval<DT, TS>(pv, 0, 7u, bb);
+        team_eval3<DT, TS>(pv, 0, bb);
         s = 0;
         if (bb[1] < bb[s]) s = 1;
         if (bb[2] < bb[s]) s = 2;
@@ -159,9 +159,7 @@ __device__ __forceinline__ void encode_tile(const EncArgs &a, uint64_t tile, uin
     uint32_t plen = 0;
     if (MODE == 0) {
         const uint32_t budget = b.L == (int)a.N ? a.B : fr_budget<DT>(b.L, a.rate_num, a.rate_den);
-        uint32_t bits[3];
-        team_eval<DT, TS>(b, 0, 1u << s, bits);
-        const bool fits0 = pad32_bytes(bits[s]) <= budget;
+        const bool fits0 = pad32_bytes(team_eval1<DT, TS>(b, 0, s)) <= budget;
         int lo = 0, hi = 4095;
         // Teams of one warp share shuffles, so every team runs the same 12
         // halvings unless all of them already fit at code 0.
@@ -169,9 +167,9 @@ __device__ __forceinline__ void encode_tile(const EncArgs &a, uint64_t tile, uin
 #pragma unroll 1
             for (int it = 0; it < 12; ++it) {  // at most 12 halvings close [0, 4095]
                 const int mid = (lo + hi) >> 1;
-                team_eval<DT, TS>(b, mid, 1u << s, bits);
+                const uint32_t bm = team_eval1<DT, TS>(b, mid, s);
                 if (hi - lo > 1) {
-                    if (pad32_bytes(bits[s]) <= budget) hi = mid;
+                    if (pad32_bytes(bm) <= budget) hi = mid;
                     else lo = mid;
                 }
             }
@@ -184,16 +182,15 @@ __device__ __forceinline__ void encode_tile(const EncArgs &a, uint64_t tile, uin
     const Quant<DT> Q(code, b.Eb);
     TokCount tc;
     tc.init();
+    const Carry cin = carry_in<DT>(b, Q, 4 * b.g0);
     {
-        int32_t qp, s1p;
-        seg_carry<DT>(b, Q, 4 * b.g0, qp, s1p);
+        Stream1 st(s, cin);
 #pragma unroll 1
         for (int g = b.g0; g < b.g1; ++g) {
             lt xv[4];
-            load4<DT>(b, 4 * g, xv);
-            int32_t q[4], v0[4], v1[4], v2[4];
-            group_streams<DT>(b, Q, g, xv, qp, s1p, q, v0, v1, v2);
-            const int e = exp_from_or(s == 0 ? or4(v0) : (s == 1 ? or4(v1) : or4(v2)));
+            load4<DT, true>(b, 4 * g, xv);
+            int32_t u[4];
+            const int e = exp_from_or(group1<DT>(Q, xv, st, u));
             ebuf[g] = (uint8_t)e;
             tc.push(e, true);
         }
@@ -248,22 +245,18 @@ __device__ __forceinline__ void encode_tile(const EncArgs &a, uint64_t tile, uin
         // mantissas of my groups after the token section
         NibWriter mw;
         mw.start(pkt, (uint32_t)H + 4u * (uint32_t)nib_total + 4u * (uint32_t)sume_before);
-        int32_t qp, s1p;
-        seg_carry<DT>(b, Q, 4 * b.g0, qp, s1p);
+        Stream1 sm(s, cin);
 #pragma unroll 1
         for (int g = b.g0; g < b.g1; ++g) {
             lt xv[4];
-            load4<DT>(b, 4 * g, xv);
-            int32_t q[4], v0[4], v1[4], v2[4];
-            group_streams<DT>(b, Q, g, xv, qp, s1p, q, v0, v1, v2);
+            load4<DT, true>(b, 4 * g, xv);
+            int32_t u[4];
+            group1<DT>(Q, xv, sm, u);
             const int e = ebuf[g];
             if (e) {
                 const uint32_t m = e >= 32 ? 0xffffffffu : ((1u << e) - 1u);
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const uint32_t u = (uint32_t)(s == 0 ? v0[i] : (s == 1 ? v1[i] : v2[i]));
-                    mw.put(u & m, e);
-                }
+                for (int i = 0; i < 4; ++i) mw.put((uint32_t)u[i] & m, e);
             }
         }
         mw.flush();

@@ -198,7 +198,7 @@ __device__ __forceinline__ void profile_run(const ProfArgs &a, uint64_t run, uin
         TBlock<DT> pv;
         open_team_block<DT, TS>(pv, x, a.n, a.N, a.nb, j == 0 ? 0 : j - 1, gp);
         uint32_t bb[3];
-        team_eval<DT, TS>(pv, 0, 7u, bb);
+        team_eval3<DT, TS>(pv, 0, bb);
         s = 0;
         if (bb[1] < bb[s]) s = 1;
         if (bb[2] < bb[s]) s = 2;
@@ -353,16 +353,14 @@ __device__ __forceinline__ void profile_run(const ProfArgs &a, uint64_t run, uin
         tc.init();
         int64_t sq = 0, sA = 0, sB = 0, sD = 0;  // 64-bit partials (f32, i8, i16)
         i128 wq = 0, wA = 0, wB = 0, wD = 0;     // 128-bit partials (f64, i32)
-        int32_t qp, s1p;
-        seg_carry<DT>(b, Q, 4 * b.g0, qp, s1p);
+        Stream1 sm(s, carry_in<DT>(b, Q, 4 * b.g0));
         const int cD = -103 - b.Eb - k;  // f32: D' shift = bexp + cD
 #pragma unroll 1
         for (int g = b.g0; g < ge; ++g) {
             lt xv[4];
-            load4<DT>(b, 4 * g, xv);
-            int32_t qq[4], v0[4], v1[4], v2[4];
-            group_streams<DT>(b, Q, g, xv, qp, s1p, qq, v0, v1, v2);
-            tc.push(exp_from_or(s == 0 ? or4(v0) : (s == 1 ? or4(v1) : or4(v2))), true);
+            load4<DT, true>(b, 4 * g, xv);
+            int32_t qq[4], uu[4];
+            tc.push(exp_from_or(group1q<DT>(Q, xv, sm, qq, uu)), true);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 if (4 * g + i >= b.L) continue;

@@ -73,9 +73,11 @@ struct TBlock {
     bool active;   // the block exists
 };
 
-// Load the 4 samples of the group starting at sample s (zeros past L):
-// one vector load when the group is whole and aligned.
-template <int DT>
+// Load the 4 samples of the group starting at sample s: one vector load
+// when the group is whole and aligned.  Past L the group is padded with
+// zeros, or (PAD) with x[L-1], whose quantised value is the last-group
+// padding of Sec. 6 packets (the replicated q[L-1]).
+template <int DT, bool PAD = false>
 __device__ __forceinline__ void load4(const TBlock<DT> &b, int s, typename LaneT<DT>::t (&x)[4])
 {
     using raw = typename DT_<DT>::raw;
@@ -102,11 +104,13 @@ __device__ __forceinline__ void load4(const TBlock<DT> &b, int s, typename LaneT
     } else {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            if (b.active && s + j < b.L) {
+            int i = s + j;
+            if (PAD && i >= b.L) i = b.L - 1;
+            if (b.active && i >= 0 && i < b.L) {
                 if constexpr (DT_<DT>::F)
-                    x[j] = __ldg(reinterpret_cast<const typename DT_<DT>::bits *>(q + j));
+                    x[j] = __ldg(reinterpret_cast<const typename DT_<DT>::bits *>(b.p + i));
                 else
-                    x[j] = (lt)__ldg(q + j);
+                    x[j] = (lt)__ldg(b.p + i);
             } else {
                 x[j] = 0;
             }
@@ -126,27 +130,42 @@ __device__ __forceinline__ typename LaneT<DT>::t load1(const TBlock<DT> &b, int 
 }
 
 // ---------------------------------------------------------------- quantiser
-// Per (block, code) quantiser.  Floats with a power-of-two code (m = 0) use
-// one fused multiply-add: x 2^(Q-Eb-k) is exact, adding 1.5 2^23 (k >= 1, so
-// |value| < 2^22) rounds it to the nearest integer with ties to even in the
+// Per (block, code) quantiser (Sec. 6 attenuator, one rounding of the exact
+// product).  Floats with a power-of-two code (m = 0): x 2^(Q-Eb-k) is exact
+// (a power-of-two scale, |value| <= 2^23), so for k >= 1 (|value| < 2^22)
+// adding 1.5 2^23 rounds it to the nearest integer with ties to even in the
 // binade [2^23, 2^24), whose bit patterns then differ from that of 1.5 2^23
-// by exactly the integer.  For k = 0 the addend carries the value's sign
-// (|value| < 2^23).  Everything else uses exact integer significand
-// arithmetic (Sec. 6 attenuator, one rounding of the exact product).
+// by exactly the integer; for k = 0 a round-to-nearest-even conversion of
+// the exact product does it (a product below the normal range rounds to
+// +-0, as the exact value, below 2^-126, does).  int8/int16: the product
+// x (256 - m) and the rounding shift by 8 + k in 32 bits.  Everything else
+// takes exact integer significand arithmetic.
 template <int DT>
 struct Quant {
     Code c;
     int Eb;
-    int mode;     // 0 integer, 1 fused (k >= 1), 2 fused signed (k == 0)
+    int mode;     // 0 exact integer path, 1 fused (k >= 1), 2 convert (k == 0), 3 small int
     float scale;  // 2^(Q - Eb - k)
+    int32_t mul, sh, bias;
     __device__ __forceinline__ Quant(int code, int eb) : c(code), Eb(eb), mode(0), scale(0.f)
     {
+        mul = 0;
+        sh = 1;
+        bias = 0;
         if constexpr (DT == 4) {
             const int se = 23 - eb - c.k;
             if (!c.zero && c.m == 0 && se >= -126 && se <= 127) {
                 mode = c.k >= 1 ? 1 : 2;
                 scale = __int_as_float((se + 127) << 23);
             }
+        }
+        if constexpr (DT == 1 || DT == 2) {
+            // |x (256 - m)| < 2^23: a shift of 25 or more rounds to 0
+            mode = 3;
+            const int s0 = 8 + c.k;
+            mul = (c.zero || s0 >= 25) ? 0 : 256 - c.m;
+            sh = s0 >= 25 ? 24 : s0;
+            bias = (1 << (sh - 1)) - 1;
         }
     }
     __device__ __forceinline__ int32_t operator()(typename LaneT<DT>::t v) const
@@ -156,12 +175,11 @@ struct Quant {
                 const float t = __fmaf_rn(__uint_as_float(v), scale, 12582912.0f);
                 return __float_as_int(t) - 0x4B400000;
             }
-            if (mode == 2) {
-                const uint32_t sg = v & 0x80000000u;
-                const float t = __fmaf_rn(__uint_as_float(v), scale, __uint_as_float(sg | 0x4B000000u));
-                const int32_t a = (__float_as_int(t) & 0x7fffffff) - 0x4B000000;
-                return sg ? -a : a;
-            }
+            if (mode == 2) return __float2int_rn(__fmul_rn(__uint_as_float(v), scale));
+        }
+        if constexpr (DT == 1 || DT == 2) {
+            const int32_t t = (int32_t)v * mul;
+            return (t + bias + ((t >> sh) & 1)) >> sh;
         }
         return quantise<DT>(v, c, Eb);
     }
@@ -258,8 +276,10 @@ __device__ __forceinline__ void team_tokens(const TokCount &c, bool block_first,
     uint32_t exc = tshfl_up<TS>(inc, 1);
     const bool s_in = t == 0 ? false : (bool)(exc & 1);
     const int mine = s_in ? nb : na;
-    nib_total = team_sum<TS>(mine);
-    sume_total = team_sum<TS>(c.sume);
+    // one team sum of both counts: nibbles < 2^14, exponent bits < 2^18
+    const uint32_t both = team_sum<TS>((uint32_t)mine | ((uint32_t)c.sume << 14));
+    nib_total = (int)(both & 0x3fffu);
+    sume_total = (int)(both >> 14);
     if (s_in_out) *s_in_out = s_in;
     if (nib_mine) *nib_mine = mine;
 }
@@ -386,6 +406,192 @@ __device__ __forceinline__ void team_eval(const TBlock<DT> &b, int code, unsigne
         team_tokens<TS>(tc[s], first, nib, sume);
         bits[s] = ((smask >> s) & 1) ? (uint32_t)DT_<DT>::H + 4u * (uint32_t)nib + 4u * (uint32_t)sume : 0u;
     }
+}
+
+// ---------------------------------------------------------------- streams (carried)
+// The derivative streams of Sec. 6 from carried predecessors, with no
+// per-sample position tests: S1 u_i = q_i - qp1, S2 u_i = q_i - 2 qp2 + qpp2
+// (mod 2^W).  At the block start qp1 = 0, qp2 = q_0 and qpp2 = 2 q_0, which
+// give u_0 = q_0 (both streams) and S2's u_1 = q_1 - q_0 through the same
+// formulas; elsewhere the carries are the two preceding q.
+struct Carry {
+    uint32_t qp1, qp2, qpp2;
+};
+
+template <int DT>
+__device__ __forceinline__ Carry carry_in(const TBlock<DT> &b, const Quant<DT> &Q, int s0)
+{
+    Carry c;
+    if (s0 == 0) {
+        const uint32_t q0 = (uint32_t)Q(load1<DT>(b, 0));
+        c.qp1 = 0;
+        c.qp2 = q0;
+        c.qpp2 = 2u * q0;
+    } else {
+        const uint32_t a = (uint32_t)Q(load1<DT>(b, s0 - 1));
+        c.qp1 = a;
+        c.qp2 = a;
+        c.qpp2 = (uint32_t)Q(load1<DT>(b, s0 - 2));
+    }
+    return c;
+}
+
+// One group, all three streams: OR of the width terms of each stream.
+template <int DT>
+__device__ __forceinline__ void group3(const Quant<DT> &Q, const typename LaneT<DT>::t (&xv)[4],
+                                       Carry &c, uint32_t &o0, uint32_t &o1, uint32_t &o2)
+{
+    constexpr int W = DT_<DT>::W;
+    o0 = o1 = o2 = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const uint32_t q = (uint32_t)Q(xv[i]);
+        const uint32_t u1 = q - c.qp1, u2 = q - 2u * c.qp2 + c.qpp2;
+        o0 |= bits_term((int32_t)q);  // q is already a W-bit value
+        o1 |= bits_term(sext_w(u1, W));
+        o2 |= bits_term(sext_w(u2, W));
+        c.qp1 = q;
+        c.qpp2 = c.qp2;
+        c.qp2 = q;
+    }
+}
+
+// One stream s: coefficients of u = q - a qp + bb qpp and its carries.
+struct Stream1 {
+    uint32_t a, bb, qp, qpp;
+    __device__ __forceinline__ Stream1(int s, const Carry &c)
+    {
+        a = s == 0 ? 0u : (s == 1 ? 1u : 2u);
+        bb = s == 2 ? 1u : 0u;
+        qp = s == 1 ? c.qp1 : c.qp2;
+        qpp = c.qpp2;
+    }
+};
+
+// One group, one stream: the quantised values, the stream values
+// (sign-extended) and their OR of width terms.
+template <int DT>
+__device__ __forceinline__ uint32_t group1q(const Quant<DT> &Q, const typename LaneT<DT>::t (&xv)[4],
+                                            Stream1 &st, int32_t (&qv)[4], int32_t (&u)[4])
+{
+    constexpr int W = DT_<DT>::W;
+    uint32_t o = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const uint32_t q = (uint32_t)Q(xv[i]);
+        qv[i] = (int32_t)q;
+        u[i] = sext_w(q - st.a * st.qp + st.bb * st.qpp, W);
+        o |= bits_term(u[i]);
+        st.qpp = st.qp;
+        st.qp = q;
+    }
+    return o;
+}
+
+template <int DT>
+__device__ __forceinline__ uint32_t group1(const Quant<DT> &Q, const typename LaneT<DT>::t (&xv)[4],
+                                           Stream1 &st, int32_t (&u)[4])
+{
+    int32_t qv[4];
+    return group1q<DT>(Q, xv, st, qv, u);
+}
+
+// Greedy JEE counters of the three streams at once (SIMD within a register:
+// one 10-bit lane per stream; exponents <= 32, counts < 1024 per thread).
+// Same transitions as TokCount::push.
+struct Tok3 {
+    static constexpr uint32_t L1 = 0x00100401u, L2 = 0x00200802u, L3 = 0x00300C03u,
+                              B9 = 0x20080200u;
+    uint32_t nib, lead, leading, st, e_first, e_last;
+    int sume0, sume1, sume2;
+    bool any;
+    __device__ __forceinline__ void init()
+    {
+        nib = lead = st = e_first = e_last = 0;
+        leading = L1;
+        sume0 = sume1 = sume2 = 0;
+        any = false;
+    }
+    __device__ __forceinline__ void push(int e0, int e1, int e2)
+    {
+        sume0 += e0;
+        sume1 += e1;
+        sume2 += e2;
+        const uint32_t E = (uint32_t)e0 | ((uint32_t)e1 << 10) | ((uint32_t)e2 << 20);
+        if (!any) {
+            any = true;
+            e_first = e_last = E;
+            return;
+        }
+        const uint32_t D = E + B9 - e_last;  // 512 + e - e_prev per lane
+        const uint32_t sm = (((D + L1) & ~(D - L2)) & B9) >> 9;  // |d| <= 1
+        const uint32_t s2 = (((D + L2) & ~(D - L3)) & B9) >> 9;  // |d| <= 2
+        nib = nib + L2 - s2 - (sm & st);
+        st = sm & ~st;
+        leading &= sm;
+        lead += leading;
+        e_last = E;
+    }
+    __device__ __forceinline__ TokCount lane(int s) const
+    {
+        TokCount t;
+        const int sh = 10 * s;
+        t.nib = (int)((nib >> sh) & 1023u);
+        t.lead = (int)((lead >> sh) & 1023u);
+        t.leading = (leading >> sh) & 1u;
+        t.st = (st >> sh) & 1u;
+        t.e_first = (int)((e_first >> sh) & 1023u);
+        t.e_last = (int)((e_last >> sh) & 1023u);
+        t.sume = s == 0 ? sume0 : (s == 1 ? sume1 : sume2);
+        t.any = any;
+        return t;
+    }
+};
+
+// Unpadded packet bits of the team's block for all three streams at `code`
+// (the stream decision of Sec. 6 evaluates them at code 0).
+template <int DT, int TS>
+__device__ __forceinline__ void team_eval3(const TBlock<DT> &b, int code, uint32_t (&bits)[3])
+{
+    const Quant<DT> Q(code, b.Eb);
+    Tok3 tk;
+    tk.init();
+    Carry c = carry_in<DT>(b, Q, 4 * b.g0);
+#pragma unroll 1
+    for (int g = b.g0; g < b.g1; ++g) {
+        typename LaneT<DT>::t xv[4];
+        load4<DT, true>(b, 4 * g, xv);
+        uint32_t o0, o1, o2;
+        group3<DT>(Q, xv, c, o0, o1, o2);
+        tk.push(exp_from_or(o0), exp_from_or(o1), exp_from_or(o2));
+    }
+    const bool first = b.g0 == 0;
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        int nib, sume;
+        team_tokens<TS>(tk.lane(s), first, nib, sume);
+        bits[s] = (uint32_t)DT_<DT>::H + 4u * (uint32_t)nib + 4u * (uint32_t)sume;
+    }
+}
+
+// Unpadded packet bits of the team's block for stream s at `code`.
+template <int DT, int TS>
+__device__ __forceinline__ uint32_t team_eval1(const TBlock<DT> &b, int code, int s)
+{
+    const Quant<DT> Q(code, b.Eb);
+    TokCount tc;
+    tc.init();
+    Stream1 st(s, carry_in<DT>(b, Q, 4 * b.g0));
+#pragma unroll 1
+    for (int g = b.g0; g < b.g1; ++g) {
+        typename LaneT<DT>::t xv[4];
+        load4<DT, true>(b, 4 * g, xv);
+        int32_t u[4];
+        tc.push(exp_from_or(group1<DT>(Q, xv, st, u)), true);
+    }
+    int nib, sume;
+    team_tokens<TS>(tc, b.g0 == 0, nib, sume);
+    return (uint32_t)DT_<DT>::H + 4u * (uint32_t)nib + 4u * (uint32_t)sume;
 }
 
 // Largest packet of a block of N samples (all widths W, all tokens absolute).
