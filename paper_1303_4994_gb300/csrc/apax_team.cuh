@@ -130,22 +130,27 @@ __device__ __forceinline__ typename LaneT<DT>::t load1(const TBlock<DT> &b, int 
 }
 
 // ---------------------------------------------------------------- quantiser
-// Per (block, code) quantiser (Sec. 6 attenuator, one rounding of the exact
-// product).  Floats with a power-of-two code (m = 0): x 2^(Q-Eb-k) is exact
-// (a power-of-two scale, |value| <= 2^23), so for k >= 1 (|value| < 2^22)
-// adding 1.5 2^23 rounds it to the nearest integer with ties to even in the
-// binade [2^23, 2^24), whose bit patterns then differ from that of 1.5 2^23
-// by exactly the integer; for k = 0 a round-to-nearest-even conversion of
-// the exact product does it (a product below the normal range rounds to
-// +-0, as the exact value, below 2^-126, does).  int8/int16: the product
-// x (256 - m) and the rounding shift by 8 + k in 32 bits.  Everything else
-// takes exact integer significand arithmetic.
+// Per (block, code) quantiser (Sec. 6 attenuator: q = RNE(x a(c) 2^(Q-Eb)),
+// one rounding of the exact product).
+//   float32: with b = (256 - m) 2^(Q-Eb-8-k), an 8-bit integer times a power
+//   of two and so exact in float32, q = RNE(x b).  A fused multiply-add
+//   forms x b exactly and rounds x b + c once.  For k >= 1, |x b| < 2^22 and
+//   c = 1.5 2^23 puts the sum in the binade [2^23, 2^24), whose unit is 1:
+//   the rounding is RNE to an integer (c is even), and the result's bit
+//   pattern differs from c's by exactly q.  For k = 0, |x b| < 2^23 and
+//   c = +-2^23 with the sign of x does the same in magnitude; with m = 0 as
+//   well b is a power of two, x b is exact in float32 (or below the normal
+//   range, where it and q are 0), and one conversion with RNE gives q.
+//   Blocks whose b leaves the normal range take the exact integer path.
+//   int8/int16: the product x (256 - m) and the rounding shift by 8 + k in
+//   32 bits.  Everything else: exact integer significand arithmetic.
 template <int DT>
 struct Quant {
     Code c;
     int Eb;
-    int mode;     // 0 exact integer path, 1 fused (k >= 1), 2 convert (k == 0), 3 small int
-    float scale;  // 2^(Q - Eb - k)
+    int mode;     // 0 exact integer, 1 fused (k >= 1), 2 convert (k = 0, m = 0),
+                  // 3 small int, 4 fused signed (k = 0, m > 0)
+    float scale;  // b
     int32_t mul, sh, bias;
     __device__ __forceinline__ Quant(int code, int eb) : c(code), Eb(eb), mode(0), scale(0.f)
     {
@@ -153,10 +158,10 @@ struct Quant {
         sh = 1;
         bias = 0;
         if constexpr (DT == 4) {
-            const int se = 23 - eb - c.k;
-            if (!c.zero && c.m == 0 && se >= -126 && se <= 127) {
-                mode = c.k >= 1 ? 1 : 2;
-                scale = __int_as_float((se + 127) << 23);
+            const int se = 15 - eb - c.k;  // b = (256 - m) 2^se; 2^(se+8) for m = 0
+            if (!c.zero && se + 8 >= -126 && se + 8 <= 127 && se >= -126) {
+                mode = c.k >= 1 ? 1 : (c.m == 0 ? 2 : 4);
+                scale = __fmul_rn((float)(256 - c.m), __int_as_float((se + 127) << 23));
             }
         }
         if constexpr (DT == 1 || DT == 2) {
@@ -176,6 +181,12 @@ struct Quant {
                 return __float_as_int(t) - 0x4B400000;
             }
             if (mode == 2) return __float2int_rn(__fmul_rn(__uint_as_float(v), scale));
+            if (mode == 4) {
+                const uint32_t sg = v & 0x80000000u;
+                const float t = __fmaf_rn(__uint_as_float(v), scale, __uint_as_float(sg | 0x4B000000u));
+                const int32_t a = (__float_as_int(t) & 0x7fffffff) - 0x4B000000;
+                return sg ? -a : a;
+            }
         }
         if constexpr (DT == 1 || DT == 2) {
             const int32_t t = (int32_t)v * mul;

@@ -118,6 +118,19 @@ def test_parity_block_sizes(dt, N):
         pass
 
 
+@pytest.mark.parametrize("dt", [4, 5])
+def test_quantiser_code_classes(dt):
+    # every class of attenuation code: k = 0 with m = 0 and m > 0, both ends
+    # of m, large k, the zero code, and random codes; wide and narrow blocks
+    rng = np.random.default_rng(70 + dt)
+    codes = [0, 1, 5, 64, 127, 128, 129, 255, 256, 300, 1000, 2047, 2048, 3000, 3968, 3969,
+             4000, 4094, 4095] + [int(c) for c in rng.integers(0, 4096, 24)]
+    for kind in (0, 1, 2):
+        x = _data(dt, 256 * 6 + 7, rng, kind)
+        for code in codes:
+            _roundtrip(x, 256, 1, (1, 1), code)
+
+
 def test_empty_array():
     for dt in (2, 4):
         x = np.zeros(0, dtype=NP[dt])
