@@ -182,19 +182,18 @@ __device__ __forceinline__ void encode_tile(const EncArgs &a, uint64_t tile, uin
     const Quant<DT> Q(code, b.Eb);
     TokCount tc;
     tc.init();
-    const Carry cin = carry_in<DT>(b, Q, 4 * b.g0);
-    {
-        Stream1 st(s, cin);
+    with_quant<DT>(Q, [&](const auto &qf) {
+        Stream1 st(s, carry_in<DT>(b, qf, 4 * b.g0));
 #pragma unroll 1
         for (int g = b.g0; g < b.g1; ++g) {
             lt xv[4];
             load4<DT, true>(b, 4 * g, xv);
             int32_t u[4];
-            const int e = exp_from_or(group1<DT>(Q, xv, st, u));
+            const int e = exp_from_or(group1<DT>(qf, xv, st, u));
             ebuf[g] = (uint8_t)e;
             tc.push(e, true);
         }
-    }
+    });
     int nib_total, sume_total, nib_mine;
     bool s_in;
     team_tokens<TS>(tc, b.g0 == 0, nib_total, sume_total, &s_in, &nib_mine);
@@ -245,20 +244,34 @@ __device__ __forceinline__ void encode_tile(const EncArgs &a, uint64_t tile, uin
         // mantissas of my groups after the token section
         NibWriter mw;
         mw.start(pkt, (uint32_t)H + 4u * (uint32_t)nib_total + 4u * (uint32_t)sume_before);
-        Stream1 sm(s, cin);
+        with_quant<DT>(Q, [&](const auto &qf) {
+            Stream1 sm(s, carry_in<DT>(b, qf, 4 * b.g0));
 #pragma unroll 1
-        for (int g = b.g0; g < b.g1; ++g) {
-            lt xv[4];
-            load4<DT, true>(b, 4 * g, xv);
-            int32_t u[4];
-            group1<DT>(Q, xv, sm, u);
-            const int e = ebuf[g];
-            if (e) {
-                const uint32_t m = e >= 32 ? 0xffffffffu : ((1u << e) - 1u);
-#pragma unroll
-                for (int i = 0; i < 4; ++i) mw.put((uint32_t)u[i] & m, e);
+            for (int g = b.g0; g < b.g1; ++g) {
+                lt xv[4];
+                load4<DT, true>(b, 4 * g, xv);
+                int32_t u[4];
+                group1<DT>(qf, xv, sm, u);
+                const int e = ebuf[g];
+                if (e) {
+                    // the group's four e-bit fields, appended as few wide pieces
+                    const uint32_t m = e >= 32 ? 0xffffffffu : ((1u << e) - 1u);
+                    const uint32_t f0 = (uint32_t)u[0] & m, f1 = (uint32_t)u[1] & m,
+                                   f2 = (uint32_t)u[2] & m, f3 = (uint32_t)u[3] & m;
+                    if (e <= 8) {
+                        mw.put(f0 | (f1 << e) | (f2 << (2 * e)) | (f3 << (3 * e)), 4 * e);
+                    } else if (e <= 16) {
+                        mw.put(f0 | (f1 << e), 2 * e);
+                        mw.put(f2 | (f3 << e), 2 * e);
+                    } else {
+                        mw.put(f0, e);
+                        mw.put(f1, e);
+                        mw.put(f2, e);
+                        mw.put(f3, e);
+                    }
+                }
             }
-        }
+        });
         mw.flush();
     }
     __syncthreads();
@@ -274,24 +287,31 @@ __device__ __forceinline__ void encode_tile(const EncArgs &a, uint64_t tile, uin
             const uint32_t total = __shfl_sync(kFull, incl, 31);
             __syncwarp();
             if (l < nteams) s_words[l] = incl - v;
-            if (l == 0) {
-                uint64_t excl = 0;
-                const bool hook = a.test_stall_tile == (long long)tile;
-                if (tile == 0) {
-                    if (!hook) atomicExch(a.tiles, kFlagP | total);
-                } else {
-                    if (!hook) atomicExch(a.tiles + tile, kFlagA | total);
-                    int64_t tt = (int64_t)tile - 1;
-                    while (tt >= 0) {
-                        const uint64_t st = wait_tile(a.tiles, (uint64_t)tt, a.spin_limit, a.status);
-                        excl += st & kValMask;
-                        if ((st & ~kValMask) == kFlagP) break;
-                        --tt;
-                    }
-                    if (!hook) atomicExch(a.tiles + tile, kFlagP | ((excl + total) & kValMask));
+            // decoupled look-back, 32 predecessors per probe: lane l reads
+            // tile base - l; the nearest inclusive prefix ends the walk
+            const bool hook = a.test_stall_tile == (long long)tile;
+            uint64_t excl = 0;
+            if (tile == 0) {
+                if (l == 0 && !hook) atomicExch(a.tiles, kFlagP | total);
+            } else {
+                if (l == 0 && !hook) atomicExch(a.tiles + tile, kFlagA | total);
+                int64_t base = (int64_t)tile - 1;
+                while (true) {
+                    const int64_t tt = base - l;
+                    const uint64_t st = tt >= 0 ? wait_tile(a.tiles, (uint64_t)tt, a.spin_limit, a.status)
+                                                : kFlagP;
+                    const unsigned pm = __ballot_sync(kFull, (st & ~kValMask) == kFlagP);
+                    const int near = pm ? __ffs(pm) - 1 : 31;
+                    uint64_t val = l <= near ? (st & kValMask) : 0;
+#pragma unroll
+                    for (int m = 16; m >= 1; m >>= 1) val += __shfl_xor_sync(kFull, val, m);
+                    excl += val;
+                    if (pm) break;
+                    base -= 32;
                 }
-                s_base = excl;
+                if (l == 0 && !hook) atomicExch(a.tiles + tile, kFlagP | ((excl + total) & kValMask));
             }
+            if (l == 0) s_base = excl;
         }
         __syncthreads();
         off_words = s_base + s_words[team];

@@ -353,59 +353,61 @@ __device__ __forceinline__ void profile_run(const ProfArgs &a, uint64_t run, uin
         tc.init();
         int64_t sq = 0, sA = 0, sB = 0, sD = 0;  // 64-bit partials (f32, i8, i16)
         i128 wq = 0, wA = 0, wB = 0, wD = 0;     // 128-bit partials (f64, i32)
-        Stream1 sm(s, carry_in<DT>(b, Q, 4 * b.g0));
-        const int cD = -103 - b.Eb - k;  // f32: D' shift = bexp + cD
+        with_quant<DT>(Q, [&](const auto &qf) {
+            Stream1 sm(s, carry_in<DT>(b, qf, 4 * b.g0));
+            const int cD = -103 - b.Eb - k;  // f32: D' shift = bexp + cD
 #pragma unroll 1
-        for (int g = b.g0; g < ge; ++g) {
-            lt xv[4];
-            load4<DT, true>(b, 4 * g, xv);
-            int32_t qq[4], uu[4];
-            tc.push(exp_from_or(group1q<DT>(Q, xv, sm, qq, uu)), true);
+            for (int g = b.g0; g < ge; ++g) {
+                lt xv[4];
+                load4<DT, true>(b, 4 * g, xv);
+                int32_t qq[4], uu[4];
+                tc.push(exp_from_or(group1q<DT>(qf, xv, sm, qq, uu)), true);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                if (4 * g + i >= b.L) continue;
-                const int32_t qi = qq[i];
-                if constexpr (DT == 4) {
-                    const uint32_t v = (uint32_t)xv[i];
-                    const uint32_t qm = (uint32_t)abs(qi);
-                    const uint32_t M = (v & 0x7fffffu) | 0x800000u;
-                    const int32_t Dm = (int32_t)(shl_clamp(M, (int)((v >> 23) & 0xff) + cD) - (qm << 24));
-                    sq += qi;
-                    sA += (int64_t)qm * qm;
-                    sB += (int64_t)(int32_t)qm * Dm;
-                } else if constexpr (DT == 5) {
-                    if (qi) {
-                        const FDec<DT> d = fdec<DT>(xv[i]);
-                        const int sh = s_exp - d.ex;
-                        const uint64_t qm = (uint64_t)(qi < 0 ? -(int64_t)qi : (int64_t)qi);
-                        int64_t rem = 0;
-                        if (sh > 0 && sh < 64) rem = (int64_t)(d.M - (qm << sh));
-                        const int64_t Dp = (sh > 0 && sh <= 53) ? rem * ((int64_t)1 << (53 - sh)) : 0;
-                        wq += qi;
-                        wA += (i128)((int64_t)qi * qi);
-                        wB += (i128)(int64_t)qm * Dp;
-                    }
-                } else {
-                    const int64_t xi = (int64_t)xv[i];
-                    int64_t yv = (int64_t)qi * ((int64_t)1 << k);
-                    constexpr int64_t lo = DT == 1 ? -128 : (DT == 2 ? -32768 : -2147483648ll);
-                    constexpr int64_t hi = DT == 1 ? 127 : (DT == 2 ? 32767 : 2147483647ll);
-                    yv = yv < lo ? lo : (yv > hi ? hi : yv);
-                    const int64_t dd = xi - yv;
-                    if constexpr (DT == 3) {
-                        wq += yv;
-                        wA += (i128)(xi * yv);
-                        wB += (i128)(yv * yv);
-                        wD += (i128)dd * dd;
+                for (int i = 0; i < 4; ++i) {
+                    if (4 * g + i >= b.L) continue;
+                    const int32_t qi = qq[i];
+                    if constexpr (DT == 4) {
+                        const uint32_t v = (uint32_t)xv[i];
+                        const uint32_t qm = (uint32_t)abs(qi);
+                        const uint32_t M = (v & 0x7fffffu) | 0x800000u;
+                        const int32_t Dm = (int32_t)(shl_clamp(M, (int)((v >> 23) & 0xff) + cD) - (qm << 24));
+                        sq += qi;
+                        sA += (int64_t)qm * qm;
+                        sB += (int64_t)(int32_t)qm * Dm;
+                    } else if constexpr (DT == 5) {
+                        if (qi) {
+                            const FDec<DT> d = fdec<DT>(xv[i]);
+                            const int sh = s_exp - d.ex;
+                            const uint64_t qm = (uint64_t)(qi < 0 ? -(int64_t)qi : (int64_t)qi);
+                            int64_t rem = 0;
+                            if (sh > 0 && sh < 64) rem = (int64_t)(d.M - (qm << sh));
+                            const int64_t Dp = (sh > 0 && sh <= 53) ? rem * ((int64_t)1 << (53 - sh)) : 0;
+                            wq += qi;
+                            wA += (i128)((int64_t)qi * qi);
+                            wB += (i128)(int64_t)qm * Dp;
+                        }
                     } else {
-                        sq += yv;
-                        sA += xi * yv;
-                        sB += yv * yv;
-                        sD += dd * dd;
+                        const int64_t xi = (int64_t)xv[i];
+                        int64_t yv = (int64_t)qi * ((int64_t)1 << k);
+                        constexpr int64_t lo = DT == 1 ? -128 : (DT == 2 ? -32768 : -2147483648ll);
+                        constexpr int64_t hi = DT == 1 ? 127 : (DT == 2 ? 32767 : 2147483647ll);
+                        yv = yv < lo ? lo : (yv > hi ? hi : yv);
+                        const int64_t dd = xi - yv;
+                        if constexpr (DT == 3) {
+                            wq += yv;
+                            wA += (i128)(xi * yv);
+                            wB += (i128)(yv * yv);
+                            wD += (i128)dd * dd;
+                        } else {
+                            sq += yv;
+                            sA += xi * yv;
+                            sB += yv * yv;
+                            sD += dd * dd;
+                        }
                     }
                 }
             }
-        }
+        });
         int nib, sume;
         team_tokens<TS>(tc, b.g0 == 0, nib, sume);
         const uint32_t bits = (uint32_t)H + 4u * (uint32_t)nib + 4u * (uint32_t)sume;

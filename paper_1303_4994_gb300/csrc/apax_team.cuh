@@ -196,6 +196,52 @@ struct Quant {
     }
 };
 
+// The quantiser with its mode fixed at compile time (no per-sample mode
+// test), and the dispatch that picks it once per (block, code).  Callers
+// keep warp collectives outside the dispatched function: teams of one warp
+// may take different modes.
+template <int DT, int M>
+struct QuantM {
+    const Quant<DT> &Q;
+    __device__ __forceinline__ explicit QuantM(const Quant<DT> &q) : Q(q) {}
+    __device__ __forceinline__ int32_t operator()(typename LaneT<DT>::t v) const
+    {
+        if constexpr (DT == 4 && M == 1) {
+            const float t = __fmaf_rn(__uint_as_float(v), Q.scale, 12582912.0f);
+            return __float_as_int(t) - 0x4B400000;
+        } else if constexpr (DT == 4 && M == 2) {
+            return __float2int_rn(__fmul_rn(__uint_as_float(v), Q.scale));
+        } else if constexpr (DT == 4 && M == 4) {
+            const uint32_t sg = v & 0x80000000u;
+            const float t = __fmaf_rn(__uint_as_float(v), Q.scale, __uint_as_float(sg | 0x4B000000u));
+            const int32_t a = (__float_as_int(t) & 0x7fffffff) - 0x4B000000;
+            return sg ? -a : a;
+        } else if constexpr ((DT == 1 || DT == 2) && M == 3) {
+            const int32_t t = (int32_t)v * Q.mul;
+            return (t + Q.bias + ((t >> Q.sh) & 1)) >> Q.sh;
+        } else {
+            return quantise<DT>(v, Q.c, Q.Eb);
+        }
+    }
+};
+
+template <int DT, class F>
+__device__ __forceinline__ void with_quant(const Quant<DT> &Q, F &&f)
+{
+    if constexpr (DT == 4) {
+        switch (Q.mode) {
+        case 1: f(QuantM<DT, 1>(Q)); break;
+        case 2: f(QuantM<DT, 2>(Q)); break;
+        case 4: f(QuantM<DT, 4>(Q)); break;
+        default: f(QuantM<DT, 0>(Q)); break;
+        }
+    } else if constexpr (DT == 1 || DT == 2) {
+        f(QuantM<DT, 3>(Q));
+    } else {
+        f(QuantM<DT, 0>(Q));
+    }
+}
+
 // ---------------------------------------------------------------- token counter
 // Greedy JEE (Sec. 6) over one thread's groups.  The first group of the
 // thread waits for its predecessor's exponent (exchanged afterwards); the
@@ -314,11 +360,12 @@ __device__ __forceinline__ void open_team_block(TBlock<DT> &b, const typename DT
     b.Eb = 0;
     b.bad = false;
     if constexpr (T::F) {
+        // the largest magnitude's bit pattern; NaN and infinities have all
+        // exponent bits set and so compare above every finite magnitude
         using B = typename T::bits;
         constexpr B absm = ~((B)1 << (sizeof(B) * 8 - 1));
         constexpr B expm = (B)T::EMAX << T::MB;
-        uint64_t mx = 0;
-        bool bad = false;
+        B mx = 0;
 #pragma unroll 1
         for (int g = b.g0; g < b.g1; ++g) {
             typename LaneT<DT>::t xv[4];
@@ -326,14 +373,16 @@ __device__ __forceinline__ void open_team_block(TBlock<DT> &b, const typename DT
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const B a = xv[i] & absm;
-                bad |= (a & expm) == expm;
-                mx = umax64(mx, (uint64_t)a);
+                mx = a > mx ? a : mx;
             }
         }
 #pragma unroll
-        for (int m = TS / 2; m >= 1; m >>= 1) mx = umax64(mx, tshfl_xor<TS>(mx, m));
-        b.bad = team_sum<TS>((int)bad) > 0;
-        b.Eb = b.bad ? 0 : block_exp_from_maxbits<DT>(mx);
+        for (int m = TS / 2; m >= 1; m >>= 1) {
+            const B o = tshfl_xor<TS>(mx, m);
+            mx = o > mx ? o : mx;
+        }
+        b.bad = mx >= expm;
+        b.Eb = b.bad ? 0 : block_exp_from_maxbits<DT>((uint64_t)mx);
     }
 }
 
@@ -429,8 +478,8 @@ struct Carry {
     uint32_t qp1, qp2, qpp2;
 };
 
-template <int DT>
-__device__ __forceinline__ Carry carry_in(const TBlock<DT> &b, const Quant<DT> &Q, int s0)
+template <int DT, class QF>
+__device__ __forceinline__ Carry carry_in(const TBlock<DT> &b, const QF &Q, int s0)
 {
     Carry c;
     if (s0 == 0) {
@@ -448,8 +497,8 @@ __device__ __forceinline__ Carry carry_in(const TBlock<DT> &b, const Quant<DT> &
 }
 
 // One group, all three streams: OR of the width terms of each stream.
-template <int DT>
-__device__ __forceinline__ void group3(const Quant<DT> &Q, const typename LaneT<DT>::t (&xv)[4],
+template <int DT, class QF>
+__device__ __forceinline__ void group3(const QF &Q, const typename LaneT<DT>::t (&xv)[4],
                                        Carry &c, uint32_t &o0, uint32_t &o1, uint32_t &o2)
 {
     constexpr int W = DT_<DT>::W;
@@ -481,8 +530,8 @@ struct Stream1 {
 
 // One group, one stream: the quantised values, the stream values
 // (sign-extended) and their OR of width terms.
-template <int DT>
-__device__ __forceinline__ uint32_t group1q(const Quant<DT> &Q, const typename LaneT<DT>::t (&xv)[4],
+template <int DT, class QF>
+__device__ __forceinline__ uint32_t group1q(const QF &Q, const typename LaneT<DT>::t (&xv)[4],
                                             Stream1 &st, int32_t (&qv)[4], int32_t (&u)[4])
 {
     constexpr int W = DT_<DT>::W;
@@ -499,8 +548,8 @@ __device__ __forceinline__ uint32_t group1q(const Quant<DT> &Q, const typename L
     return o;
 }
 
-template <int DT>
-__device__ __forceinline__ uint32_t group1(const Quant<DT> &Q, const typename LaneT<DT>::t (&xv)[4],
+template <int DT, class QF>
+__device__ __forceinline__ uint32_t group1(const QF &Q, const typename LaneT<DT>::t (&xv)[4],
                                            Stream1 &st, int32_t (&u)[4])
 {
     int32_t qv[4];
@@ -567,15 +616,17 @@ __device__ __forceinline__ void team_eval3(const TBlock<DT> &b, int code, uint32
     const Quant<DT> Q(code, b.Eb);
     Tok3 tk;
     tk.init();
-    Carry c = carry_in<DT>(b, Q, 4 * b.g0);
+    with_quant<DT>(Q, [&](const auto &qf) {
+        Carry c = carry_in<DT>(b, qf, 4 * b.g0);
 #pragma unroll 1
-    for (int g = b.g0; g < b.g1; ++g) {
-        typename LaneT<DT>::t xv[4];
-        load4<DT, true>(b, 4 * g, xv);
-        uint32_t o0, o1, o2;
-        group3<DT>(Q, xv, c, o0, o1, o2);
-        tk.push(exp_from_or(o0), exp_from_or(o1), exp_from_or(o2));
-    }
+        for (int g = b.g0; g < b.g1; ++g) {
+            typename LaneT<DT>::t xv[4];
+            load4<DT, true>(b, 4 * g, xv);
+            uint32_t o0, o1, o2;
+            group3<DT>(qf, xv, c, o0, o1, o2);
+            tk.push(exp_from_or(o0), exp_from_or(o1), exp_from_or(o2));
+        }
+    });
     const bool first = b.g0 == 0;
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
@@ -592,14 +643,16 @@ __device__ __forceinline__ uint32_t team_eval1(const TBlock<DT> &b, int code, in
     const Quant<DT> Q(code, b.Eb);
     TokCount tc;
     tc.init();
-    Stream1 st(s, carry_in<DT>(b, Q, 4 * b.g0));
+    with_quant<DT>(Q, [&](const auto &qf) {
+        Stream1 st(s, carry_in<DT>(b, qf, 4 * b.g0));
 #pragma unroll 1
-    for (int g = b.g0; g < b.g1; ++g) {
-        typename LaneT<DT>::t xv[4];
-        load4<DT, true>(b, 4 * g, xv);
-        int32_t u[4];
-        tc.push(exp_from_or(group1<DT>(Q, xv, st, u)), true);
-    }
+        for (int g = b.g0; g < b.g1; ++g) {
+            typename LaneT<DT>::t xv[4];
+            load4<DT, true>(b, 4 * g, xv);
+            int32_t u[4];
+            tc.push(exp_from_or(group1<DT>(qf, xv, st, u)), true);
+        }
+    });
     int nib, sume;
     team_tokens<TS>(tc, b.g0 == 0, nib, sume);
     return (uint32_t)DT_<DT>::H + 4u * (uint32_t)nib + 4u * (uint32_t)sume;
