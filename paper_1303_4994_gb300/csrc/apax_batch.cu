@@ -96,9 +96,34 @@ Geo geo_of(const apax_batch *b, const apax_batch_config &c)
     return g;
 }
 
-size_t smem_of(const apax_batch *b, const Geo &g)
+size_t pkt_smem_of(const apax_batch *b, const Geo &g)
 {
     return (size_t)(g.threads / g.ts) * (b->pkt_words + b->ebuf_words) * 4;
+}
+
+// Staging of a tile for the largest block (elements x element size) of the
+// batch, or 0.
+size_t stage_of(const apax_batch *b, const Geo &g)
+{
+    const int pol = stage_policy();
+    bool any_fr = false;
+    for (const EncArgs &a : b->jobs) any_fr |= a.mode == APAX_FIXED_RATE;
+    if (pol == 0 || (pol < 0 && !any_fr)) return 0;
+    uint64_t mx = 0;
+    for (const EncArgs &a : b->jobs) {
+        Fmt f;
+        fmt_of(a.dtype, f);
+        const uint64_t v = (uint64_t)a.N * f.size;
+        mx = v > mx ? v : mx;
+    }
+    const size_t ps = pkt_smem_of(b, g);
+    return stage_bytes(1, (uint32_t)mx, g.threads / g.ts, (ps + 15) / 16 * 16);
+}
+
+size_t smem_of(const apax_batch *b, const Geo &g)
+{
+    const size_t ps = pkt_smem_of(b, g), sb = stage_of(b, g);
+    return sb ? (ps + 15) / 16 * 16 + sb : ps;
 }
 
 bool config_ok(const apax_batch *b, const apax_batch_config &c)
@@ -109,7 +134,7 @@ bool config_ok(const apax_batch *b, const apax_batch_config &c)
         if (c.threads != 64 && c.threads != 128) return false;
     }
     Geo g = geo_of(b, c);
-    return smem_of(b, g) <= kEncSmemCap;
+    return pkt_smem_of(b, g) <= kEncSmemCap;
 }
 
 // Smallest tile of any allowed geometry (sizes the look-back arrays).
@@ -155,6 +180,7 @@ int apply_config(apax_batch *b, const apax_batch_config &c)
         EncArgs &a = tab[i];
         a.pkt_words = b->pkt_words;
         a.ebuf_words = b->ebuf_words;
+        a.stage_off = stage_of(b, g) ? (uint32_t)((pkt_smem_of(b, g) + 15) / 16 * 16) : 0;
         a.gp = (int)(g.ts == 8 ? b->gp8[i] : b->gp32[i]);
         a.ntiles = a.nb ? (a.nb + nteams - 1) / nteams : 1;
         a.ticket = nullptr;

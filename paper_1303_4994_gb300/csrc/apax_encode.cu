@@ -142,11 +142,23 @@ __device__ __forceinline__ void encode_tile(const EncArgs &a, uint64_t tile, uin
     if (tile == 0 && threadIdx.x == 0) write_container_header(a, code);
 
     const raw *x = reinterpret_cast<const raw *>(a.x);
+    // the tile's blocks and the one before it (the lag decision's halo) in
+    // shared memory, when the plan has room for them
+    uint64_t base = 0;
+    if (a.stage_off) {
+        raw *xs = reinterpret_cast<raw *>(reinterpret_cast<uint8_t *>(smem) + a.stage_off);
+        const uint64_t jb0 = tile * (uint64_t)nteams;
+        base = jb0 ? jb0 - 1 : 0;
+        const uint64_t bend = min(jb0 + (uint64_t)nteams, a.nb);
+        stage_blocks<DT>(xs, x, a.n, a.N, base, bend > base ? bend : base);
+        __syncthreads();
+        x = xs;
+    }
     // stream decision: best(j-1) at code 0 (block 0 uses its own)
     int s;
     {
         TBlock<DT> pv;
-        open_team_block<DT, TS>(pv, x, a.n, a.N, a.nb, j == 0 ? 0 : j - 1, gp);
+        open_team_block<DT, TS>(pv, x, a.n, a.N, a.nb, j == 0 ? 0 : j - 1, gp, base);
         uint32_t bb[3];
         team_eval3<DT, TS>(pv, 0, bb);
         s = 0;
@@ -154,7 +166,7 @@ __device__ __forceinline__ void encode_tile(const EncArgs &a, uint64_t tile, uin
         if (bb[2] < bb[s]) s = 2;
     }
     TBlock<DT> b;
-    open_team_block<DT, TS>(b, x, a.n, a.N, a.nb, j, gp);
+    open_team_block<DT, TS>(b, x, a.n, a.N, a.nb, j, gp, base);
     if (b.active && b.bad && t == 0) set_status(a.status, -8);
     uint32_t plen = 0;
     if (MODE == 0) {

@@ -25,6 +25,7 @@ struct EncArgs {
     uint64_t cap;
     uint64_t poff;      // payload offset in the container
     uint32_t pkt_words, ebuf_words;  // per-team shared-memory layout
+    uint32_t stage_off; // byte offset of the staged tile in shared memory (0: none)
     int gp;             // groups per team thread
     uint64_t ntiles;
     // workspace
@@ -82,6 +83,7 @@ struct ProfArgs {
     int ncand;
     uint32_t codes[32];
     uint64_t nruns;     // level-1 nodes (16 blocks each)
+    uint32_t stage_off; // byte offset of the staged run in shared memory (0: none)
     int gp;             // groups per team thread
     double *run_sums;   // [nruns][2 + 4*ncand]: sx, sxx, then (sy, sxy, syy, sdd) per candidate
     unsigned long long *bytes;  // [ncand] payload bytes (atomic)

@@ -4,6 +4,7 @@
 
 #include <stdint.h>
 #include <stddef.h>
+#include <stdlib.h>
 
 #include "apax_team.cuh"
 #include "apax_kernels.h"
@@ -118,6 +119,30 @@ inline void default_geometry(size_t per_team_bytes, int &ts, int &threads)
         while (warps > 1 && (size_t)warps * per_team_bytes > kEncSmemCap) --warps;
         threads = 32 * warps;
     }
+}
+
+// Staging policy: APAX_STAGE=0 or 1 in the environment forces shared-memory
+// staging of the input off or on (for measurement); otherwise each path
+// uses its default: on for the fixed-rate search (13 passes over a block),
+// off for fixed quality and the profiler sweep, whose occupancy matters
+// more than their L2 re-reads (measured on GB300).
+inline int stage_policy()
+{
+    static int p = [] {
+        const char *e = getenv("APAX_STAGE");
+        return e && (e[0] == '0' || e[0] == '1') ? e[0] - '0' : -1;
+    }();
+    return p;
+}
+
+// Shared-memory staging of a tile (its blocks and the one before): the
+// bytes, or 0 when it would not leave room for enough CTAs per SM.
+constexpr size_t kStageCap = 48 * 1024, kStageTotalCap = 100 * 1024;
+
+inline size_t stage_bytes(int elem_size, uint32_t N, int nteams, size_t smem_before)
+{
+    const size_t b = ((size_t)(nteams + 1) * N * elem_size + 15) / 16 * 16;
+    return (b <= kStageCap && smem_before + b <= kStageTotalCap) ? b : 0;
 }
 
 inline Plan plan_encode(const Fmt &f, uint32_t N, uint64_t nb, uint64_t fr_budget_bytes)

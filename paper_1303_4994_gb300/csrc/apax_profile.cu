@@ -20,9 +20,12 @@
 // range, take an exact fallback with a shared-memory superaccumulator.  Each
 // block sum is rounded once to binary64 and added into the run's partial in
 // block order.
+#include <type_traits>
+
 #include "apax_team.cuh"
 #include "apax_exact.cuh"
 #include "apax_kernels.h"
+#include "apax_plan.h"
 
 namespace apax {
 
@@ -99,11 +102,16 @@ __device__ __forceinline__ W256 team_sum_w256(W256 a)
 }
 
 // per (team, candidate) staging
-struct CandStage {
-    i128 sq, A, B, D;  // float: sum q, A, B; int: sum y, sum xy, sum y^2, sum d^2
+// float: sum q, A, B; int: sum y, sum xy, sum y^2, sum d^2.  64-bit for
+// float32, int8 and int16 (every per-block sum fits), 128-bit otherwise.
+template <typename V>
+struct CandStageT {
+    V sq, A, B, D;
     uint32_t bits;
     int fast;
 };
+template <int DT>
+using CandStage = CandStageT<typename std::conditional<DT == 5 || DT == 3, i128, int64_t>::type>;
 
 template <int DT>
 struct PS {
@@ -170,6 +178,13 @@ __device__ void fallback_team(const TBlock<DT> &b, int code, bool want_block,
     }
 }
 
+// Staging of a run and its halo block, or 0 when it would crowd the SM.
+__host__ __device__ inline size_t profile_stage_bytes(size_t elem, uint32_t N, size_t smem_before)
+{
+    const size_t bytes = ((size_t)(kRun + 1) * N * elem + 15) / 16 * 16;
+    return (bytes <= 48 * 1024 && smem_before + bytes <= 100 * 1024) ? bytes : 0;
+}
+
 // One run (kRun consecutive blocks, a level-1 node of the summation tree):
 // the CTA's teams take one block each and write the run's partial sums.
 template <int DT>
@@ -183,8 +198,8 @@ __device__ __forceinline__ void profile_run(const ProfArgs &a, uint64_t run, uin
     const int nteams = blockDim.x / TS;  // = kRun
     const int nc = a.ncand;
     const int Qn = 2 + 4 * nc;
-    CandStage *cs = reinterpret_cast<CandStage *>(psm) + (size_t)team * nc;
-    double *bv = reinterpret_cast<double *>(psm + (size_t)nteams * nc * sizeof(CandStage));
+    CandStage<DT> *cs = reinterpret_cast<CandStage<DT> *>(psm) + (size_t)team * nc;
+    double *bv = reinterpret_cast<double *>(psm + (size_t)nteams * nc * sizeof(CandStage<DT>));
     long long *accmem = reinterpret_cast<long long *>(bv + (size_t)nteams * Qn);
     __shared__ uint32_t s_fb[kRun];   // fallback requests: bit 0 block, bit 1+i candidate i
     __shared__ int s_ok[kRun];
@@ -193,10 +208,22 @@ __device__ __forceinline__ void profile_run(const ProfArgs &a, uint64_t run, uin
     const int gp = a.gp;
     const uint64_t j = run * nteams + team;
     const raw *x = reinterpret_cast<const raw *>(a.x);
+    // the run's blocks and the one before it in shared memory: the sweep
+    // passes over every block once per candidate
+    uint64_t base = 0;
+    if (a.stage_off) {
+        raw *xs = reinterpret_cast<raw *>(psm + a.stage_off);
+        const uint64_t jb0 = run * (uint64_t)nteams;
+        base = jb0 ? jb0 - 1 : 0;
+        const uint64_t bend = min(jb0 + (uint64_t)nteams, a.nb);
+        stage_blocks<DT>(xs, x, a.n, a.N, base, bend > base ? bend : base);
+        __syncthreads();
+        x = xs;
+    }
     int s;
     {
         TBlock<DT> pv;
-        open_team_block<DT, TS>(pv, x, a.n, a.N, a.nb, j == 0 ? 0 : j - 1, gp);
+        open_team_block<DT, TS>(pv, x, a.n, a.N, a.nb, j == 0 ? 0 : j - 1, gp, base);
         uint32_t bb[3];
         team_eval3<DT, TS>(pv, 0, bb);
         s = 0;
@@ -204,7 +231,7 @@ __device__ __forceinline__ void profile_run(const ProfArgs &a, uint64_t run, uin
         if (bb[2] < bb[s]) s = 2;
     }
     TBlock<DT> b;
-    open_team_block<DT, TS>(b, x, a.n, a.N, a.nb, j, gp);
+    open_team_block<DT, TS>(b, x, a.n, a.N, a.nb, j, gp, base);
     const bool live = b.active && !b.bad;
     if (b.active && b.bad && t == 0) set_status(a.status, -8);
     const int ge = live ? b.g1 : b.g0;  // my groups [g0, ge)
@@ -257,7 +284,7 @@ __device__ __forceinline__ void profile_run(const ProfArgs &a, uint64_t run, uin
             if (tiny) {
 #pragma unroll 1
                 for (int i = 4 * b.g0; i < min(4 * ge, b.L); ++i) {
-                    const uint32_t v = (uint32_t)__ldg(reinterpret_cast<const uint32_t *>(b.p) + i);
+                    const uint32_t v = reinterpret_cast<const uint32_t *>(b.p)[i];
                     const int bexp = (int)((v >> 23) & 0xff);
                     if (!(v & 0x7fffffffu) || (bexp != 0 && bexp - bmax + 23 >= 0)) continue;
                     const int ex = (bexp ? bexp : 1) - 150;
@@ -441,7 +468,7 @@ __device__ __forceinline__ void profile_run(const ProfArgs &a, uint64_t run, uin
         mybv[1] = blk_x[1];
     }
     for (int ci = t; ci < nc; ci += TS) {
-        const CandStage &st = cs[ci];
+        const CandStage<DT> &st = cs[ci];
         const int k = (int)(a.codes[ci] >> 7);
         double v[4] = {0.0, 0.0, 0.0, 0.0};
         if (live) {
@@ -520,7 +547,7 @@ __device__ __forceinline__ void profile_run(const ProfArgs &a, uint64_t run, uin
         unsigned long long by = 0;
         for (int tm = 0; tm < nteams; ++tm)
             if (s_ok[tm]) {
-                const uint32_t bt = reinterpret_cast<CandStage *>(psm)[(size_t)tm * nc + ci].bits;
+                const uint32_t bt = reinterpret_cast<CandStage<DT> *>(psm)[(size_t)tm * nc + ci].bits;
                 by += 4ull * ((bt + 31u) >> 5);
             }
         atomicAdd(a.bytes + ci, by);
@@ -709,12 +736,18 @@ cudaError_t launch_prof_dt(const ProfArgs &a, cudaStream_t s)
 {
     const int threads = TS * kRun;
     const int Qn = 2 + 4 * a.ncand;
-    const size_t smem = (size_t)kRun * a.ncand * sizeof(CandStage) + (size_t)kRun * Qn * 8 +
-                        (DT_<DT>::F ? (size_t)6 * PS<DT>::ND * 8 : 0);
+    size_t smem = (size_t)kRun * a.ncand * sizeof(CandStage<DT>) + (size_t)kRun * Qn * 8 +
+                  (DT_<DT>::F ? (size_t)6 * PS<DT>::ND * 8 : 0);
+    ProfArgs b = a;
+    const size_t sb = host::stage_policy() == 1
+                          ? profile_stage_bytes(sizeof(typename DT_<DT>::raw), a.N, smem)
+                          : 0;
+    b.stage_off = sb ? (uint32_t)((smem + 15) / 16 * 16) : 0;
+    if (sb) smem = b.stage_off + sb;
     auto k = k_profile<DT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    if (a.nruns) k<<<(unsigned)a.nruns, threads, smem, s>>>(a);
+    if (a.nruns) k<<<(unsigned)a.nruns, threads, smem, s>>>(b);
     return cudaGetLastError();
 }
 
@@ -724,7 +757,7 @@ size_t profile_smem(int ncand, bool any_float, int dtype_max_nd)
 {
     const int Qn = 2 + 4 * ncand;
     (void)any_float;
-    return (size_t)kRun * ncand * sizeof(CandStage) + (size_t)kRun * Qn * 8 +
+    return (size_t)kRun * ncand * sizeof(CandStage<5>) + (size_t)kRun * Qn * 8 +
            (size_t)6 * dtype_max_nd * 8;
 }
 

@@ -74,7 +74,8 @@ struct TBlock {
 };
 
 // Load the 4 samples of the group starting at sample s: one vector load
-// when the group is whole and aligned.  Past L the group is padded with
+// when the group is whole and aligned.  Plain (generic) loads: the block
+// may sit in global memory or in a shared-memory staging copy.  Past L the group is padded with
 // zeros, or (PAD) with x[L-1], whose quantised value is the last-group
 // padding of Sec. 6 packets (the replicated q[L-1]).
 template <int DT, bool PAD = false>
@@ -86,19 +87,19 @@ __device__ __forceinline__ void load4(const TBlock<DT> &b, int s, typename LaneT
     constexpr int ES = sizeof(raw);
     if (b.active && s + 4 <= b.L && ((uintptr_t)q & (4 * ES - 1)) == 0) {
         if constexpr (ES == 1) {
-            const uint32_t w = __ldg(reinterpret_cast<const uint32_t *>(q));
+            const uint32_t w = *reinterpret_cast<const uint32_t *>(q);
 #pragma unroll
             for (int j = 0; j < 4; ++j) x[j] = (int8_t)(w >> (8 * j));
         } else if constexpr (ES == 2) {
-            const uint2 w = __ldg(reinterpret_cast<const uint2 *>(q));
+            const uint2 w = *reinterpret_cast<const uint2 *>(q);
             x[0] = (int16_t)w.x; x[1] = (int16_t)(w.x >> 16);
             x[2] = (int16_t)w.y; x[3] = (int16_t)(w.y >> 16);
         } else if constexpr (ES == 4) {
-            const uint4 w = __ldg(reinterpret_cast<const uint4 *>(q));
+            const uint4 w = *reinterpret_cast<const uint4 *>(q);
             x[0] = (lt)w.x; x[1] = (lt)w.y; x[2] = (lt)w.z; x[3] = (lt)w.w;
         } else {
             const ulonglong2 *r = reinterpret_cast<const ulonglong2 *>(q);
-            const ulonglong2 w0 = __ldg(r), w1 = __ldg(r + 1);
+            const ulonglong2 w0 = r[0], w1 = r[1];
             x[0] = w0.x; x[1] = w0.y; x[2] = w1.x; x[3] = w1.y;
         }
     } else {
@@ -108,9 +109,9 @@ __device__ __forceinline__ void load4(const TBlock<DT> &b, int s, typename LaneT
             if (PAD && i >= b.L) i = b.L - 1;
             if (b.active && i >= 0 && i < b.L) {
                 if constexpr (DT_<DT>::F)
-                    x[j] = __ldg(reinterpret_cast<const typename DT_<DT>::bits *>(b.p + i));
+                    x[j] = *reinterpret_cast<const typename DT_<DT>::bits *>(b.p + i);
                 else
-                    x[j] = (lt)__ldg(b.p + i);
+                    x[j] = (lt)b.p[i];
             } else {
                 x[j] = 0;
             }
@@ -124,9 +125,9 @@ __device__ __forceinline__ typename LaneT<DT>::t load1(const TBlock<DT> &b, int 
     using lt = typename LaneT<DT>::t;
     if (!b.active || s < 0 || s >= b.L) return 0;
     if constexpr (DT_<DT>::F)
-        return __ldg(reinterpret_cast<const typename DT_<DT>::bits *>(b.p + s));
+        return *reinterpret_cast<const typename DT_<DT>::bits *>(b.p + s);
     else
-        return (lt)__ldg(b.p + s);
+        return (lt)b.p[s];
 }
 
 // ---------------------------------------------------------------- quantiser
@@ -346,12 +347,13 @@ __device__ __forceinline__ void team_tokens(const TokCount &c, bool block_first,
 template <int DT, int TS>
 __device__ __forceinline__ void open_team_block(TBlock<DT> &b, const typename DT_<DT>::raw *x,
                                                 uint64_t n, uint32_t N, uint64_t nb, uint64_t j,
-                                                int gp)
+                                                int gp, uint64_t base_block = 0)
 {
     using T = DT_<DT>;
     b.active = j < nb;
     const uint64_t off = j * (uint64_t)N;
-    b.p = x + (b.active ? off : 0);
+    // x holds blocks from base_block on (the array itself, or a staged tile)
+    b.p = x + (b.active ? off - base_block * (uint64_t)N : 0);
     b.L = b.active ? (int)((n - off) < N ? (n - off) : N) : 0;
     b.G = (b.L + 3) >> 2;
     const int t = tlane<TS>();
@@ -656,6 +658,43 @@ __device__ __forceinline__ uint32_t team_eval1(const TBlock<DT> &b, int code, in
     int nib, sume;
     team_tokens<TS>(tc, b.g0 == 0, nib, sume);
     return (uint32_t)DT_<DT>::H + 4u * (uint32_t)nib + 4u * (uint32_t)sume;
+}
+
+// ---------------------------------------------------------------- staging
+// Copy blocks [b0, b1) of the array into shared memory (all threads of the
+// CTA; zeros past n), one group of 4 samples per vector access, so that the
+// codec's repeated passes over a block read shared memory instead of L2.
+template <int DT>
+__device__ __forceinline__ void stage_blocks(typename DT_<DT>::raw *xs, const typename DT_<DT>::raw *x,
+                                             uint64_t n, uint32_t N, uint64_t b0, uint64_t b1)
+{
+    using raw = typename DT_<DT>::raw;
+    constexpr int ES = sizeof(raw);
+    const uint64_t s0 = b0 * (uint64_t)N;
+    const uint64_t s1 = min(b1 * (uint64_t)N, n);
+    const uint32_t groups = (uint32_t)((b1 - b0) * (uint64_t)N / 4);
+    const bool al = (((uintptr_t)(x + s0)) & (4 * ES - 1)) == 0;
+    for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x) {
+        const uint64_t i = s0 + 4ull * g;
+        raw *d = xs + 4ull * g;
+        if (al && i + 4 <= s1) {
+            if constexpr (ES == 1) {
+                *reinterpret_cast<uint32_t *>(d) = __ldg(reinterpret_cast<const uint32_t *>(x + i));
+            } else if constexpr (ES == 2) {
+                *reinterpret_cast<uint2 *>(d) = __ldg(reinterpret_cast<const uint2 *>(x + i));
+            } else if constexpr (ES == 4) {
+                *reinterpret_cast<uint4 *>(d) = __ldg(reinterpret_cast<const uint4 *>(x + i));
+            } else {
+                const ulonglong2 *r = reinterpret_cast<const ulonglong2 *>(x + i);
+                ulonglong2 *w = reinterpret_cast<ulonglong2 *>(d);
+                w[0] = __ldg(r);
+                w[1] = __ldg(r + 1);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) d[k] = i + k < s1 ? x[i + k] : (raw)0;
+        }
+    }
 }
 
 // Largest packet of a block of N samples (all widths W, all tokens absolute).
