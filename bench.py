@@ -44,6 +44,28 @@ TARGET = 0.9999
 N_BLOCK = 256
 
 
+# Profiler sweep, integer operations per sample of the algorithm (16
+# candidates x (quantise 2, derivative 2, width 2, exact sums 7, exponent
+# and JEE 2) + stream decision 17 + block sums 6 + maximum 2).
+PROFILE_OPS_PER_SAMPLE = 16 * 15 + 17 + 6 + 2
+ALU_PEAK_TOPS = 152 * 4 * 32 * 2.070e9 / 1e12
+
+
+def _traffic(kernel):
+    """DRAM bytes per launch of `kernel` on this workload, from the committed
+    ncu summary (profiles/traffic_f32_4096x4096.txt: 'kernel bytes' lines)."""
+    path = os.path.join(ROOT, "profiles", "traffic_f32_4096x4096.txt")
+    try:
+        with open(path) as f:
+            for ln in f:
+                parts = ln.split()
+                if len(parts) == 2 and parts[0] == kernel:
+                    return int(parts[1])
+    except OSError:
+        pass
+    return None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -69,7 +91,7 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -108,6 +130,21 @@ class Clocks:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def max_over_ranks(values, device, world):
+    """Timings of every rank -> the slowest rank's, on every rank."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def aggregate_gbs(bytes_per_rank, world, ms):
+    """Whole-job throughput: every rank's bytes over the slowest rank's time."""
+    return world * bytes_per_rank / ms / 1e6
 
 
 def run_ours(args, rank, world, local_rank):
@@ -160,7 +197,8 @@ def run_ours(args, rank, world, local_rank):
     while c > 1:
         c = (c + 15) // 16
         levels += 1
-    launches_per_step = 1 + levels + 1 + 1 + 1  # profile, tree levels, finalize, encode, decode
+    # profile, tree levels, finalize, encode, decode (two size classes)
+    launches_per_step = 1 + levels + 1 + 1 + 2
 
     for _ in range(max(args.warmup, 3)):
         flush.zero_()
@@ -218,10 +256,7 @@ def run_ours(args, rank, world, local_rank):
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e = float(np.mean(e2e_ms))
 
-    tens = torch.tensor([ms, ms_prof, ms_enc, ms_dec, e2e], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tens, op=dist.ReduceOp.MAX)
-    ms, ms_prof, ms_enc, ms_dec, e2e = tens.tolist()
+    ms, ms_prof, ms_enc, ms_dec, e2e = max_over_ranks([ms, ms_prof, ms_enc, ms_dec, e2e], dev, world)
 
     peak, peak_kind = _peaks()
     enc_bytes = xb + er.bytes
@@ -235,14 +270,24 @@ def run_ours(args, rank, world, local_rank):
     for k in kern.values():
         k["frac_hbm"] = k["gbs"] / peak
     dom = max(kern, key=lambda k: kern[k]["ms"])
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tfile):
-        with open(tfile) as f:
-            traffic = json.load(f).get(dom)
+    traffic = _traffic(dom)
+    if dom == "profile":
+        # the sweep is bound by integer issue: algorithmic operations per
+        # sample (the model stated with the design notes) over the issue peak
+        ops = PROFILE_OPS_PER_SAMPLE * n / (ms_prof * 1e-3)
+        roof = {"bound": "alu", "kernel": dom, "achieved": ops / 1e12,
+                "peak": ALU_PEAK_TOPS, "unit": "Tops/s", "frac": ops / 1e12 / ALU_PEAK_TOPS,
+                "traffic": traffic, "ops_per_sample": PROFILE_OPS_PER_SAMPLE,
+                "peak_source": "152 SMs x 4 schedulers x 32 lanes x 2070 MHz (one warp "
+                               "instruction per scheduler per clock)",
+                "hbm_frac": kern[dom]["gbs"] / peak}
+    else:
+        roof = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["gbs"], "peak": peak,
+                "unit": "GB/s", "frac": kern[dom]["gbs"] / peak, "traffic": traffic,
+                "peak_source": f"{peak_kind} hbm_gbs"}
     line = {
         "metric": METRIC,
-        "value": round(world * xb / ms / 1e6, 3),
+        "value": round(aggregate_gbs(xb, world, ms), 3),
         "unit": "GB/s",
         "n_gpus": world,
         "steps": args.steps,
@@ -263,9 +308,7 @@ def run_ours(args, rank, world, local_rank):
         "encode_gbs": round(kern["encode"]["uncompressed_gbs"] * world, 2),
         "decode_gbs": round(kern["decode"]["uncompressed_gbs"] * world, 2),
         "kernels": kern,
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["gbs"], "peak": peak,
-                     "unit": "GB/s", "frac": kern[dom]["gbs"] / peak, "traffic": traffic,
-                     "peak_source": f"{peak_kind} hbm_gbs"},
+        "roofline": roof,
         "e2e": {"value": round(world * xb / e2e / 1e6, 3), "unit": "GB/s",
                 "h2d_bytes_per_step": xb, "d2h_bytes_per_step": er.bytes + pts.numel(),
                 "ms_per_step": round(e2e, 4)},
