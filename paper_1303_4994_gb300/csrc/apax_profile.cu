@@ -383,6 +383,38 @@ __device__ __forceinline__ void profile_run(const ProfArgs &a, uint64_t run, uin
         with_quant<DT>(Q, [&](const auto &qf) {
             Stream1 sm(s, carry_in<DT>(b, qf, 4 * b.g0));
             const int cD = -103 - b.Eb - k;  // f32: D' shift = bexp + cD
+            constexpr int QM = std::remove_reference_t<decltype(qf)>::kMode;
+            if constexpr (DT == 4 && QM == 1) {
+                // FMA form (k >= 1): T = x b + 1.5 2^23 rounded gives q; then
+                // r = x b - q is exact in one FMA (|r| <= 1/2 within 24 bits)
+                // and D' = r 2^24 is an integer whenever q != 0.
+                const float bsc = Q.scale;
+#pragma unroll 1
+                for (int g = b.g0; g < ge; ++g) {
+                    lt xv[4];
+                    load4<DT, true>(b, 4 * g, xv);
+                    const int nv = b.L - 4 * g;  // samples of the block from here
+                    uint32_t o = 0;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float xf = __uint_as_float(xv[i]);
+                        const float T = __fmaf_rn(xf, bsc, 12582912.0f);
+                        const uint32_t q = (uint32_t)(__float_as_int(T) - 0x4B400000);
+                        const int32_t u = (int32_t)(q - sm.a * sm.qp + sm.bb * sm.qpp);
+                        o |= bits_term(u);
+                        sm.qpp = sm.qp;
+                        sm.qp = q;
+                        const float r = __fmaf_rn(xf, bsc, -__fsub_rn(T, 12582912.0f));
+                        const int32_t Dp = __float2int_rn(__fmul_rn(r, 16777216.0f));
+                        const int32_t qs = i < nv ? (int32_t)q : 0;  // padding adds nothing
+                        sq += qs;
+                        sA += (int64_t)qs * qs;
+                        sB += (int64_t)qs * Dp;
+                    }
+                    tc.push(exp_from_or(o), true);
+                }
+                return;
+            }
 #pragma unroll 1
             for (int g = b.g0; g < ge; ++g) {
                 lt xv[4];

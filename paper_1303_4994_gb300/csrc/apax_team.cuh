@@ -203,6 +203,7 @@ struct Quant {
 // may take different modes.
 template <int DT, int M>
 struct QuantM {
+    static constexpr int kMode = M;
     const Quant<DT> &Q;
     __device__ __forceinline__ explicit QuantM(const Quant<DT> &q) : Q(q) {}
     __device__ __forceinline__ int32_t operator()(typename LaneT<DT>::t v) const
