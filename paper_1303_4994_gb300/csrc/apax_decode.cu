@@ -495,6 +495,153 @@ __device__ __forceinline__ void decode_tile(const DecArgs &a, const DecHdr &hd, 
     }
 }
 
+// One block by one thread (block sizes up to kT1MaxN): header, the JEE
+// tokens in order, then the mantissas, inverse derivatives and
+// dequantisation in one sequential pass -- no team scans.  eb is this
+// thread's column of exponent bytes (stride est).
+constexpr uint32_t kT1MaxN = 1024;
+
+template <int DT>
+__device__ __forceinline__ void decode_block_t1(const DecArgs &a, const DecHdr &hd, uint64_t j,
+                                                uint8_t *eb, int est)
+{
+    using T = DT_<DT>;
+    using raw = typename T::raw;
+    using lt = typename LaneT<DT>::t;
+    constexpr int W = T::W, H = T::H;
+    const uint32_t N = hd.N;
+    const uint64_t off = j * (uint64_t)N;
+    const int L = (int)((hd.n - off) < N ? (hd.n - off) : N);
+    const int G = (L + 3) >> 2;
+    const uint8_t *in = a.in;
+    const uint64_t start = hd.mode == 1
+                               ? 4ull * (uint64_t)__ldg(reinterpret_cast<const uint32_t *>(in + 40) + j)
+                               : j * (uint64_t)hd.B;
+    if (start >= hd.payload || (start & 3)) {
+        set_status(a.status, -9);
+        return;
+    }
+    const uint32_t *pw = reinterpret_cast<const uint32_t *>(in + hd.poff + start);
+    const uint64_t aw = (hd.payload - start) >> 2;
+    uint32_t nwords = (uint32_t)(aw > 0xffffffffull ? 0xffffffffull : aw);
+    bool bad = false;
+    auto word = [&](uint32_t i) -> uint32_t {
+        if (i >= nwords) {
+            bad = true;
+            return 0u;
+        }
+        return __ldg(pw + i);
+    };
+    const uint32_t h0 = word(0);
+    const int s = h0 & 3, code = (h0 >> 2) & 4095;
+    const uint32_t plen = h0 >> 14;
+    bad |= s == 3 || plen < 4 || (plen & 3) || (uint64_t)plen > 4ull * nwords;
+    if (hd.mode == 0 && j + 1 < hd.nb && plen != hd.B) bad = true;
+    if (bad) {
+        set_status(a.status, -9);
+        return;
+    }
+    nwords = plen >> 2;
+    int Eb = 0;
+    if (T::F) Eb = (int)(int16_t)(word(1) & 0xffffu);
+    // LSB-first bit window over the packet words
+    uint64_t acc = 0;
+    int fill = 0;
+    uint32_t wi = 0;
+    auto seek = [&](uint32_t bit) {  // bit <= 32 nwords; nothing is read at the very end
+        wi = bit >> 5;
+        acc = 0;
+        fill = 0;
+        if (wi < nwords) {
+            acc = (uint64_t)word(wi) >> (bit & 31);
+            fill = 32 - (int)(bit & 31);
+            ++wi;
+        }
+    };
+    auto take = [&](int k) -> uint32_t {  // 0 <= k <= 32
+        if (fill < k) {
+            acc |= (uint64_t)word(wi) << fill;
+            ++wi;
+            fill += 32;
+        }
+        const uint32_t v = (uint32_t)acc & (uint32_t)((1ull << k) - 1);
+        acc >>= k;
+        fill -= k;
+        return v;
+    };
+    // tokens (Sec. 6 JEE): absolute first, then joint / single / absolute
+    constexpr int lim = W >= 32 ? 32 : W;
+    seek((uint32_t)H);
+    int g = 0, ep = 0, nib = 0, sume = 0;
+    auto put = [&](int e) {
+        bad |= e < 0 || e > lim || e == 31;
+        e = e < 0 ? 0 : (e > 32 ? 32 : e);
+        eb[(size_t)g * est] = (uint8_t)e;
+        sume += e;
+        ep = e;
+        ++g;
+    };
+    while (g < G && !bad) {
+        const int nb = (int)take(4);
+        ++nib;
+        if (nb >= 14) {
+            const int v = ((nb - 14) << 4) | (int)take(4);
+            ++nib;
+            put(v == 31 ? 32 : v);
+        } else if (g == 0) {
+            bad = true;  // the first exponent is absolute
+        } else if (nb <= 8) {
+            if (g + 1 >= G) {
+                bad = true;  // a joint token needs two diffs
+            } else {
+                const int e1 = ep + nb / 3 - 1;
+                put(e1);
+                put(e1 + nb % 3 - 1);
+            }
+        } else {
+            put(ep + nb - 11);
+        }
+    }
+    if (!bad && (uint64_t)H + 4ull * (uint64_t)nib + 4ull * (uint64_t)sume > 8ull * plen) bad = true;
+    if (bad) {
+        set_status(a.status, -9);
+        return;
+    }
+    // values: fields, inverse derivative, dequantisation, 4 at a time
+    const Dequant<DT> DQ(code, Eb);
+    raw *yb = reinterpret_cast<raw *>(a.y) + (a.ranged ? (j - a.b0) * (uint64_t)N : off);
+    seek((uint32_t)H + 4u * (uint32_t)nib);
+    uint32_t run = 0, runD = 0, u0 = 0;
+#pragma unroll 1
+    for (int gg = 0; gg < G; ++gg) {
+        const int e = eb[(size_t)gg * est];
+        lt out[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t f = take(e);
+            const uint32_t uv = e == 0 ? 0u : (uint32_t)sext_w(f, e);
+            uint32_t q;
+            if (s == 0) {
+                q = uv;
+            } else if (s == 1) {
+                run += uv;
+                q = run;
+            } else {
+                if (gg == 0 && i == 0) {
+                    u0 = uv;
+                } else {
+                    run += uv;
+                }
+                runD += run;
+                q = u0 + runD;
+            }
+            out[i] = DQ(sext_w(q, W));
+        }
+        store4<DT>(yb, 4 * gg, L, out);
+    }
+    if (bad) set_status(a.status, -9);
+}
+
 // Size class of a container: teams of 32 for blocks above 4096 samples
 // (header errors are reported by the small class).
 template <int EB>
@@ -518,6 +665,15 @@ __global__ void __launch_bounds__(128) k_decode(DecArgs a)
     if (my_class<EB>(hd)) {
         if (hd.err) {
             if (threadIdx.x == 0) set_status(a.status, hd.err);
+        } else if (!LARGE && hd.N <= kT1MaxN) {
+            // a block per thread
+            const uint64_t jb = a.ranged ? a.b0 : 0, je = a.ranged ? a.b1 : hd.nb;
+            const uint64_t per = blockDim.x;
+            const uint64_t ntiles = (je - jb + per - 1) / per;
+            for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+                const uint64_t j = jb + tile * per + threadIdx.x;
+                if (j < je) decode_block_t1<DT>(a, hd, j, dsm + threadIdx.x, (int)blockDim.x);
+            }
         } else {
             const int nteams = blockDim.x / TS;
             const uint64_t jb = a.ranged ? a.b0 : 0, je = a.ranged ? a.b1 : hd.nb;
@@ -623,7 +779,8 @@ template <int DT, int TS, int EB>
 static cudaError_t launch_one(const DecArgs &a, unsigned ctas, cudaStream_t s)
 {
     constexpr int threads = 128;
-    const size_t smem = (size_t)(threads / TS) * EB;
+    size_t smem = (size_t)(threads / TS) * EB;
+    if (EB <= 1024 && smem < (size_t)threads * (kT1MaxN / 4)) smem = (size_t)threads * (kT1MaxN / 4);
     auto k = k_decode<DT, TS, EB>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
