@@ -544,25 +544,30 @@ __device__ __forceinline__ void decode_block_t1(const DecArgs &a, const DecHdr &
     nwords = plen >> 2;
     int Eb = 0;
     if (T::F) Eb = (int)(int16_t)(word(1) & 0xffffu);
-    // LSB-first bit window over the packet words
+    // LSB-first bit window over the packet words, with the next word loaded
+    // one refill ahead (its latency overlaps the fields before it is needed)
     uint64_t acc = 0;
     int fill = 0;
-    uint32_t wi = 0;
+    uint32_t wi = 0, nxt = 0;
+    auto peek = [&](uint32_t i) -> uint32_t { return i < nwords ? __ldg(pw + i) : 0u; };
     auto seek = [&](uint32_t bit) {  // bit <= 32 nwords; nothing is read at the very end
         wi = bit >> 5;
         acc = 0;
         fill = 0;
         if (wi < nwords) {
-            acc = (uint64_t)word(wi) >> (bit & 31);
+            acc = (uint64_t)__ldg(pw + wi) >> (bit & 31);
             fill = 32 - (int)(bit & 31);
             ++wi;
         }
+        nxt = peek(wi);
     };
     auto take = [&](int k) -> uint32_t {  // 0 <= k <= 32
         if (fill < k) {
-            acc |= (uint64_t)word(wi) << fill;
+            bad |= wi >= nwords;  // past the packet
+            acc |= (uint64_t)nxt << fill;
             ++wi;
             fill += 32;
+            nxt = peek(wi);
         }
         const uint32_t v = (uint32_t)acc & (uint32_t)((1ull << k) - 1);
         acc >>= k;
@@ -666,11 +671,18 @@ __global__ void __launch_bounds__(128) k_decode(DecArgs a)
         if (hd.err) {
             if (threadIdx.x == 0) set_status(a.status, hd.err);
         } else if (!LARGE && hd.N <= kT1MaxN) {
-            // a block per thread
+            // a block per thread; CTAs take tiles of blockDim.x blocks from a
+            // counter (blocks differ in cost, a static stride leaves a tail)
             const uint64_t jb = a.ranged ? a.b0 : 0, je = a.ranged ? a.b1 : hd.nb;
             const uint64_t per = blockDim.x;
             const uint64_t ntiles = (je - jb + per - 1) / per;
-            for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            __shared__ uint64_t s_tile;
+            while (true) {
+                __syncthreads();
+                if (threadIdx.x == 0) s_tile = atomicAdd(a.ticket, 1ull);
+                __syncthreads();
+                const uint64_t tile = s_tile;
+                if (tile >= ntiles) break;
                 const uint64_t j = jb + tile * per + threadIdx.x;
                 if (j < je) decode_block_t1<DT>(a, hd, j, dsm + threadIdx.x, (int)blockDim.x);
             }

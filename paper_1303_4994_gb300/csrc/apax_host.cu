@@ -171,6 +171,7 @@ int decode_impl(const void *in, uint64_t in_bytes, uint64_t b0, uint64_t b1, boo
     a.ranged = ranged;
     uint8_t *w = (uint8_t *)ws;
     a.done = (unsigned *)(w + 16);
+    a.ticket = (unsigned long long *)(w + 24);
     a.status = (int *)(w + 8);
     a.res = res;
     int dev = 0, sms = 152;

@@ -57,6 +57,7 @@ struct DecArgs {
     uint64_t b0, b1;    // block range to decode
     bool ranged;        // y receives blocks [b0, b1) from y[0]
     unsigned *done;     // two completion counters (one per size class)
+    unsigned long long *ticket;  // tile counter of the block-per-thread mode
     int *status;
     unsigned nctas, nctas_large;
     apax_result *res;
