@@ -95,7 +95,7 @@ int fill_prof_args(const void *x, int dtype, uint64_t n, uint32_t block_size,
     a.ncand = ncand;
     for (int i = 0; i < ncand; ++i) a.codes[i] = candidates[i];
     a.nruns = (nb + 15) / 16;
-    a.gp = (int)((block_size / 4 + 7) / 8);  // teams of 8 threads
+    a.gp = (int)((block_size / 4 + kProfTS - 1) / kProfTS);  // groups per team thread
     a.target = target;
     a.points = points;
     a.summary = summary;

@@ -75,6 +75,9 @@ struct DecBatchArgs {
     unsigned long long *ticket;
 };
 
+// Profiler team size: threads per codec block (16 blocks per CTA).
+constexpr int kProfTS = 8;
+
 struct ProfArgs {
     const void *x;
     uint64_t n;

@@ -31,7 +31,8 @@ namespace apax {
 
 namespace {
 
-constexpr int TS = 8;
+constexpr int TS = kProfTS;
+static_assert(TS >= 8, "the exact fallback rounds its six sums on team threads 0..5");
 constexpr int kRun = 16;   // blocks per CTA = one tree node
 constexpr int kWin = 200;  // f64: window LSB = 2^(2 Eb - kWin) for sum x^2
 
@@ -130,7 +131,7 @@ __device__ void fallback_team(const TBlock<DT> &b, int code, bool want_block,
     using T = DT_<DT>;
     constexpr int ND = PS<DT>::ND, LO = PS<DT>::LO;
     const int t = tlane<TS>();
-    const unsigned tm = 0xffu << (lane_id() & ~7u);
+    const unsigned tm = ((1u << TS) - 1u) << (lane_id() & ~(unsigned)(TS - 1));
     if (me) {
         for (int i = t; i < 6 * ND; i += TS) accmem[i] = 0;
         __syncwarp(tm);
