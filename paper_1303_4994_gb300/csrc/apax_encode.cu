@@ -118,6 +118,125 @@ struct NibWriter {
     }
 };
 
+// Decoupled look-back (warp 0, every lane): publish this tile's aggregate,
+// then read 32 predecessors per probe (lane l reads tile base - l); the
+// nearest inclusive prefix ends the walk.  Returns the exclusive prefix.
+__device__ __forceinline__ uint64_t lookback(const EncArgs &a, uint64_t tile, uint32_t total)
+{
+    const int l = threadIdx.x & 31;
+    const bool hook = a.test_stall_tile == (long long)tile;
+    uint64_t excl = 0;
+    if (tile == 0) {
+        if (l == 0 && !hook) atomicExch(a.tiles, kFlagP | total);
+        return 0;
+    }
+    if (l == 0 && !hook) atomicExch(a.tiles + tile, kFlagA | total);
+    int64_t base = (int64_t)tile - 1;
+    while (true) {
+        const int64_t tt = base - l;
+        const uint64_t st = tt >= 0 ? wait_tile(a.tiles, (uint64_t)tt, a.spin_limit, a.status) : kFlagP;
+        const unsigned pm = __ballot_sync(kFull, (st & ~kValMask) == kFlagP);
+        const int near = pm ? __ffs(pm) - 1 : 31;
+        uint64_t val = l <= near ? (st & kValMask) : 0;
+#pragma unroll
+        for (int m = 16; m >= 1; m >>= 1) val += __shfl_xor_sync(kFull, val, m);
+        excl += val;
+        if (pm) break;
+        base -= 32;
+    }
+    if (l == 0 && !hook) atomicExch(a.tiles + tile, kFlagP | ((excl + total) & kValMask));
+    return excl;
+}
+
+// Writes the Sec. 6 JEE tokens of groups [g0, g1) of a block of G groups
+// whose exponents are eb[g * est]; s_in: the group before g0 opened a joint
+// token that g0 completes.
+template <class Wr>
+__device__ __forceinline__ void write_tokens(Wr &nw, const uint8_t *eb, int est, int g0, int g1, int G,
+                                             bool s_in)
+{
+    bool st = s_in;
+    int eprev = g0 > 0 && g0 < G ? eb[(size_t)(g0 - 1) * est] : 0;
+#pragma unroll 1
+    for (int g = g0; g < g1; ++g) {
+        const int e = eb[(size_t)g * est];
+        if (g == 0) {
+            nw.put(abs_token(e), 8);
+            st = false;
+        } else {
+            const int d = e - eprev;
+            if ((unsigned)(d + 1) <= 2u) {
+                if (st) {
+                    st = false;  // second diff of the previous joint token
+                } else {
+                    const int dn = g + 1 < G ? (int)eb[(size_t)(g + 1) * est] - e : 99;
+                    if ((unsigned)(dn + 1) <= 2u) nw.put((uint32_t)(3 * (d + 1) + (dn + 1)), 4);
+                    else nw.put((uint32_t)(11 + d), 4);
+                    st = true;
+                }
+            } else {
+                if ((unsigned)(d + 2) <= 4u) nw.put((uint32_t)(11 + d), 4);
+                else nw.put(abs_token(e), 8);
+                st = false;
+            }
+        }
+        eprev = e;
+    }
+}
+
+// Appends one group's four e-bit fields in as few wide pieces as fit.
+template <class Wr>
+__device__ __forceinline__ void write_group_fields(Wr &mw, int e, const int32_t (&u)[4])
+{
+    if (!e) return;
+    const uint32_t m = e >= 32 ? 0xffffffffu : ((1u << e) - 1u);
+    const uint32_t f0 = (uint32_t)u[0] & m, f1 = (uint32_t)u[1] & m, f2 = (uint32_t)u[2] & m,
+                   f3 = (uint32_t)u[3] & m;
+    if (e <= 8) {
+        mw.put(f0 | (f1 << e) | (f2 << (2 * e)) | (f3 << (3 * e)), 4 * e);
+    } else if (e <= 16) {
+        mw.put(f0 | (f1 << e), 2 * e);
+        mw.put(f2 | (f3 << e), 2 * e);
+    } else {
+        mw.put(f0, e);
+        mw.put(f1, e);
+        mw.put(f2, e);
+        mw.put(f3, e);
+    }
+}
+
+// A packet written by its only owner straight to global memory: complete
+// words are stored as they fill.
+struct GWriter {
+    uint32_t *dst;
+    uint64_t acc;
+    int fill;
+    uint32_t w;
+    __device__ __forceinline__ void start(uint32_t *d)
+    {
+        dst = d;
+        acc = 0;
+        fill = 0;
+        w = 0;
+    }
+    __device__ __forceinline__ void put(uint32_t v, int nbits)
+    {
+        acc |= (uint64_t)v << fill;
+        fill += nbits;
+        if (fill >= 32) {
+            dst[w++] = (uint32_t)acc;
+            acc >>= 32;
+            fill -= 32;
+        }
+    }
+    __device__ __forceinline__ void flush()
+    {
+        if (fill > 0) dst[w++] = (uint32_t)acc;
+        acc = 0;
+        fill = 0;
+    }
+};
+
 // ---------------------------------------------------------------- tile body
 // One tile (nteams consecutive blocks) of the array described by `a`.
 // Called by every thread of the CTA; `smem` holds the teams' packet images.
@@ -225,33 +344,7 @@ __device__ __forceinline__ void encode_tile(const EncArgs &a, uint64_t tile, uin
         // tokens of my groups (Sec. 6 JEE), starting at my nibble offset
         NibWriter nw;
         nw.start(pkt, (uint32_t)H + 4u * (uint32_t)nib_before);
-        bool st = s_in;
-        int eprev = b.g0 > 0 && b.g0 < b.G ? ebuf[b.g0 - 1] : 0;
-#pragma unroll 1
-        for (int g = b.g0; g < b.g1; ++g) {
-            const int e = ebuf[g];
-            if (g == 0) {
-                nw.put(abs_token(e), 8);
-                st = false;
-            } else {
-                const int d = e - eprev;
-                if ((unsigned)(d + 1) <= 2u) {
-                    if (st) {
-                        st = false;  // second diff of the previous joint token
-                    } else {
-                        const int dn = g + 1 < b.G ? (int)ebuf[g + 1] - e : 99;
-                        if ((unsigned)(dn + 1) <= 2u) nw.put((uint32_t)(3 * (d + 1) + (dn + 1)), 4);
-                        else nw.put((uint32_t)(11 + d), 4);
-                        st = true;
-                    }
-                } else {
-                    if ((unsigned)(d + 2) <= 4u) nw.put((uint32_t)(11 + d), 4);
-                    else nw.put(abs_token(e), 8);
-                    st = false;
-                }
-            }
-            eprev = e;
-        }
+        write_tokens(nw, ebuf, 1, b.g0, b.g1, b.G, s_in);
         nw.flush();
         // mantissas of my groups after the token section
         NibWriter mw;
@@ -264,24 +357,7 @@ __device__ __forceinline__ void encode_tile(const EncArgs &a, uint64_t tile, uin
                 load4<DT, true>(b, 4 * g, xv);
                 int32_t u[4];
                 group1<DT>(qf, xv, sm, u);
-                const int e = ebuf[g];
-                if (e) {
-                    // the group's four e-bit fields, appended as few wide pieces
-                    const uint32_t m = e >= 32 ? 0xffffffffu : ((1u << e) - 1u);
-                    const uint32_t f0 = (uint32_t)u[0] & m, f1 = (uint32_t)u[1] & m,
-                                   f2 = (uint32_t)u[2] & m, f3 = (uint32_t)u[3] & m;
-                    if (e <= 8) {
-                        mw.put(f0 | (f1 << e) | (f2 << (2 * e)) | (f3 << (3 * e)), 4 * e);
-                    } else if (e <= 16) {
-                        mw.put(f0 | (f1 << e), 2 * e);
-                        mw.put(f2 | (f3 << e), 2 * e);
-                    } else {
-                        mw.put(f0, e);
-                        mw.put(f1, e);
-                        mw.put(f2, e);
-                        mw.put(f3, e);
-                    }
-                }
+                write_group_fields(mw, ebuf[g], u);
             }
         });
         mw.flush();
@@ -299,30 +375,7 @@ __device__ __forceinline__ void encode_tile(const EncArgs &a, uint64_t tile, uin
             const uint32_t total = __shfl_sync(kFull, incl, 31);
             __syncwarp();
             if (l < nteams) s_words[l] = incl - v;
-            // decoupled look-back, 32 predecessors per probe: lane l reads
-            // tile base - l; the nearest inclusive prefix ends the walk
-            const bool hook = a.test_stall_tile == (long long)tile;
-            uint64_t excl = 0;
-            if (tile == 0) {
-                if (l == 0 && !hook) atomicExch(a.tiles, kFlagP | total);
-            } else {
-                if (l == 0 && !hook) atomicExch(a.tiles + tile, kFlagA | total);
-                int64_t base = (int64_t)tile - 1;
-                while (true) {
-                    const int64_t tt = base - l;
-                    const uint64_t st = tt >= 0 ? wait_tile(a.tiles, (uint64_t)tt, a.spin_limit, a.status)
-                                                : kFlagP;
-                    const unsigned pm = __ballot_sync(kFull, (st & ~kValMask) == kFlagP);
-                    const int near = pm ? __ffs(pm) - 1 : 31;
-                    uint64_t val = l <= near ? (st & kValMask) : 0;
-#pragma unroll
-                    for (int m = 16; m >= 1; m >>= 1) val += __shfl_xor_sync(kFull, val, m);
-                    excl += val;
-                    if (pm) break;
-                    base -= 32;
-                }
-                if (l == 0 && !hook) atomicExch(a.tiles + tile, kFlagP | ((excl + total) & kValMask));
-            }
+            const uint64_t excl = lookback(a, tile, total);
             if (l == 0) s_base = excl;
         }
         __syncthreads();
@@ -372,6 +425,174 @@ __device__ __forceinline__ void encode_tile(const EncArgs &a, uint64_t tile, uin
             }
         }
     }
+}
+
+// ---------------------------------------------------------------- block per thread
+// A tile of blockDim.x blocks, one per thread (block sizes up to
+// kT1MaxBlock): the team functions run with a team of one, exponents sit in
+// a lane-interleaved shared-memory column (smem bytes g * blockDim.x +
+// thread), and each thread writes its own packet straight to global memory
+// once the CTA-wide scan and the look-back have placed it.
+constexpr uint32_t kT1MaxBlock = 1024;
+
+template <int DT, int MODE>
+__device__ __forceinline__ void encode_tile_t1(const EncArgs &a, uint64_t tile, uint8_t *smem)
+{
+    __shared__ uint32_t s_wt[32];
+    __shared__ uint64_t s_base;
+    using T = DT_<DT>;
+    using raw = typename T::raw;
+    using lt = typename LaneT<DT>::t;
+    constexpr int H = T::H;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const uint64_t j = tile * (uint64_t)nt + (uint64_t)tid;
+    int code = (int)a.code;
+    if (a.code_dev) code = (int)*a.code_dev;
+    uint8_t *eb = smem + tid;  // exponent of group g at eb[g * nt]
+    if (tile == 0 && tid == 0) write_container_header(a, code);
+    const raw *x = reinterpret_cast<const raw *>(a.x);
+    // stream decision: best(j-1) at code 0 (block 0 uses its own)
+    int s;
+    {
+        TBlock<DT> pv;
+        open_team_block<DT, 1>(pv, x, a.n, a.N, a.nb, j == 0 ? 0 : j - 1, a.gp);
+        uint32_t bb[3];
+        team_eval3<DT, 1>(pv, 0, bb);
+        s = 0;
+        if (bb[1] < bb[s]) s = 1;
+        if (bb[2] < bb[s]) s = 2;
+    }
+    TBlock<DT> b;
+    open_team_block<DT, 1>(b, x, a.n, a.N, a.nb, j, a.gp);
+    if (b.active && b.bad) set_status(a.status, -8);
+    uint32_t plen = 0;
+    if (MODE == 0) {
+        const uint32_t budget = b.L == (int)a.N ? a.B : fr_budget<DT>(b.L, a.rate_num, a.rate_den);
+        const bool fits0 = pad32_bytes(team_eval1<DT, 1>(b, 0, s)) <= budget;
+        int lo = 0, hi = 4095;
+        if (!fits0) {
+#pragma unroll 1
+            for (int it = 0; it < 12 && hi - lo > 1; ++it) {  // 12 halvings close [0, 4095]
+                const int mid = (lo + hi) >> 1;
+                if (pad32_bytes(team_eval1<DT, 1>(b, mid, s)) <= budget) hi = mid;
+                else lo = mid;
+            }
+        }
+        code = fits0 ? 0 : hi;
+        plen = budget;
+    }
+    // final pass: exponents into the column, token count
+    const Quant<DT> Q(code, b.Eb);
+    TokCount tc;
+    tc.init();
+    with_quant<DT>(Q, [&](const auto &qf) {
+        Stream1 st(s, carry_in<DT>(b, qf, 0));
+#pragma unroll 1
+        for (int g = 0; g < b.G; ++g) {
+            lt xv[4];
+            load4<DT, true>(b, 4 * g, xv);
+            int32_t u[4];
+            const int e = exp_from_or(group1<DT>(qf, xv, st, u));
+            eb[(size_t)g * nt] = (uint8_t)e;
+            tc.push(e, true);
+        }
+    });
+    int nib, sume;
+    team_tokens<1>(tc, true, nib, sume);
+    const uint32_t bits = (uint32_t)H + 4u * (uint32_t)nib + 4u * (uint32_t)sume;
+    if (MODE == 1) plen = pad32_bytes(bits);
+    const uint32_t words = b.active ? plen >> 2 : 0;
+
+    uint64_t off_words;
+    if (MODE == 1) {
+        // CTA-wide exclusive scan of the packet words, then the look-back
+        const uint32_t incl = warp_incl_scan(words);
+        if (lane == 31) s_wt[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const int nw = nt >> 5;
+            const uint32_t v = lane < nw ? s_wt[lane] : 0;
+            const uint32_t wi = warp_incl_scan(v);
+            const uint32_t total = __shfl_sync(kFull, wi, 31);
+            __syncwarp();
+            if (lane < nw) s_wt[lane] = wi - v;
+            const uint64_t excl = lookback(a, tile, total);
+            if (lane == 0) s_base = excl;
+        }
+        __syncthreads();
+        off_words = s_base + s_wt[warp] + (incl - words);
+    } else {
+        off_words = j * (uint64_t)(a.B >> 2);
+    }
+
+    if (b.active) {
+        const uint64_t start = a.poff + 4ull * off_words;
+        if (MODE == 1) {
+            if (off_words > 0xffffffffull) {
+                set_status(a.status, -6);
+            } else {
+                reinterpret_cast<uint32_t *>(a.out + 40)[j] = (uint32_t)off_words;
+                if (j == a.nb - 1 && (a.nb & 1)) reinterpret_cast<uint32_t *>(a.out + 40)[j + 1] = 0;
+            }
+        }
+        if (start + 4ull * words > a.cap) {
+            set_status(a.status, -5);
+        } else {
+            GWriter w;
+            w.start(reinterpret_cast<uint32_t *>(a.out + start));
+            w.put((uint32_t)s | ((uint32_t)code << 2) | (plen << 14), 32);
+            if (H == 48) w.put((uint32_t)(uint16_t)(int16_t)b.Eb, 16);
+            write_tokens(w, eb, nt, 0, b.G, b.G, false);
+            with_quant<DT>(Q, [&](const auto &qf) {
+                Stream1 sm(s, carry_in<DT>(b, qf, 0));
+#pragma unroll 1
+                for (int g = 0; g < b.G; ++g) {
+                    lt xv[4];
+                    load4<DT, true>(b, 4 * g, xv);
+                    int32_t u[4];
+                    group1<DT>(qf, xv, sm, u);
+                    write_group_fields(w, eb[(size_t)g * nt], u);
+                }
+            });
+            w.flush();
+            while (w.w < words) w.dst[w.w++] = 0u;  // padding (fixed rate)
+        }
+    }
+
+    // completion: the CTA that finishes the array's last tile writes the
+    // payload size and the result
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(a.done, 1u);
+        if (prev == a.ntiles - 1) {
+            __threadfence();
+            uint64_t payload;
+            if (MODE == 1) {
+                volatile unsigned long long *last = a.tiles + (a.ntiles - 1);
+                payload = 4ull * ((uint64_t)(*last) & kValMask);
+            } else {
+                payload = a.fr_payload;
+            }
+            put_le(a.out + 28, payload, 8);
+            volatile int *st = a.status;
+            if (a.res) {
+                a.res->bytes = a.poff + payload;
+                a.res->status = *st;
+            }
+        }
+    }
+}
+
+template <int DT, int MODE>
+__global__ void __launch_bounds__(128) k_encode_t1(EncArgs a)
+{
+    extern __shared__ uint32_t smem[];
+    __shared__ uint64_t s_tile;
+    if (threadIdx.x == 0) s_tile = MODE == 1 ? (uint64_t)atomicAdd(a.ticket, 1u) : blockIdx.x;
+    __syncthreads();
+    encode_tile_t1<DT, MODE>(a, s_tile, reinterpret_cast<uint8_t *>(smem));
 }
 
 // ---------------------------------------------------------------- kernels
@@ -463,8 +684,19 @@ static cudaError_t launch_ts(const EncArgs &a, int threads, size_t smem, cudaStr
 }
 
 template <int DT>
+static cudaError_t launch_t1(const EncArgs &a, int threads, size_t smem, cudaStream_t s)
+{
+    auto k = a.mode == 1 ? k_encode_t1<DT, 1> : k_encode_t1<DT, 0>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<(unsigned)a.ntiles, threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int DT>
 static cudaError_t launch_dt(const EncArgs &a, int ts, int threads, size_t smem, cudaStream_t s)
 {
+    if (ts == 1) return launch_t1<DT>(a, threads, smem, s);
     return ts == 8 ? launch_ts<DT, 8>(a, threads, smem, s) : launch_ts<DT, 32>(a, threads, smem, s);
 }
 

@@ -18,14 +18,33 @@ namespace apax {
 template <int TS>
 __device__ __forceinline__ int tlane() { return (int)(lane_id() & (TS - 1)); }
 
+// Team shuffles (width TS, every lane of the warp takes part).  A team of
+// one thread exchanges nothing: its shuffles are the identity, so code that
+// runs per thread (and may diverge) calls no warp collective.
 template <int TS, typename T>
-__device__ __forceinline__ T tshfl(T v, int src) { return __shfl_sync(kFull, v, src, TS); }
+__device__ __forceinline__ T tshfl(T v, int src)
+{
+    if constexpr (TS == 1) return v;
+    else return __shfl_sync(kFull, v, src, TS);
+}
 template <int TS, typename T>
-__device__ __forceinline__ T tshfl_up(T v, int d) { return __shfl_up_sync(kFull, v, d, TS); }
+__device__ __forceinline__ T tshfl_up(T v, int d)
+{
+    if constexpr (TS == 1) return v;
+    else return __shfl_up_sync(kFull, v, d, TS);
+}
 template <int TS, typename T>
-__device__ __forceinline__ T tshfl_down(T v, int d) { return __shfl_down_sync(kFull, v, d, TS); }
+__device__ __forceinline__ T tshfl_down(T v, int d)
+{
+    if constexpr (TS == 1) return v;
+    else return __shfl_down_sync(kFull, v, d, TS);
+}
 template <int TS, typename T>
-__device__ __forceinline__ T tshfl_xor(T v, int m) { return __shfl_xor_sync(kFull, v, m, TS); }
+__device__ __forceinline__ T tshfl_xor(T v, int m)
+{
+    if constexpr (TS == 1) return v;
+    else return __shfl_xor_sync(kFull, v, m, TS);
+}
 
 template <int TS, typename T>
 __device__ __forceinline__ T team_sum(T v)
