@@ -186,6 +186,73 @@ __host__ __device__ inline size_t profile_stage_bytes(size_t elem, uint32_t N, s
     return (bytes <= 48 * 1024 && smem_before + bytes <= 100 * 1024) ? bytes : 0;
 }
 
+// Three float32 candidates with k >= 1 (FMA form, see the candidate loop)
+// in one walk over the thread's groups: one load per group, the three JEE
+// counters in the lanes of one register.  Every lane of the warp calls it.
+template <typename Stage>
+__device__ __forceinline__ void profile_chunk3(const TBlock<4> &b, int s, int ge, const uint32_t *codes,
+                                               Stage *cs, int t)
+{
+    using lt = typename LaneT<4>::t;
+    constexpr int H = DT_<4>::H;
+    float bs[3];
+    uint32_t qp[3], qpp[3];
+    int64_t sq[3], sA[3], sB[3];
+    const uint32_t ca = s == 0 ? 0u : (s == 1 ? 1u : 2u), cb = s == 2 ? 1u : 0u;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const Quant<4> Q((int)codes[j], b.Eb);
+        bs[j] = Q.scale;
+        const Carry c = carry_in<4>(b, QuantM<4, 1>(Q), 4 * b.g0);
+        qp[j] = s == 1 ? c.qp1 : c.qp2;
+        qpp[j] = c.qpp2;
+        sq[j] = sA[j] = sB[j] = 0;
+    }
+    Tok3 tk;
+    tk.init();
+#pragma unroll 1
+    for (int g = b.g0; g < ge; ++g) {
+        lt xv[4];
+        load4<4, true>(b, 4 * g, xv);
+        const int nv = b.L - 4 * g;
+        uint32_t o[3] = {0u, 0u, 0u};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float xf = __uint_as_float(xv[i]);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const float T = __fmaf_rn(xf, bs[j], 12582912.0f);
+                const uint32_t q = (uint32_t)(__float_as_int(T) - 0x4B400000);
+                o[j] |= bits_term((int32_t)(q - ca * qp[j] + cb * qpp[j]));
+                qpp[j] = qp[j];
+                qp[j] = q;
+                const float r = __fmaf_rn(xf, bs[j], -__fsub_rn(T, 12582912.0f));
+                const int32_t Dp = __float2int_rn(__fmul_rn(r, 16777216.0f));
+                const int32_t qs = i < nv ? (int32_t)q : 0;
+                sq[j] += qs;
+                sA[j] += (int64_t)qs * qs;
+                sB[j] += (int64_t)qs * Dp;
+            }
+        }
+        // |u| < 2^25 here, so no width reaches 31
+        tk.push(32 - __clz(o[0]), 32 - __clz(o[1]), 32 - __clz(o[2]));
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        int nib, sume;
+        team_tokens<TS>(tk.lane(j), b.g0 == 0, nib, sume);
+        const int64_t rq = team_sum_i64(sq[j]), rA = team_sum_i64(sA[j]), rB = team_sum_i64(sB[j]);
+        if (t == 0) {
+            cs[j].sq = rq;
+            cs[j].A = rA;
+            cs[j].B = rB;
+            cs[j].D = 0;
+            cs[j].bits = (uint32_t)H + 4u * (uint32_t)nib + 4u * (uint32_t)sume;
+            cs[j].fast = 1;
+        }
+    }
+}
+
 // One run (kRun consecutive blocks, a level-1 node of the summation tree):
 // the CTA's teams take one block each and write the run's partial sums.
 template <int DT>
@@ -370,6 +437,23 @@ __device__ __forceinline__ void profile_run(const ProfArgs &a, uint64_t run, uin
     uint32_t fbmask = tiny ? 1u : 0u;
 #pragma unroll 1
     for (int ci = 0; ci < nc; ++ci) {
+        if constexpr (DT == 4) {
+            // three float32 candidates in one walk (FMA form, all k >= 1, no
+            // fallback); warp-uniform, so the team collectives stay in step
+            if (ci + 3 <= nc) {
+                bool ok = !tiny && b.Eb >= -80;
+#pragma unroll
+                for (int jj = 0; jj < 3; ++jj) {
+                    const int cd = (int)a.codes[ci + jj];
+                    ok &= Quant<DT>(cd, b.Eb).mode == 1 && b.Eb + (cd >> 7) <= 127;
+                }
+                if (__all_sync(kFull, ok || !b.active)) {
+                    profile_chunk3(b, s, ge, &a.codes[ci], cs + ci, t);
+                    ci += 2;
+                    continue;
+                }
+            }
+        }
         const int code = (int)a.codes[ci];
         const int k = code >> 7;
         const Quant<DT> Q(code, b.Eb);
