@@ -17,6 +17,7 @@ Other workloads (one GPU):
   batched  8,192 arrays (4 KB..64 MB, int16/int32/float32/float64, fixed
            rates 2:1..6:1, 56.6 GB): one persistent launch each for encode,
            decode and the profiler sweep, against the plain per-array loop.
+  sensor   int16 trace at 4:1: single-call latency, and GB/s on 8,192 copies.
   serving  Poisson arrivals (2,000 requests/s, 50/50 encode/decode, 64 KB..
            256 MB of float32 field slices at a fixed quality or int16 traces
            at 4:1) through the request server with a 64 GB admission cap:
@@ -491,6 +492,80 @@ def run_batched(args):
     }
 
 
+def run_sensor(args):
+    """int16 sensor trace at 4:1: single-call latency of the 262,144-sample
+    trace, and throughput on a 4 GiB array of 8,192 copies (cold L2)."""
+    import torch
+
+    from paper_1303_4994_gb300 import apax as A
+    from paper_1303_4994_gb300 import build as B
+    from paper_1303_4994_gb300 import synth
+
+    B.build()
+    A.lib()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    p = A.params(N_BLOCK, A.FIXED_RATE, (4, 1), 0)
+    t = torch.from_numpy(synth.sensor_trace()).to(dev)
+
+    def bufs(x):
+        cap = A.encoded_size(A.I16, x.numel(), p)
+        return (torch.empty(cap, dtype=torch.uint8, device=dev),
+                torch.empty(A.workspace_size(A.I16, x.numel(), p), dtype=torch.uint8, device=dev),
+                torch.empty(A.decode_workspace_size(), dtype=torch.uint8, device=dev),
+                torch.empty_like(x), A.new_result(dev), A.new_result(dev))
+
+    def timed(fn, reps):
+        ts = []
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.mean(ts))
+
+    out, ews, dws, y, er, dr = bufs(t)
+    for _ in range(max(args.warmup, 3)):
+        A.encode_into(t, p, out, ews, er, stream)
+        A.decode_into(out, y, dws, dr, stream)
+    torch.cuda.synchronize()
+    lat_enc = timed(lambda: A.encode_into(t, p, out, ews, er, stream), max(args.steps, 20))
+    lat_dec = timed(lambda: A.decode_into(out, y, dws, dr, stream), max(args.steps, 20))
+    assert A.read_result(er).status == 0 and A.read_result(dr).status == 0
+    xr = t.repeat(8192)
+    out, ews, dws, y, er, dr = bufs(xr)
+    for _ in range(max(args.warmup, 3)):
+        A.encode_into(xr, p, out, ews, er, stream)
+        A.decode_into(out, y, dws, dr, stream)
+    torch.cuda.synchronize()
+    with Clocks(0) as clk:
+        ms_enc = timed(lambda: A.encode_into(xr, p, out, ews, er, stream), args.steps)
+        ms_dec = timed(lambda: A.decode_into(out, y, dws, dr, stream), args.steps)
+    xb, cb = xr.numel() * 2, A.read_result(er).bytes
+    peak, peak_kind = _peaks()
+    enc_gbs, dec_gbs = (xb + cb) / ms_enc / 1e6, (xb + cb) / ms_dec / 1e6
+    return {
+        "metric": METRIC, "value": round(xb / (ms_enc + ms_dec) / 1e6, 3), "unit": "GB/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 3),
+        "ms_per_step": round(ms_enc + ms_dec, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "i16", "data": "synthetic",
+        "config": {"workload": "int16 sensor trace (262,144 samples, seed 0), fixed rate 4:1, N=256; "
+                               "throughput on 8,192 copies (4 GiB)", "l2": "inputs larger than L2"},
+        "single_call_us": {"encode": round(lat_enc * 1e3, 2), "decode": round(lat_dec * 1e3, 2)},
+        "single_call_gbs": {"encode": round(t.numel() * 2 / lat_enc / 1e6, 2),
+                            "decode": round(t.numel() * 2 / lat_dec / 1e6, 2)},
+        "replica_gbs_uncompressed": {"encode": round(xb / ms_enc / 1e6, 2),
+                                     "decode": round(xb / ms_dec / 1e6, 2)},
+        "roofline": {"bound": "hbm", "encode_frac": enc_gbs / peak, "decode_frac": dec_gbs / peak,
+                     "peak": peak, "unit": "GB/s", "peak_source": f"{peak_kind} hbm_gbs"},
+        "ratio": round(xb / cb, 4),
+        "clocks": clk.summary(),
+    }
+
+
 def run_serving(args):
     import torch
 
@@ -611,14 +686,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="field", choices=["field", "batched", "serving"])
+    ap.add_argument("--workload", default="field", choices=["field", "batched", "serving", "sensor"])
     ap.add_argument("--arrays", type=int, default=8192)
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     args = ap.parse_args()
     if args.workload != "field" and args.impl == "ours":
         import torch
         torch.cuda.set_device(0)
-        line = run_batched(args) if args.workload == "batched" else run_serving(args)
+        line = {"batched": run_batched, "serving": run_serving, "sensor": run_sensor}[args.workload](args)
         print(json.dumps(line))
         return
     rank = int(os.environ.get("RANK", 0))

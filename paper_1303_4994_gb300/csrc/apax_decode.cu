@@ -500,6 +500,7 @@ __device__ __forceinline__ void decode_tile(const DecArgs &a, const DecHdr &hd, 
 // dequantisation in one sequential pass -- no team scans.  eb is this
 // thread's column of exponent bytes (stride est).
 constexpr uint32_t kT1MaxN = 1024;
+constexpr uint64_t kT1MinBlocks = 32768;  // fewer blocks leave SMs idle: use teams
 
 template <int DT>
 __device__ __forceinline__ void decode_block_t1(const DecArgs &a, const DecHdr &hd, uint64_t j,
@@ -670,7 +671,8 @@ __global__ void __launch_bounds__(128) k_decode(DecArgs a)
     if (my_class<EB>(hd)) {
         if (hd.err) {
             if (threadIdx.x == 0) set_status(a.status, hd.err);
-        } else if (!LARGE && hd.N <= kT1MaxN) {
+        } else if (!LARGE && hd.N <= kT1MaxN &&
+                   (a.ranged ? a.b1 - a.b0 : hd.nb) >= kT1MinBlocks) {
             // a block per thread; CTAs take tiles of blockDim.x blocks from a
             // counter (blocks differ in cost, a static stride leaves a tail)
             const uint64_t jb = a.ranged ? a.b0 : 0, je = a.ranged ? a.b1 : hd.nb;

@@ -1,0 +1,108 @@
+"""Parity at the benchmark's full sizes, in the launch configuration bench.py
+times: the GPU runs the whole array; the oracle checks sampled blocks one by
+one, and properties that hold at any size are checked on everything.
+
+* float32 4096 x 4096 k^-3 field: profile (16 codes, r >= 0.9999) ->
+  fixed-quality encode at the recommended code read on the device -> decode.
+  Sampled blocks: packet bytes equal the oracle's, decoded values equal the
+  oracle's decode of the same block (encoded with its predecessor, which
+  fixes the lag decision).  Whole array: the recommended point's byte count
+  is the container size, and its r matches an fp64 recomputation from the
+  decoded array.
+* int16 sensor trace replicated 64 times, fixed rate 4:1: every copy after
+  the first repeats the first copy's packets, except its first packet,
+  whose lag decision sees the previous copy's last block (checked against
+  the oracle).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1303_4994_gb300 import apax as A
+from paper_1303_4994_gb300 import build as B
+from paper_1303_4994_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+N = 256
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+    A.lib()
+    torch.cuda.init()
+
+
+def _packets(container: bytes, nb: int, mode: int, budget: int = 0):
+    """Packets of a container (offset table for fixed quality, j*B otherwise)."""
+    poff = 40 + (((4 * nb + 7) // 8) * 8 if mode == 1 else 0)
+    if mode == 1:
+        tab = np.frombuffer(container, dtype=np.uint32, count=nb, offset=40).astype(np.int64)
+        starts = poff + 4 * tab
+    else:
+        starts = poff + budget * np.arange(nb, dtype=np.int64)
+    out = []
+    for j in range(nb):
+        h0 = int(np.frombuffer(container, dtype=np.uint32, count=1, offset=int(starts[j]))[0])
+        plen = h0 >> 14
+        out.append(container[int(starts[j]):int(starts[j]) + plen])
+    return out
+
+
+def test_field_4096_full_size_sampled_parity():
+    x = synth.grf2d(4096, 4096, seed=1).reshape(-1)
+    n = x.size
+    xt = torch.from_numpy(x).cuda()
+    nc = 16
+    pws, pts, summ = A.profile_buffers(xt, N, nc)
+    A.profile_into(xt, N, list(A.DEFAULT_CANDIDATES), 0.9999, pws, pts, summ)
+    p = A.params(N, A.FIXED_QUALITY)
+    out = torch.empty(A.encoded_size(A.F32, n, p), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(A.workspace_size(A.F32, n, p), dtype=torch.uint8, device="cuda")
+    res = A.new_result("cuda")
+    A.encode_into(xt, p, out, ws, res, summary=summ)
+    torch.cuda.synchronize()
+    sm = A.read_summary(summ)
+    r = A.read_result(res)
+    assert sm.status == 0 and r.status == 0
+    code = int(sm.recommended_code)
+    point = A.read_points(pts, nc)[sm.recommended]
+    assert point.code == code and point.r >= 0.9999
+    assert point.bytes == r.bytes  # exact size prediction
+    cont = out[:r.bytes].cpu().numpy().tobytes()
+    y = A.decode(out[:r.bytes], torch.float32, n)
+    yd = y.double()
+    xd = xt.double()
+    r64 = float((xd * yd).sum() / torch.sqrt((xd * xd).sum() * (yd * yd).sum()))
+    assert abs(r64 - point.r) < 1e-12
+    nb = n // N
+    pk = _packets(cont, nb, 1)
+    yh = y.cpu().numpy()
+    rng = np.random.default_rng(41)
+    for j in [1, 2, nb - 1] + [int(v) for v in rng.integers(1, nb, 40)]:
+        want = O.encode_blocks(x, N, O.MODE_FQ, 1, 1, code, j, j + 1)[0]
+        assert pk[j] == want, j
+        sub = x[(j - 1) * N:(j + 1) * N]
+        ysub = O.decode(O.encode(sub, N, O.MODE_FQ, 1, 1, code), np.float32, 2 * N)
+        np.testing.assert_array_equal(yh[j * N:(j + 1) * N].view(np.uint32),
+                                      ysub[N:].view(np.uint32))
+
+
+def test_sensor_replica_repeats_packets():
+    trace = synth.sensor_trace()
+    reps = 64
+    x = np.tile(trace, reps)
+    xt = torch.from_numpy(x).cuda()
+    c = A.encode(xt, N, A.FIXED_RATE, (4, 1), 0).cpu().numpy().tobytes()
+    single = O.encode(trace, N, O.MODE_FR, 4, 1, 0)
+    budget = 128  # 256 int16 samples at 4:1
+    nb1 = trace.size // N
+    assert len(c) == 40 + reps * nb1 * budget
+    pk = _packets(c, reps * nb1, 0, budget)
+    first = _packets(single, nb1, 0, budget)
+    assert pk[:nb1] == first
+    seam = O.encode_blocks(x, N, O.MODE_FR, 4, 1, 0, nb1, nb1 + 1)[0]
+    for k in range(1, reps):
+        assert pk[k * nb1] == seam  # its lag decision sees the previous copy
+        assert pk[k * nb1 + 1:(k + 1) * nb1] == first[1:]

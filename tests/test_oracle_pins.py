@@ -562,3 +562,19 @@ def test_exponent_diff_statistic_reported():
     d = np.concatenate([np.diff(P.exps(u)) for u in q])
     frac = float(np.mean(np.abs(d) <= 1))
     assert 0.0 < frac <= 1.0
+
+
+def test_blocks_are_independent_replicated_trace():
+    # D2: no state crosses a block boundary except the lag decision, so a
+    # trace repeated twice encodes as its own packets twice, except the first
+    # packet of the second copy (its decision sees the first copy's last block)
+    from paper_1303_4994_gb300 import synth
+    t = synth.sensor_trace(4096, seed=9)
+    x = np.tile(t, 2)
+    one = O.encode(t, 256, O.MODE_FR, 4, 1, 0)
+    two = O.encode(x, 256, O.MODE_FR, 4, 1, 0)
+    B = 128
+    p1 = [one[40 + B * j:40 + B * (j + 1)] for j in range(16)]
+    p2 = [two[40 + B * j:40 + B * (j + 1)] for j in range(32)]
+    assert p2[:16] == p1 and p2[17:] == p1[1:]
+    assert p2[16] == O.encode_blocks(x, 256, O.MODE_FR, 4, 1, 0, 16, 17)[0]
