@@ -9,6 +9,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <string>
@@ -96,6 +97,10 @@ Geo geo_of(const apax_batch *b, const apax_batch_config &c)
     return g;
 }
 
+// Fixed-rate arrays with blocks of at most 1024 samples are encoded one
+// block per thread (the search runs without team exchanges).
+bool t1_job(const EncArgs &a) { return a.mode == APAX_FIXED_RATE && a.N <= kEncT1MaxBlock; }
+
 size_t pkt_smem_of(const apax_batch *b, const Geo &g)
 {
     return (size_t)(g.threads / g.ts) * (b->pkt_words + b->ebuf_words) * 4;
@@ -107,7 +112,7 @@ size_t stage_of(const apax_batch *b, const Geo &g)
 {
     const int pol = stage_policy();
     bool any_fr = false;
-    for (const EncArgs &a : b->jobs) any_fr |= a.mode == APAX_FIXED_RATE;
+    for (const EncArgs &a : b->jobs) any_fr |= a.mode == APAX_FIXED_RATE && !t1_job(a);
     if (pol == 0 || (pol < 0 && !any_fr)) return 0;
     uint64_t mx = 0;
     for (const EncArgs &a : b->jobs) {
@@ -123,7 +128,10 @@ size_t stage_of(const apax_batch *b, const Geo &g)
 size_t smem_of(const apax_batch *b, const Geo &g)
 {
     const size_t ps = pkt_smem_of(b, g), sb = stage_of(b, g);
-    return sb ? (ps + 15) / 16 * 16 + sb : ps;
+    size_t sm = sb ? (ps + 15) / 16 * 16 + sb : ps;
+    for (const EncArgs &a : b->jobs)  // the exponent columns of block-per-thread tiles
+        if (t1_job(a)) sm = std::max(sm, (size_t)g.threads * (a.N / 4));
+    return sm;
 }
 
 bool config_ok(const apax_batch *b, const apax_batch_config &c)
@@ -183,6 +191,11 @@ int apply_config(apax_batch *b, const apax_batch_config &c)
         a.stage_off = stage_of(b, g) ? (uint32_t)((pkt_smem_of(b, g) + 15) / 16 * 16) : 0;
         a.gp = (int)(g.ts == 8 ? b->gp8[i] : b->gp32[i]);
         a.ntiles = a.nb ? (a.nb + nteams - 1) / nteams : 1;
+        a.t1 = t1_job(a) ? 1 : 0;
+        if (a.t1) {  // a block per thread: tiles of `threads` blocks
+            a.gp = (int)(a.N / 4);
+            a.ntiles = a.nb ? (a.nb + g.threads - 1) / g.threads : 1;
+        }
         a.ticket = nullptr;
         a.done = (unsigned *)(b->ws + L.counters + 16 * (size_t)i);
         a.status = (int *)(b->ws + L.counters + 16 * (size_t)i + 4);
@@ -319,7 +332,9 @@ int apply_decode_config(apax_batch *b, const apax_batch_config &c)
     for (int i = 0; i < b->count; ++i) {
         DecArgs &a = tab[i];
         const uint64_t nb = (a.n + b->dN[i] - 1) / b->dN[i];
-        tiles[i] = nb ? (nb + nteams - 1) / nteams : 1;
+        // blocks of up to 1024 samples: one per thread, tiles of `threads` blocks
+        const uint64_t per = b->dN[i] <= kDecT1MaxBlock ? c.threads : (uint64_t)nteams;
+        tiles[i] = nb ? (nb + per - 1) / per : 1;
         a.done = (unsigned *)(b->ws + L.counters + 16 * (size_t)i);
         a.status = (int *)(b->ws + L.counters + 16 * (size_t)i + 4);
         prefix[i + 1] = prefix[i] + tiles[i];

@@ -712,6 +712,13 @@ __global__ void __launch_bounds__(128) k_decode(DecArgs a)
     }
 }
 
+template <int DT>
+__device__ __noinline__ void decode_t1_call(const DecArgs &a, const DecHdr &hd, uint64_t j, uint8_t *eb,
+                                            int est)
+{
+    decode_block_t1<DT>(a, hd, j, eb, est);
+}
+
 template <int DT, int TS, int EB>
 __device__ __noinline__ void decode_tile_call(const DecArgs &a, const DecHdr &hd, uint64_t tile,
                                               uint8_t *dsm)
@@ -763,7 +770,20 @@ __global__ void __launch_bounds__(128) k_decode_batch(DecBatchArgs ba)
         }
         __syncthreads();
         const DecHdr hd = s_h;
-        if (hd.err == 0) {
+        if (hd.err == 0 && ba.block_size[s_job] <= kT1MaxN) {
+            // a block per thread: the plan made this array's tiles blockDim.x blocks
+            const uint64_t j = s_tile * blockDim.x + threadIdx.x;
+            if (j < hd.nb) {
+                uint8_t *eb = dsm + threadIdx.x;
+                switch (s_args.dtype) {
+                case 1: decode_t1_call<1>(s_args, hd, j, eb, (int)blockDim.x); break;
+                case 2: decode_t1_call<2>(s_args, hd, j, eb, (int)blockDim.x); break;
+                case 3: decode_t1_call<3>(s_args, hd, j, eb, (int)blockDim.x); break;
+                case 4: decode_t1_call<4>(s_args, hd, j, eb, (int)blockDim.x); break;
+                default: decode_t1_call<5>(s_args, hd, j, eb, (int)blockDim.x); break;
+                }
+            }
+        } else if (hd.err == 0) {
             switch (s_args.dtype) {
             case 1: decode_tile_call<1, TS, EB>(s_args, hd, s_tile, dsm); break;
             case 2: decode_tile_call<2, TS, EB>(s_args, hd, s_tile, dsm); break;
@@ -812,10 +832,17 @@ static cudaError_t launch_dt(const DecArgs &a, cudaStream_t s)
 
 }  // namespace
 
+static size_t decode_batch_smem(int ts, int threads)
+{
+    const size_t teams = (size_t)(threads / ts) * (ts == 8 ? 1024 : 4096);
+    const size_t cols = (size_t)threads * (kT1MaxN / 4);  // block-per-thread exponent columns
+    return teams > cols ? teams : cols;
+}
+
 cudaError_t launch_decode_batch(const DecBatchArgs &b, int ts, int threads, unsigned ctas,
                                cudaStream_t s)
 {
-    const size_t smem = (size_t)(threads / ts) * (ts == 8 ? 1024 : 4096);
+    const size_t smem = decode_batch_smem(ts, threads);
     auto k = ts == 8 ? k_decode_batch<8, 1024> : k_decode_batch<32, 4096>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -825,7 +852,7 @@ cudaError_t launch_decode_batch(const DecBatchArgs &b, int ts, int threads, unsi
 
 int decode_batch_occupancy(int ts, int threads)
 {
-    const size_t smem = (size_t)(threads / ts) * (ts == 8 ? 1024 : 4096);
+    const size_t smem = decode_batch_smem(ts, threads);
     auto k = ts == 8 ? k_decode_batch<8, 1024> : k_decode_batch<32, 4096>;
     int nb = 0;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)

@@ -614,9 +614,25 @@ __device__ __noinline__ void encode_tile_call(const EncArgs &a, uint64_t tile, u
     encode_tile<DT, TS, MODE>(a, tile, smem);
 }
 
+template <int DT, int MODE>
+__device__ __noinline__ void encode_tile_t1_call(const EncArgs &a, uint64_t tile, uint32_t *smem)
+{
+    encode_tile_t1<DT, MODE>(a, tile, reinterpret_cast<uint8_t *>(smem));
+}
+
 template <int TS>
 __device__ __forceinline__ void encode_tile_any(const EncArgs &a, uint64_t tile, uint32_t *smem)
 {
+    if (a.t1) {  // fixed rate, a block per thread
+        switch (a.dtype) {
+        case 1: encode_tile_t1_call<1, 0>(a, tile, smem); break;
+        case 2: encode_tile_t1_call<2, 0>(a, tile, smem); break;
+        case 3: encode_tile_t1_call<3, 0>(a, tile, smem); break;
+        case 4: encode_tile_t1_call<4, 0>(a, tile, smem); break;
+        default: encode_tile_t1_call<5, 0>(a, tile, smem); break;
+        }
+        return;
+    }
     const int k = 2 * a.dtype + a.mode;
     switch (k) {
     case 2: encode_tile_call<1, TS, 0>(a, tile, smem); break;

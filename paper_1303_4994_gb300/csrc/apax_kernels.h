@@ -26,6 +26,7 @@ struct EncArgs {
     uint64_t poff;      // payload offset in the container
     uint32_t pkt_words, ebuf_words;  // per-team shared-memory layout
     uint32_t stage_off; // byte offset of the staged tile in shared memory (0: none)
+    int t1;             // batches: this array is encoded one block per thread
     int gp;             // groups per team thread
     uint64_t ntiles;
     // workspace
