@@ -118,19 +118,24 @@ struct NibWriter {
     }
 };
 
-// Decoupled look-back (warp 0, every lane): publish this tile's aggregate,
-// then read 32 predecessors per probe (lane l reads tile base - l); the
-// nearest inclusive prefix ends the walk.  Returns the exclusive prefix.
-__device__ __forceinline__ uint64_t lookback(const EncArgs &a, uint64_t tile, uint32_t total)
+// Decoupled look-back, in two steps so that a tile's aggregate is visible
+// early: publish_aggregate (one lane) as soon as the tile's size is known,
+// lookback_prefix (warp 0, every lane) after the tile's other work.
+__device__ __forceinline__ void publish_aggregate(const EncArgs &a, uint64_t tile, uint32_t total)
+{
+    if (a.test_stall_tile == (long long)tile) return;  // test hook: never publishes
+    atomicExch(a.tiles + tile, (tile == 0 ? kFlagP : kFlagA) | total);
+}
+
+// Reads 32 predecessors per probe (lane l reads tile base - l); the nearest
+// inclusive prefix ends the walk.  Returns the exclusive prefix and
+// publishes this tile's inclusive prefix.
+__device__ __forceinline__ uint64_t lookback_prefix(const EncArgs &a, uint64_t tile, uint32_t total)
 {
     const int l = threadIdx.x & 31;
+    if (tile == 0) return 0;
     const bool hook = a.test_stall_tile == (long long)tile;
     uint64_t excl = 0;
-    if (tile == 0) {
-        if (l == 0 && !hook) atomicExch(a.tiles, kFlagP | total);
-        return 0;
-    }
-    if (l == 0 && !hook) atomicExch(a.tiles + tile, kFlagA | total);
     int64_t base = (int64_t)tile - 1;
     while (true) {
         const int64_t tt = base - l;
@@ -146,6 +151,12 @@ __device__ __forceinline__ uint64_t lookback(const EncArgs &a, uint64_t tile, ui
     }
     if (l == 0 && !hook) atomicExch(a.tiles + tile, kFlagP | ((excl + total) & kValMask));
     return excl;
+}
+
+__device__ __forceinline__ uint64_t lookback(const EncArgs &a, uint64_t tile, uint32_t total)
+{
+    if ((threadIdx.x & 31) == 0) publish_aggregate(a, tile, total);
+    return lookback_prefix(a, tile, total);
 }
 
 // Writes the Sec. 6 JEE tokens of groups [g0, g1) of a block of G groups
@@ -244,6 +255,7 @@ template <int DT, int TS, int MODE>
 __device__ __forceinline__ void encode_tile(const EncArgs &a, uint64_t tile, uint32_t *smem)
 {
     __shared__ uint32_t s_words[32];
+    __shared__ uint32_t s_total;
     __shared__ uint64_t s_base;
     using T = DT_<DT>;
     using raw = typename T::raw;
@@ -331,6 +343,24 @@ __device__ __forceinline__ void encode_tile(const EncArgs &a, uint64_t tile, uin
     const uint32_t bits = (uint32_t)H + 4u * (uint32_t)nib_total + 4u * (uint32_t)sume_total;
     if (MODE == 1) plen = pad32_bytes(bits);
     const uint32_t words = b.active ? plen >> 2 : 0;
+    if (MODE == 1) {
+        // the tile's size is known: scan it and publish the aggregate now,
+        // so that successors' look-backs find it while this tile assembles
+        if (t == 0) s_words[team] = words;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const int l = threadIdx.x;
+            const uint32_t v = l < nteams ? s_words[l] : 0;
+            const uint32_t incl = warp_incl_scan(v);
+            const uint32_t total = __shfl_sync(kFull, incl, 31);
+            __syncwarp();
+            if (l < nteams) s_words[l] = incl - v;
+            if (l == 0) {
+                s_total = total;
+                publish_aggregate(a, tile, total);
+            }
+        }
+    }
     for (uint32_t w = t; w < words; w += TS) pkt[w] = 0;
     __syncwarp();
     // team scans before any divergence: every lane of the warp takes part
@@ -366,17 +396,9 @@ __device__ __forceinline__ void encode_tile(const EncArgs &a, uint64_t tile, uin
 
     uint64_t off_words;  // packet start in payload words
     if (MODE == 1) {
-        if (t == 0) s_words[team] = words;
-        __syncthreads();
         if (threadIdx.x < 32) {
-            const int l = threadIdx.x;
-            const uint32_t v = l < nteams ? s_words[l] : 0;
-            const uint32_t incl = warp_incl_scan(v);
-            const uint32_t total = __shfl_sync(kFull, incl, 31);
-            __syncwarp();
-            if (l < nteams) s_words[l] = incl - v;
-            const uint64_t excl = lookback(a, tile, total);
-            if (l == 0) s_base = excl;
+            const uint64_t excl = lookback_prefix(a, tile, s_total);
+            if (threadIdx.x == 0) s_base = excl;
         }
         __syncthreads();
         off_words = s_base + s_words[team];
