@@ -153,12 +153,6 @@ __device__ __forceinline__ uint64_t lookback_prefix(const EncArgs &a, uint64_t t
     return excl;
 }
 
-__device__ __forceinline__ uint64_t lookback(const EncArgs &a, uint64_t tile, uint32_t total)
-{
-    if ((threadIdx.x & 31) == 0) publish_aggregate(a, tile, total);
-    return lookback_prefix(a, tile, total);
-}
-
 // Writes the Sec. 6 JEE tokens of groups [g0, g1) of a block of G groups
 // whose exponents are eb[g * est]; s_in: the group before g0 opened a joint
 // token that g0 completes.
@@ -450,29 +444,23 @@ __device__ __forceinline__ void encode_tile(const EncArgs &a, uint64_t tile, uin
 }
 
 // ---------------------------------------------------------------- block per thread
-// A tile of blockDim.x blocks, one per thread (block sizes up to
+// Fixed rate, a tile of blockDim.x blocks, one per thread (block sizes up to
 // kT1MaxBlock): the team functions run with a team of one, exponents sit in
 // a lane-interleaved shared-memory column (smem bytes g * blockDim.x +
-// thread), and each thread writes its own packet straight to global memory
-// once the CTA-wide scan and the look-back have placed it.
+// thread), and each thread writes its own packet straight to its place j*B.
 constexpr uint32_t kT1MaxBlock = 1024;
 
-template <int DT, int MODE>
+template <int DT>
 __device__ __forceinline__ void encode_tile_t1(const EncArgs &a, uint64_t tile, uint8_t *smem)
 {
-    __shared__ uint32_t s_wt[32];
-    __shared__ uint64_t s_base;
     using T = DT_<DT>;
     using raw = typename T::raw;
     using lt = typename LaneT<DT>::t;
     constexpr int H = T::H;
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5;
     const uint64_t j = tile * (uint64_t)nt + (uint64_t)tid;
-    int code = (int)a.code;
-    if (a.code_dev) code = (int)*a.code_dev;
     uint8_t *eb = smem + tid;  // exponent of group g at eb[g * nt]
-    if (tile == 0 && tid == 0) write_container_header(a, code);
+    if (tile == 0 && tid == 0) write_container_header(a, 0);
     const raw *x = reinterpret_cast<const raw *>(a.x);
     // stream decision: best(j-1) at code 0 (block 0 uses its own)
     int s;
@@ -488,26 +476,22 @@ __device__ __forceinline__ void encode_tile_t1(const EncArgs &a, uint64_t tile, 
     TBlock<DT> b;
     open_team_block<DT, 1>(b, x, a.n, a.N, a.nb, j, a.gp);
     if (b.active && b.bad) set_status(a.status, -8);
-    uint32_t plen = 0;
-    if (MODE == 0) {
-        const uint32_t budget = b.L == (int)a.N ? a.B : fr_budget<DT>(b.L, a.rate_num, a.rate_den);
-        const bool fits0 = pad32_bytes(team_eval1<DT, 1>(b, 0, s)) <= budget;
-        int lo = 0, hi = 4095;
-        if (!fits0) {
+    // BISECT against the block budget (Sec. 6 adaptive loop)
+    const uint32_t budget = b.L == (int)a.N ? a.B : fr_budget<DT>(b.L, a.rate_num, a.rate_den);
+    const bool fits0 = pad32_bytes(team_eval1<DT, 1>(b, 0, s)) <= budget;
+    int lo = 0, hi = 4095;
+    if (!fits0) {
 #pragma unroll 1
-            for (int it = 0; it < 12 && hi - lo > 1; ++it) {  // 12 halvings close [0, 4095]
-                const int mid = (lo + hi) >> 1;
-                if (pad32_bytes(team_eval1<DT, 1>(b, mid, s)) <= budget) hi = mid;
-                else lo = mid;
-            }
+        for (int it = 0; it < 12 && hi - lo > 1; ++it) {  // 12 halvings close [0, 4095]
+            const int mid = (lo + hi) >> 1;
+            if (pad32_bytes(team_eval1<DT, 1>(b, mid, s)) <= budget) hi = mid;
+            else lo = mid;
         }
-        code = fits0 ? 0 : hi;
-        plen = budget;
     }
-    // final pass: exponents into the column, token count
+    const int code = fits0 ? 0 : hi;
+    const uint32_t plen = budget;
+    // final pass: exponents into the column
     const Quant<DT> Q(code, b.Eb);
-    TokCount tc;
-    tc.init();
     with_quant<DT>(Q, [&](const auto &qf) {
         Stream1 st(s, carry_in<DT>(b, qf, 0));
 #pragma unroll 1
@@ -515,49 +499,12 @@ __device__ __forceinline__ void encode_tile_t1(const EncArgs &a, uint64_t tile, 
             lt xv[4];
             load4<DT, true>(b, 4 * g, xv);
             int32_t u[4];
-            const int e = exp_from_or(group1<DT>(qf, xv, st, u));
-            eb[(size_t)g * nt] = (uint8_t)e;
-            tc.push(e, true);
+            eb[(size_t)g * nt] = (uint8_t)exp_from_or(group1<DT>(qf, xv, st, u));
         }
     });
-    int nib, sume;
-    team_tokens<1>(tc, true, nib, sume);
-    const uint32_t bits = (uint32_t)H + 4u * (uint32_t)nib + 4u * (uint32_t)sume;
-    if (MODE == 1) plen = pad32_bytes(bits);
     const uint32_t words = b.active ? plen >> 2 : 0;
-
-    uint64_t off_words;
-    if (MODE == 1) {
-        // CTA-wide exclusive scan of the packet words, then the look-back
-        const uint32_t incl = warp_incl_scan(words);
-        if (lane == 31) s_wt[warp] = incl;
-        __syncthreads();
-        if (warp == 0) {
-            const int nw = nt >> 5;
-            const uint32_t v = lane < nw ? s_wt[lane] : 0;
-            const uint32_t wi = warp_incl_scan(v);
-            const uint32_t total = __shfl_sync(kFull, wi, 31);
-            __syncwarp();
-            if (lane < nw) s_wt[lane] = wi - v;
-            const uint64_t excl = lookback(a, tile, total);
-            if (lane == 0) s_base = excl;
-        }
-        __syncthreads();
-        off_words = s_base + s_wt[warp] + (incl - words);
-    } else {
-        off_words = j * (uint64_t)(a.B >> 2);
-    }
-
     if (b.active) {
-        const uint64_t start = a.poff + 4ull * off_words;
-        if (MODE == 1) {
-            if (off_words > 0xffffffffull) {
-                set_status(a.status, -6);
-            } else {
-                reinterpret_cast<uint32_t *>(a.out + 40)[j] = (uint32_t)off_words;
-                if (j == a.nb - 1 && (a.nb & 1)) reinterpret_cast<uint32_t *>(a.out + 40)[j + 1] = 0;
-            }
-        }
+        const uint64_t start = a.poff + (uint64_t)j * a.B;
         if (start + 4ull * words > a.cap) {
             set_status(a.status, -5);
         } else {
@@ -578,7 +525,7 @@ __device__ __forceinline__ void encode_tile_t1(const EncArgs &a, uint64_t tile, 
                 }
             });
             w.flush();
-            while (w.w < words) w.dst[w.w++] = 0u;  // padding (fixed rate)
+            while (w.w < words) w.dst[w.w++] = 0u;  // padding to the budget
         }
     }
 
@@ -590,31 +537,21 @@ __device__ __forceinline__ void encode_tile_t1(const EncArgs &a, uint64_t tile, 
         const unsigned prev = atomicAdd(a.done, 1u);
         if (prev == a.ntiles - 1) {
             __threadfence();
-            uint64_t payload;
-            if (MODE == 1) {
-                volatile unsigned long long *last = a.tiles + (a.ntiles - 1);
-                payload = 4ull * ((uint64_t)(*last) & kValMask);
-            } else {
-                payload = a.fr_payload;
-            }
-            put_le(a.out + 28, payload, 8);
+            put_le(a.out + 28, a.fr_payload, 8);
             volatile int *st = a.status;
             if (a.res) {
-                a.res->bytes = a.poff + payload;
+                a.res->bytes = a.poff + a.fr_payload;
                 a.res->status = *st;
             }
         }
     }
 }
 
-template <int DT, int MODE>
+template <int DT>
 __global__ void __launch_bounds__(128) k_encode_t1(EncArgs a)
 {
     extern __shared__ uint32_t smem[];
-    __shared__ uint64_t s_tile;
-    if (threadIdx.x == 0) s_tile = MODE == 1 ? (uint64_t)atomicAdd(a.ticket, 1u) : blockIdx.x;
-    __syncthreads();
-    encode_tile_t1<DT, MODE>(a, s_tile, reinterpret_cast<uint8_t *>(smem));
+    encode_tile_t1<DT>(a, blockIdx.x, reinterpret_cast<uint8_t *>(smem));
 }
 
 // ---------------------------------------------------------------- kernels
@@ -636,10 +573,10 @@ __device__ __noinline__ void encode_tile_call(const EncArgs &a, uint64_t tile, u
     encode_tile<DT, TS, MODE>(a, tile, smem);
 }
 
-template <int DT, int MODE>
+template <int DT>
 __device__ __noinline__ void encode_tile_t1_call(const EncArgs &a, uint64_t tile, uint32_t *smem)
 {
-    encode_tile_t1<DT, MODE>(a, tile, reinterpret_cast<uint8_t *>(smem));
+    encode_tile_t1<DT>(a, tile, reinterpret_cast<uint8_t *>(smem));
 }
 
 template <int TS>
@@ -647,11 +584,11 @@ __device__ __forceinline__ void encode_tile_any(const EncArgs &a, uint64_t tile,
 {
     if (a.t1) {  // fixed rate, a block per thread
         switch (a.dtype) {
-        case 1: encode_tile_t1_call<1, 0>(a, tile, smem); break;
-        case 2: encode_tile_t1_call<2, 0>(a, tile, smem); break;
-        case 3: encode_tile_t1_call<3, 0>(a, tile, smem); break;
-        case 4: encode_tile_t1_call<4, 0>(a, tile, smem); break;
-        default: encode_tile_t1_call<5, 0>(a, tile, smem); break;
+        case 1: encode_tile_t1_call<1>(a, tile, smem); break;
+        case 2: encode_tile_t1_call<2>(a, tile, smem); break;
+        case 3: encode_tile_t1_call<3>(a, tile, smem); break;
+        case 4: encode_tile_t1_call<4>(a, tile, smem); break;
+        default: encode_tile_t1_call<5>(a, tile, smem); break;
         }
         return;
     }
@@ -724,7 +661,7 @@ static cudaError_t launch_ts(const EncArgs &a, int threads, size_t smem, cudaStr
 template <int DT>
 static cudaError_t launch_t1(const EncArgs &a, int threads, size_t smem, cudaStream_t s)
 {
-    auto k = a.mode == 1 ? k_encode_t1<DT, 1> : k_encode_t1<DT, 0>;
+    auto k = k_encode_t1<DT>;  // fixed rate only
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<(unsigned)a.ntiles, threads, smem, s>>>(a);

@@ -408,88 +408,6 @@ __device__ __forceinline__ void open_team_block(TBlock<DT> &b, const typename DT
     }
 }
 
-// Derivative carry at a thread's first sample s0: the previous sample's q
-// and first difference (Sec. 5/6 streams live within a block).
-template <int DT>
-__device__ __forceinline__ void seg_carry(const TBlock<DT> &b, const Quant<DT> &Q, int s0,
-                                          int32_t &qp, int32_t &s1p)
-{
-    if (s0 == 0) {
-        qp = 0;
-        s1p = 0;
-        return;
-    }
-    const int32_t a = Q(load1<DT>(b, s0 - 1));
-    const int32_t c = s0 >= 2 ? Q(load1<DT>(b, s0 - 2)) : 0;
-    qp = a;
-    s1p = s0 - 1 == 0 ? 0 : (int32_t)((uint32_t)a - (uint32_t)c);
-}
-
-// Quantise group g (samples xv) and derive its three streams (S0 the data,
-// S1 first differences, S2 second differences with u_1 = q_1 - q_0; mod
-// 2^W, sign-extended).  Samples past L repeat q[L-1] (last-group padding).
-// qp / s1p carry the previous sample's q and first difference.
-template <int DT>
-__device__ __forceinline__ void group_streams(const TBlock<DT> &b, const Quant<DT> &Q, int g,
-                                              const typename LaneT<DT>::t (&xv)[4], int32_t &qp,
-                                              int32_t &s1p, int32_t (&q)[4], int32_t (&v0)[4],
-                                              int32_t (&v1)[4], int32_t (&v2)[4])
-{
-    constexpr int W = DT_<DT>::W;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int idx = 4 * g + i;
-        const int32_t qi = idx < b.L ? Q(xv[i]) : qp;
-        const int32_t d1 = (int32_t)((uint32_t)qi - (uint32_t)qp);
-        int32_t d2 = (int32_t)((uint32_t)d1 - (uint32_t)s1p);
-        if (idx == 1) d2 = d1;
-        q[i] = qi;
-        v0[i] = sext_w((uint32_t)qi, W);
-        v1[i] = sext_w((uint32_t)d1, W);
-        v2[i] = sext_w((uint32_t)d2, W);
-        s1p = idx == 0 ? 0 : d1;
-        qp = qi;
-    }
-}
-
-__device__ __forceinline__ uint32_t or4(const int32_t (&v)[4])
-{
-    return bits_term(v[0]) | bits_term(v[1]) | bits_term(v[2]) | bits_term(v[3]);
-}
-
-// Packet bits (unpadded) of the team's block at `code` for the streams in
-// smask.  Sec. 6 packet: header, JEE tokens, 4 e_g mantissa bits per group.
-template <int DT, int TS>
-__device__ __forceinline__ void team_eval(const TBlock<DT> &b, int code, unsigned smask,
-                                          uint32_t (&bits)[3])
-{
-    const Quant<DT> Q(code, b.Eb);
-    TokCount tc[3];
-#pragma unroll
-    for (int s = 0; s < 3; ++s) tc[s].init();
-    int32_t qp, s1p;
-    seg_carry<DT>(b, Q, 4 * b.g0, qp, s1p);
-#pragma unroll 1
-    for (int g = b.g0; g < b.g1; ++g) {
-        typename LaneT<DT>::t xv[4];
-        load4<DT>(b, 4 * g, xv);
-        int32_t q[4], v0[4], v1[4], v2[4];
-        group_streams<DT>(b, Q, g, xv, qp, s1p, q, v0, v1, v2);
-        tc[0].push(exp_from_or(or4(v0)), true);
-        tc[1].push(exp_from_or(or4(v1)), true);
-        tc[2].push(exp_from_or(or4(v2)), true);
-    }
-    const bool first = b.g0 == 0;
-    // Every stream's team exchange runs on every lane (the teams of a warp may
-    // ask for different streams; shuffles need the whole warp).
-#pragma unroll
-    for (int s = 0; s < 3; ++s) {
-        int nib, sume;
-        team_tokens<TS>(tc[s], first, nib, sume);
-        bits[s] = ((smask >> s) & 1) ? (uint32_t)DT_<DT>::H + 4u * (uint32_t)nib + 4u * (uint32_t)sume : 0u;
-    }
-}
-
 // ---------------------------------------------------------------- streams (carried)
 // The derivative streams of Sec. 6 from carried predecessors, with no
 // per-sample position tests: S1 u_i = q_i - qp1, S2 u_i = q_i - 2 qp2 + qpp2
