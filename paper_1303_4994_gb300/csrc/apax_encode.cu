@@ -275,7 +275,7 @@ __device__ __forceinline__ void encode_tile(const EncArgs &a, uint64_t tile, uin
         const uint64_t jb0 = tile * (uint64_t)nteams;
         base = jb0 ? jb0 - 1 : 0;
         const uint64_t bend = min(jb0 + (uint64_t)nteams, a.nb);
-        stage_blocks<DT>(xs, x, a.n, a.N, base, bend > base ? bend : base);
+        stage_blocks<DT>(xs, x, a.n, a.N, base, bend > base ? bend : base, a.status, a.spin_limit);
         __syncthreads();
         x = xs;
     }

@@ -126,9 +126,9 @@ inline void default_geometry(size_t per_team_bytes, int &ts, int &threads)
 
 // Staging policy: APAX_STAGE=0 or 1 in the environment forces shared-memory
 // staging of the input off or on (for measurement); otherwise each path
-// uses its default: on for the fixed-rate search (13 passes over a block),
-// off for fixed quality and the profiler sweep, whose occupancy matters
-// more than their L2 re-reads (measured on GB300).
+// uses its default: on for the profiler sweep (17 passes over a block) and
+// the fixed-rate search by teams (13 passes), off for fixed quality, whose
+// occupancy matters more than its few L2 re-reads (measured on GB300).
 inline int stage_policy()
 {
     static int p = [] {

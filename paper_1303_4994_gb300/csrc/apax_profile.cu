@@ -284,7 +284,7 @@ __device__ __forceinline__ void profile_run(const ProfArgs &a, uint64_t run, uin
         const uint64_t jb0 = run * (uint64_t)nteams;
         base = jb0 ? jb0 - 1 : 0;
         const uint64_t bend = min(jb0 + (uint64_t)nteams, a.nb);
-        stage_blocks<DT>(xs, x, a.n, a.N, base, bend > base ? bend : base);
+        stage_blocks<DT>(xs, x, a.n, a.N, base, bend > base ? bend : base, a.status, 1ll << 31);
         __syncthreads();
         x = xs;
     }
@@ -856,7 +856,7 @@ cudaError_t launch_prof_dt(const ProfArgs &a, cudaStream_t s)
     size_t smem = (size_t)kRun * a.ncand * sizeof(CandStage<DT>) + (size_t)kRun * Qn * 8 +
                   (DT_<DT>::F ? (size_t)6 * PS<DT>::ND * 8 : 0);
     ProfArgs b = a;
-    const size_t sb = host::stage_policy() == 1
+    const size_t sb = host::stage_policy() != 0
                           ? profile_stage_bytes(sizeof(typename DT_<DT>::raw), a.N, smem)
                           : 0;
     b.stage_off = sb ? (uint32_t)((smem + 15) / 16 * 16) : 0;

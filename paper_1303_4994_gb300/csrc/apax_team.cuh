@@ -599,39 +599,93 @@ __device__ __forceinline__ uint32_t team_eval1(const TBlock<DT> &b, int code, in
 }
 
 // ---------------------------------------------------------------- staging
+// Bulk (TMA) copies global -> shared memory completed on an mbarrier, in
+// inline PTX.
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *m, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(m)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *m, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(m)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_to_shared(void *dst, const void *src, uint32_t bytes, uint64_t *m)
+{
+    uint64_t g;
+    asm("cvta.to.global.u64 %0, %1;" : "=l"(g) : "l"(src));
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(g), "r"(bytes), "r"(smem_addr(m))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *m, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_addr(m)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void mbar_inval(uint64_t *m)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(m)) : "memory");
+}
+
 // Copy blocks [b0, b1) of the array into shared memory (all threads of the
-// CTA; zeros past n), one group of 4 samples per vector access, so that the
-// codec's repeated passes over a block read shared memory instead of L2.
+// CTA call it; zeros past n), so that the codec's repeated passes over a
+// block read shared memory instead of L2.  The 16-byte aligned bulk of the
+// range moves with one TMA bulk copy; the rest (an unaligned source, the
+// ragged tail, the zeros past n) with vector loads.  The wait on the copy is
+// bounded: past `spin` clock cycles the status becomes APAX_ERR_TIMEOUT and
+// the copy is waited for once more (bounded) before the CTA goes on.
 template <int DT>
 __device__ __forceinline__ void stage_blocks(typename DT_<DT>::raw *xs, const typename DT_<DT>::raw *x,
-                                             uint64_t n, uint32_t N, uint64_t b0, uint64_t b1)
+                                             uint64_t n, uint32_t N, uint64_t b0, uint64_t b1,
+                                             int *status, long long spin)
 {
     using raw = typename DT_<DT>::raw;
     constexpr int ES = sizeof(raw);
+    __shared__ __align__(8) uint64_t s_mbar;
     const uint64_t s0 = b0 * (uint64_t)N;
     const uint64_t s1 = min(b1 * (uint64_t)N, n);
-    const uint32_t groups = (uint32_t)((b1 - b0) * (uint64_t)N / 4);
-    const bool al = (((uintptr_t)(x + s0)) & (4 * ES - 1)) == 0;
-    for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x) {
-        const uint64_t i = s0 + 4ull * g;
-        raw *d = xs + 4ull * g;
-        if (al && i + 4 <= s1) {
-            if constexpr (ES == 1) {
-                *reinterpret_cast<uint32_t *>(d) = __ldg(reinterpret_cast<const uint32_t *>(x + i));
-            } else if constexpr (ES == 2) {
-                *reinterpret_cast<uint2 *>(d) = __ldg(reinterpret_cast<const uint2 *>(x + i));
-            } else if constexpr (ES == 4) {
-                *reinterpret_cast<uint4 *>(d) = __ldg(reinterpret_cast<const uint4 *>(x + i));
-            } else {
-                const ulonglong2 *r = reinterpret_cast<const ulonglong2 *>(x + i);
-                ulonglong2 *w = reinterpret_cast<ulonglong2 *>(d);
-                w[0] = __ldg(r);
-                w[1] = __ldg(r + 1);
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) d[k] = i + k < s1 ? x[i + k] : (raw)0;
+    const uint64_t send = b1 * (uint64_t)N;  // staged samples end (zeros from s1)
+    const bool al16 = (((uintptr_t)(x + s0)) & 15) == 0 && (((uintptr_t)xs) & 15) == 0;
+    // bulk part: whole 16-byte chunks of real samples
+    const uint64_t bulk_bytes = al16 && s1 > s0 ? (((s1 - s0) * ES) / 16) * 16 : 0;
+    const uint64_t bulk_elems = bulk_bytes / ES;
+    if (bulk_bytes) {
+        if (threadIdx.x == 0) {
+            mbar_init(&s_mbar, 1);
+            mbar_expect_tx(&s_mbar, (uint32_t)bulk_bytes);
+            bulk_to_shared(xs, x + s0, (uint32_t)bulk_bytes, &s_mbar);
         }
+    }
+    // the rest, element by element (disjoint from the bulk part)
+    for (uint64_t i = s0 + bulk_elems + threadIdx.x; i < send; i += blockDim.x)
+        xs[i - s0] = i < s1 ? x[i] : (raw)0;
+    if (bulk_bytes) {
+        __syncthreads();  // the barrier is initialised before anyone waits on it
+        const long long t0 = clock64();
+        bool done = mbar_try_wait(&s_mbar, 0);
+        while (!done && clock64() - t0 <= spin) done = mbar_try_wait(&s_mbar, 0);
+        if (!done) {
+            atomicMin(status, -10);
+            const long long t1 = clock64();
+            while (!mbar_try_wait(&s_mbar, 0) && clock64() - t1 <= spin) {
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) mbar_inval(&s_mbar);
     }
 }
 
