@@ -13,6 +13,9 @@ one, and properties that hold at any size are checked on everything.
   the first repeats the first copy's packets, except its first packet,
   whose lag decision sees the previous copy's last block (checked against
   the oracle).
+* 40,000 blocks of float32 (the block-per-thread decoder's size): block
+  ranges decode to the whole array's values, sampled packets equal the
+  oracle's, and a reserved stream selector is reported as corrupt.
 """
 import numpy as np
 import pytest
@@ -106,3 +109,34 @@ def test_sensor_replica_repeats_packets():
     for k in range(1, reps):
         assert pk[k * nb1] == seam  # its lag decision sees the previous copy
         assert pk[k * nb1 + 1:(k + 1) * nb1] == first[1:]
+
+
+def test_large_array_block_range_and_corruption():
+    # enough blocks for the block-per-thread decoder: a block range decodes
+    # to the same values as the whole array, and a reserved stream selector
+    # in one packet is reported as corrupt
+    rng = np.random.default_rng(43)
+    nb = 40000
+    x = np.cumsum(rng.standard_normal(nb * N)).astype(np.float32)
+    xt = torch.from_numpy(x).cuda()
+    for mode, rate, code in ((A.FIXED_QUALITY, (1, 1), 640), (A.FIXED_RATE, (4, 1), 0)):
+        c = A.encode(xt, N, mode, rate, code)
+        full = A.decode(c, torch.float32, x.size)
+        for b0, b1 in ((0, nb), (1000, 35000), (nb - 33000, nb)):
+            part = A.decode_blocks(c, torch.float32, x.size, b0, b1, N)
+            assert torch.equal(part.view(torch.int32), full[b0 * N:b1 * N].view(torch.int32))
+        # sampled blocks against the oracle
+        cont = c.cpu().numpy().tobytes()
+        pk = _packets(cont, nb, mode, 256 if mode == A.FIXED_RATE else 0)
+        for j in (1, 777, nb - 1):
+            want = O.encode_blocks(x, N, mode, rate[0], rate[1], code, j, j + 1)[0]
+            assert pk[j] == want, (mode, j)
+        # packet 12345's selector set to the reserved value 3
+        bad = bytearray(cont)
+        poff = 40 + (((4 * nb + 7) // 8) * 8 if mode == A.FIXED_QUALITY else 0)
+        start = poff + (4 * int(np.frombuffer(cont, np.uint32, 1, 40 + 4 * 12345)[0])
+                        if mode == A.FIXED_QUALITY else 256 * 12345)
+        bad[start] |= 3
+        _, r = A.decode(torch.frombuffer(bad, dtype=torch.uint8).cuda(), torch.float32, x.size,
+                        check=False)
+        assert r.status == -9
