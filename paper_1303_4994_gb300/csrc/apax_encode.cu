@@ -443,6 +443,40 @@ __device__ __forceinline__ void encode_tile(const EncArgs &a, uint64_t tile, uin
     }
 }
 
+// Does block b fit `budget` bytes at `code` on stream s (one thread owns the
+// block)?  The running packet size -- header, the first absolute token, the
+// nibbles and exponent bits so far -- only grows, so a pass stops as soon as
+// it exceeds the budget: the answer is the same as from the full size.
+template <int DT>
+__device__ __forceinline__ bool fits_t1(const TBlock<DT> &b, int code, int s, uint32_t budget)
+{
+    constexpr int H = DT_<DT>::H;
+    const Quant<DT> Q(code, b.Eb);
+    TokCount tc;
+    tc.init();
+    const uint32_t limit = 8u * budget;  // bits; budget is a multiple of 4 bytes
+    bool over = false;
+    with_quant<DT>(Q, [&](const auto &qf) {
+        Stream1 st(s, carry_in<DT>(b, qf, 0));
+#pragma unroll 1
+        for (int g = 0; g < b.G; ++g) {
+            typename LaneT<DT>::t xv[4];
+            load4<DT, true>(b, 4 * g, xv);
+            int32_t u[4];
+            tc.push(exp_from_or(group1<DT>(qf, xv, st, u)), true);
+            if ((g & 7) == 7 &&
+                (uint32_t)H + 4u * (2u + (uint32_t)tc.nib) + 4u * (uint32_t)tc.sume > limit) {
+                over = true;
+                break;
+            }
+        }
+    });
+    if (over) return false;
+    int nib, sume;
+    team_tokens<1>(tc, true, nib, sume);
+    return pad32_bytes((uint32_t)H + 4u * (uint32_t)nib + 4u * (uint32_t)sume) <= budget;
+}
+
 // ---------------------------------------------------------------- block per thread
 // Fixed rate, a tile of blockDim.x blocks, one per thread (block sizes up to
 // kT1MaxBlock): the team functions run with a team of one, exponents sit in
@@ -478,13 +512,13 @@ __device__ __forceinline__ void encode_tile_t1(const EncArgs &a, uint64_t tile, 
     if (b.active && b.bad) set_status(a.status, -8);
     // BISECT against the block budget (Sec. 6 adaptive loop)
     const uint32_t budget = b.L == (int)a.N ? a.B : fr_budget<DT>(b.L, a.rate_num, a.rate_den);
-    const bool fits0 = pad32_bytes(team_eval1<DT, 1>(b, 0, s)) <= budget;
+    const bool fits0 = fits_t1<DT>(b, 0, s, budget);
     int lo = 0, hi = 4095;
     if (!fits0) {
 #pragma unroll 1
         for (int it = 0; it < 12 && hi - lo > 1; ++it) {  // 12 halvings close [0, 4095]
             const int mid = (lo + hi) >> 1;
-            if (pad32_bytes(team_eval1<DT, 1>(b, mid, s)) <= budget) hi = mid;
+            if (fits_t1<DT>(b, mid, s, budget)) hi = mid;
             else lo = mid;
         }
     }
