@@ -545,34 +545,36 @@ __device__ __forceinline__ void decode_block_t1(const DecArgs &a, const DecHdr &
     nwords = plen >> 2;
     int Eb = 0;
     if (T::F) Eb = (int)(int16_t)(word(1) & 0xffffu);
-    // LSB-first bit window over the packet words, with the next word loaded
-    // one refill ahead (its latency overlaps the fields before it is needed)
-    uint64_t acc = 0;
-    int fill = 0;
-    uint32_t wi = 0, nxt = 0;
+    // LSB-first bit reader: bits [p, p + 32) of the packet are the funnel
+    // shift of the word pair (c0, c1); the three words after c1 are loaded
+    // ahead, so a load's latency overlaps about ten fields before its word
+    // is needed.  Words past the packet read as zero; the bit count is
+    // checked against the packet length before any field is read.
+    uint32_t p = 0, wi = 0, c0 = 0, c1 = 0, n0 = 0, n1 = 0, n2 = 0;
     auto peek = [&](uint32_t i) -> uint32_t { return i < nwords ? __ldg(pw + i) : 0u; };
-    auto seek = [&](uint32_t bit) {  // bit <= 32 nwords; nothing is read at the very end
+    auto seek = [&](uint32_t bit) {
+        p = bit;
         wi = bit >> 5;
-        acc = 0;
-        fill = 0;
-        if (wi < nwords) {
-            acc = (uint64_t)__ldg(pw + wi) >> (bit & 31);
-            fill = 32 - (int)(bit & 31);
-            ++wi;
-        }
-        nxt = peek(wi);
+        c0 = peek(wi);
+        c1 = peek(wi + 1);
+        n0 = peek(wi + 2);
+        n1 = peek(wi + 3);
+        n2 = peek(wi + 4);
     };
-    auto take = [&](int k) -> uint32_t {  // 0 <= k <= 32
-        if (fill < k) {
-            bad |= wi >= nwords;  // past the packet
-            acc |= (uint64_t)nxt << fill;
+    // the next 32 bits (a field of k <= 32 bits is their low k bits), then
+    // moves k bits on: at most one word boundary is crossed
+    auto take = [&](uint32_t k) -> uint32_t {
+        const uint32_t v = __funnelshift_r(c0, c1, p);
+        const uint32_t np = p + k;
+        if ((np ^ p) >= 32u) {
+            c0 = c1;
+            c1 = n0;
+            n0 = n1;
+            n1 = n2;
             ++wi;
-            fill += 32;
-            nxt = peek(wi);
+            n2 = peek(wi + 4);
         }
-        const uint32_t v = (uint32_t)acc & (uint32_t)((1ull << k) - 1);
-        acc >>= k;
-        fill -= k;
+        p = np;
         return v;
     };
     // tokens (Sec. 6 JEE): absolute first, then joint / single / absolute
@@ -588,10 +590,10 @@ __device__ __forceinline__ void decode_block_t1(const DecArgs &a, const DecHdr &
         ++g;
     };
     while (g < G && !bad) {
-        const int nb = (int)take(4);
+        const int nb = (int)(take(4) & 15u);
         ++nib;
         if (nb >= 14) {
-            const int v = ((nb - 14) << 4) | (int)take(4);
+            const int v = ((nb - 14) << 4) | (int)(take(4) & 15u);
             ++nib;
             put(v == 31 ? 32 : v);
         } else if (g == 0) {
@@ -600,9 +602,10 @@ __device__ __forceinline__ void decode_block_t1(const DecArgs &a, const DecHdr &
             if (g + 1 >= G) {
                 bad = true;  // a joint token needs two diffs
             } else {
-                const int e1 = ep + nb / 3 - 1;
+                const int d1 = (nb * 11) >> 5;  // nb / 3 for nb <= 8
+                const int e1 = ep + d1 - 1;
                 put(e1);
-                put(e1 + nb % 3 - 1);
+                put(e1 + (nb - 3 * d1) - 1);
             }
         } else {
             put(ep + nb - 11);
@@ -617,35 +620,68 @@ __device__ __forceinline__ void decode_block_t1(const DecArgs &a, const DecHdr &
     const Dequant<DT> DQ(code, Eb);
     raw *yb = reinterpret_cast<raw *>(a.y) + (a.ranged ? (j - a.b0) * (uint64_t)N : off);
     seek((uint32_t)H + 4u * (uint32_t)nib);
-    uint32_t run = 0, runD = 0, u0 = 0;
-#pragma unroll 1
-    for (int gg = 0; gg < G; ++gg) {
-        const int e = eb[(size_t)gg * est];
+    // the four fields of a group, sign-extended from e bits (e = 0: zeros);
+    // two fields per read when they fit in 32 bits
+    auto fields = [&](int gg, int32_t (&u)[4]) {
+        const uint32_t e = eb[(size_t)gg * est];
+        if (e <= 16) {
+            const uint32_t v0 = take(2 * e), v1 = take(2 * e);
+            u[0] = bfe_s32(v0, 0, e);
+            u[1] = bfe_s32(v0, e, e);
+            u[2] = bfe_s32(v1, 0, e);
+            u[3] = bfe_s32(v1, e, e);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) u[i] = bfe_s32(take(e), 0, e);
+        }
+    };
+    auto emit = [&](int gg, const uint32_t (&q)[4]) {
         lt out[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const uint32_t f = take(e);
-            const uint32_t uv = e == 0 ? 0u : (uint32_t)sext_w(f, e);
-            uint32_t q;
-            if (s == 0) {
-                q = uv;
-            } else if (s == 1) {
-                run += uv;
-                q = run;
-            } else {
-                if (gg == 0 && i == 0) {
-                    u0 = uv;
-                } else {
-                    run += uv;
-                }
-                runD += run;
-                q = u0 + runD;
-            }
-            out[i] = DQ(sext_w(q, W));
-        }
+        for (int i = 0; i < 4; ++i) out[i] = DQ(sext_w(q[i], W));
         store4<DT>(yb, 4 * gg, L, out);
+    };
+    // the stream selector is fixed per packet: one loop per selector
+    if (s == 0) {
+#pragma unroll 1
+        for (int gg = 0; gg < G; ++gg) {
+            int32_t u[4];
+            fields(gg, u);
+            const uint32_t q[4] = {(uint32_t)u[0], (uint32_t)u[1], (uint32_t)u[2], (uint32_t)u[3]};
+            emit(gg, q);
+        }
+    } else if (s == 1) {
+        uint32_t run = 0;
+#pragma unroll 1
+        for (int gg = 0; gg < G; ++gg) {
+            int32_t u[4];
+            fields(gg, u);
+            uint32_t q[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) q[i] = run += (uint32_t)u[i];
+            emit(gg, q);
+        }
+    } else {
+        // second differences: the first field is the first value itself
+        uint32_t run = 0, runD = 0, u0 = 0;
+#pragma unroll 1
+        for (int gg = 0; gg < G; ++gg) {
+            int32_t u[4];
+            fields(gg, u);
+            if (gg == 0) {
+                u0 = (uint32_t)u[0];
+                u[0] = 0;
+            }
+            uint32_t q[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                run += (uint32_t)u[i];
+                runD += run;
+                q[i] = u0 + runD;
+            }
+            emit(gg, q);
+        }
     }
-    if (bad) set_status(a.status, -9);
 }
 
 // Size class of a container: teams of 32 for blocks above 4096 samples

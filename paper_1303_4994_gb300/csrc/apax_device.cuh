@@ -76,6 +76,15 @@ __device__ __forceinline__ int32_t sext_w(uint32_t v, int W)
     return W >= 32 ? (int32_t)v : ((int32_t)(v << (32 - W)) >> (32 - W));
 }
 
+// Bits [pos, pos + len) of v sign-extended from bit pos + len - 1 (len = 0
+// gives 0; pos + len <= 32 here).
+__device__ __forceinline__ int32_t bfe_s32(uint32_t v, uint32_t pos, uint32_t len)
+{
+    int32_t r;
+    asm("bfe.s32 %0, %1, %2, %3;" : "=r"(r) : "r"(v), "r"(pos), "r"(len));
+    return r;
+}
+
 // Round-half-to-even of t / 2^s, s >= 1, |t| < 2^62.
 __device__ __forceinline__ int64_t rne_shift_s64(int64_t t, int s)
 {
