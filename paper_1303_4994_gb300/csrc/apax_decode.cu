@@ -709,20 +709,23 @@ __global__ void __launch_bounds__(128) k_decode(DecArgs a)
             if (threadIdx.x == 0) set_status(a.status, hd.err);
         } else if (!LARGE && hd.N <= kT1MaxN &&
                    (a.ranged ? a.b1 - a.b0 : hd.nb) >= kT1MinBlocks) {
-            // a block per thread; CTAs take tiles of blockDim.x blocks from a
-            // counter (blocks differ in cost, a static stride leaves a tail)
+            // a block per thread, tiles of blockDim.x blocks.  A CTA's first
+            // tile is its own index (the block scheduler spreads CTAs evenly
+            // over the SMs; first-come tickets piled the tiles onto the SMs
+            // whose CTAs started first); later tiles come from a counter
+            // (blocks differ in cost, a static stride leaves a tail).
             const uint64_t jb = a.ranged ? a.b0 : 0, je = a.ranged ? a.b1 : hd.nb;
             const uint64_t per = blockDim.x;
             const uint64_t ntiles = (je - jb + per - 1) / per;
             __shared__ uint64_t s_tile;
-            while (true) {
-                __syncthreads();
-                if (threadIdx.x == 0) s_tile = atomicAdd(a.ticket, 1ull);
-                __syncthreads();
-                const uint64_t tile = s_tile;
-                if (tile >= ntiles) break;
+            uint64_t tile = blockIdx.x;
+            while (tile < ntiles) {
                 const uint64_t j = jb + tile * per + threadIdx.x;
                 if (j < je) decode_block_t1<DT>(a, hd, j, dsm + threadIdx.x, (int)blockDim.x);
+                __syncthreads();
+                if (threadIdx.x == 0) s_tile = gridDim.x + atomicAdd(a.ticket, 1ull);
+                __syncthreads();
+                tile = s_tile;
             }
         } else {
             const int nteams = blockDim.x / TS;
