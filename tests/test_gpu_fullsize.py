@@ -13,6 +13,10 @@ one, and properties that hold at any size are checked on everything.
   the first repeats the first copy's packets, except its first packet,
   whose lag decision sees the previous copy's last block (checked against
   the oracle).
+* float64 512^3 field (1 GiB, one call): profile (16 codes, r >= 0.99999)
+  -> fixed-quality encode at the recommended code -> decode, checked as the
+  float32 field is (sampled packets and decoded blocks against the oracle,
+  exact size prediction, r against an fp64 recomputation).
 * 40,000 blocks of float32 (the block-per-thread decoder's size): block
   ranges decode to the whole array's values, sampled packets equal the
   oracle's, and a reserved stream selector is reported as corrupt.
@@ -53,16 +57,18 @@ def _packets(container: bytes, nb: int, mode: int, budget: int = 0):
     return out
 
 
-def test_field_4096_full_size_sampled_parity():
-    x = synth.grf2d(4096, 4096, seed=1).reshape(-1)
+def _profiled_fq_parity(x, dtype, target, seed):
+    """Profile -> fixed-quality encode at the recommended code -> decode on
+    the whole array; sampled blocks against the oracle."""
     n = x.size
     xt = torch.from_numpy(x).cuda()
     nc = 16
     pws, pts, summ = A.profile_buffers(xt, N, nc)
-    A.profile_into(xt, N, list(A.DEFAULT_CANDIDATES), 0.9999, pws, pts, summ)
+    A.profile_into(xt, N, list(A.DEFAULT_CANDIDATES), target, pws, pts, summ)
     p = A.params(N, A.FIXED_QUALITY)
-    out = torch.empty(A.encoded_size(A.F32, n, p), dtype=torch.uint8, device="cuda")
-    ws = torch.empty(A.workspace_size(A.F32, n, p), dtype=torch.uint8, device="cuda")
+    tcode = A.F32 if dtype == np.float32 else A.F64
+    out = torch.empty(A.encoded_size(tcode, n, p), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(A.workspace_size(tcode, n, p), dtype=torch.uint8, device="cuda")
     res = A.new_result("cuda")
     A.encode_into(xt, p, out, ws, res, summary=summ)
     torch.cuda.synchronize()
@@ -71,25 +77,40 @@ def test_field_4096_full_size_sampled_parity():
     assert sm.status == 0 and r.status == 0
     code = int(sm.recommended_code)
     point = A.read_points(pts, nc)[sm.recommended]
-    assert point.code == code and point.r >= 0.9999
+    assert point.code == code and point.r >= target
     assert point.bytes == r.bytes  # exact size prediction
+    del ws, pws
     cont = out[:r.bytes].cpu().numpy().tobytes()
-    y = A.decode(out[:r.bytes], torch.float32, n)
-    yd = y.double()
+    y = A.decode(out[:r.bytes], torch.float32 if dtype == np.float32 else torch.float64, n)
+    del out
     xd = xt.double()
+    yd = y.double()
     r64 = float((xd * yd).sum() / torch.sqrt((xd * xd).sum() * (yd * yd).sum()))
     assert abs(r64 - point.r) < 1e-12
+    del xd, yd
     nb = n // N
     pk = _packets(cont, nb, 1)
-    yh = y.cpu().numpy()
-    rng = np.random.default_rng(41)
+    ui = np.uint32 if dtype == np.float32 else np.uint64
+    rng = np.random.default_rng(seed)
     for j in [1, 2, nb - 1] + [int(v) for v in rng.integers(1, nb, 40)]:
         want = O.encode_blocks(x, N, O.MODE_FQ, 1, 1, code, j, j + 1)[0]
         assert pk[j] == want, j
         sub = x[(j - 1) * N:(j + 1) * N]
-        ysub = O.decode(O.encode(sub, N, O.MODE_FQ, 1, 1, code), np.float32, 2 * N)
-        np.testing.assert_array_equal(yh[j * N:(j + 1) * N].view(np.uint32),
-                                      ysub[N:].view(np.uint32))
+        ysub = O.decode(O.encode(sub, N, O.MODE_FQ, 1, 1, code), dtype, 2 * N)
+        got = y[j * N:(j + 1) * N].cpu().numpy()
+        np.testing.assert_array_equal(got.view(ui), ysub[N:].view(ui))
+    return point
+
+
+def test_field_4096_full_size_sampled_parity():
+    _profiled_fq_parity(synth.grf2d(4096, 4096, seed=1).reshape(-1), np.float32, 0.9999, 41)
+
+
+def test_field3d_512_full_size_sampled_parity():
+    # the 1 GiB float64 simulation field, encoded and decoded in one call each
+    x = synth.field3d(512, seed=2).reshape(-1)
+    point = _profiled_fq_parity(x, np.float64, 0.99999, 42)
+    assert point.code > 0  # a lossy setting was chosen
 
 
 def test_sensor_replica_repeats_packets():
