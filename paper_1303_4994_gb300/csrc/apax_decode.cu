@@ -641,8 +641,37 @@ __device__ __forceinline__ void decode_block_t1(const DecArgs &a, const DecHdr &
         for (int i = 0; i < 4; ++i) out[i] = DQ(sext_w(q[i], W));
         store4<DT>(yb, 4 * gg, L, out);
     };
-    // the stream selector is fixed per packet: one loop per selector
-    if (s == 0) {
+    // One loop per stream selector when every converged lane has the same
+    // one (lanes decode different blocks: mixed selectors would run the
+    // loops one after another), else one loop that branches per sample.
+    // float64 keeps the one loop: its dequantiser makes copies costly.
+    const unsigned am = __activemask();
+    const bool uniform = DT != 5 && __all_sync(am, s == __shfl_sync(am, s, __ffs(am) - 1));
+    if (!uniform) {
+        uint32_t run = 0, runD = 0, u0 = 0;
+#pragma unroll 1
+        for (int gg = 0; gg < G; ++gg) {
+            int32_t u[4];
+            fields(gg, u);
+            uint32_t q[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const uint32_t uv = (uint32_t)u[i];
+                if (s == 0) {
+                    q[i] = uv;
+                } else if (s == 1) {
+                    run += uv;
+                    q[i] = run;
+                } else {
+                    if (gg == 0 && i == 0) u0 = uv;  // second differences start from the first value
+                    else run += uv;
+                    runD += run;
+                    q[i] = u0 + runD;
+                }
+            }
+            emit(gg, q);
+        }
+    } else if (s == 0) {
 #pragma unroll 1
         for (int gg = 0; gg < G; ++gg) {
             int32_t u[4];
