@@ -99,7 +99,7 @@ Geo geo_of(const apax_batch *b, const apax_batch_config &c)
 
 // Fixed-rate arrays with blocks of at most 1024 samples are encoded one
 // block per thread (the search runs without team exchanges).
-bool t1_job(const EncArgs &a) { return a.mode == APAX_FIXED_RATE && a.N <= kEncT1MaxBlock; }
+bool t1_job(const EncArgs &a) { return a.mode == APAX_FIXED_RATE && a.N <= kT1MaxBlock; }
 
 size_t pkt_smem_of(const apax_batch *b, const Geo &g)
 {
@@ -333,7 +333,7 @@ int apply_decode_config(apax_batch *b, const apax_batch_config &c)
         DecArgs &a = tab[i];
         const uint64_t nb = (a.n + b->dN[i] - 1) / b->dN[i];
         // blocks of up to 1024 samples: one per thread, tiles of `threads` blocks
-        const uint64_t per = b->dN[i] <= kDecT1MaxBlock ? c.threads : (uint64_t)nteams;
+        const uint64_t per = b->dN[i] <= kT1MaxBlock ? c.threads : (uint64_t)nteams;
         tiles[i] = nb ? (nb + per - 1) / per : 1;
         a.done = (unsigned *)(b->ws + L.counters + 16 * (size_t)i);
         a.status = (int *)(b->ws + L.counters + 16 * (size_t)i + 4);

@@ -495,12 +495,10 @@ __device__ __forceinline__ void decode_tile(const DecArgs &a, const DecHdr &hd, 
     }
 }
 
-// One block by one thread (block sizes up to kT1MaxN): header, the JEE
+// One block by one thread (block sizes up to kT1MaxBlock): header, the JEE
 // tokens in order, then the mantissas, inverse derivatives and
 // dequantisation in one sequential pass -- no team scans.  eb is this
 // thread's column of exponent bytes (stride est).
-constexpr uint32_t kT1MaxN = 1024;
-constexpr uint64_t kT1MinBlocks = 32768;  // fewer blocks leave SMs idle: use teams
 
 template <int DT>
 __device__ __forceinline__ void decode_block_t1(const DecArgs &a, const DecHdr &hd, uint64_t j,
@@ -736,7 +734,7 @@ __global__ void __launch_bounds__(128) k_decode(DecArgs a)
     if (my_class<EB>(hd)) {
         if (hd.err) {
             if (threadIdx.x == 0) set_status(a.status, hd.err);
-        } else if (!LARGE && hd.N <= kT1MaxN &&
+        } else if (!LARGE && hd.N <= kT1MaxBlock &&
                    (a.ranged ? a.b1 - a.b0 : hd.nb) >= kT1MinBlocks) {
             // a block per thread, tiles of blockDim.x blocks.  A CTA's first
             // tile is its own index (the block scheduler spreads CTAs evenly
@@ -838,7 +836,7 @@ __global__ void __launch_bounds__(128) k_decode_batch(DecBatchArgs ba)
         }
         __syncthreads();
         const DecHdr hd = s_h;
-        if (hd.err == 0 && ba.block_size[s_job] <= kT1MaxN) {
+        if (hd.err == 0 && ba.block_size[s_job] <= kT1MaxBlock) {
             // a block per thread: the plan made this array's tiles blockDim.x blocks
             const uint64_t j = s_tile * blockDim.x + threadIdx.x;
             if (j < hd.nb) {
@@ -882,7 +880,7 @@ static cudaError_t launch_one(const DecArgs &a, unsigned ctas, cudaStream_t s)
 {
     constexpr int threads = 128;
     size_t smem = (size_t)(threads / TS) * EB;
-    if (EB <= 1024 && smem < (size_t)threads * (kT1MaxN / 4)) smem = (size_t)threads * (kT1MaxN / 4);
+    if (EB <= 1024 && smem < (size_t)threads * (kT1MaxBlock / 4)) smem = (size_t)threads * (kT1MaxBlock / 4);
     auto k = k_decode<DT, TS, EB>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -903,7 +901,7 @@ static cudaError_t launch_dt(const DecArgs &a, cudaStream_t s)
 static size_t decode_batch_smem(int ts, int threads)
 {
     const size_t teams = (size_t)(threads / ts) * (ts == 8 ? 1024 : 4096);
-    const size_t cols = (size_t)threads * (kT1MaxN / 4);  // block-per-thread exponent columns
+    const size_t cols = (size_t)threads * (kT1MaxBlock / 4);  // block-per-thread exponent columns
     return teams > cols ? teams : cols;
 }
 

@@ -482,7 +482,6 @@ __device__ __forceinline__ bool fits_t1(const TBlock<DT> &b, int code, int s, ui
 // kT1MaxBlock): the team functions run with a team of one, exponents sit in
 // a lane-interleaved shared-memory column (smem bytes g * blockDim.x +
 // thread), and each thread writes its own packet straight to its place j*B.
-constexpr uint32_t kT1MaxBlock = 1024;
 
 template <int DT>
 __device__ __forceinline__ void encode_tile_t1(const EncArgs &a, uint64_t tile, uint8_t *smem)

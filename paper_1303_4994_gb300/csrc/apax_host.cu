@@ -121,7 +121,7 @@ int encode_impl(const void *x, int dtype, uint64_t n, const apax_params *p,
     if (wsb < need_ws) return APAX_ERR_CAPACITY;
     int ts, threads;
     Plan pl;
-    if (p->mode == APAX_FIXED_RATE && a.N <= kEncT1MaxBlock && a.nb >= kEncT1MinBlocks &&
+    if (p->mode == APAX_FIXED_RATE && a.N <= kT1MaxBlock && a.nb >= kT1MinBlocks &&
         stage_policy() != 1) {
         // fixed rate, a block per thread: its 13-step search runs without
         // team exchanges (measured faster); fixed quality keeps teams, whose

@@ -9,6 +9,13 @@
 
 namespace apax {
 
+// Block-per-thread paths (decode and the fixed-rate search): block sizes up
+// to kT1MaxBlock samples; a single array takes them when it has at least
+// kT1MinBlocks blocks (fewer leave SMs idle, so teams are used), a batch
+// always does.
+constexpr uint32_t kT1MaxBlock = 1024;
+constexpr uint64_t kT1MinBlocks = 32768;
+
 struct EncArgs {
     const void *x;
     uint64_t n;

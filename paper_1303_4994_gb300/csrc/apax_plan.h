@@ -88,9 +88,6 @@ inline void team_words(const Fmt &f, uint32_t N, uint64_t fr_budget_bytes, uint3
 }
 
 constexpr size_t kEncSmemCap = 200 * 1024;
-constexpr uint32_t kEncT1MaxBlock = 1024;  // block sizes encoded one block per thread
-constexpr uint64_t kEncT1MinBlocks = 32768;  // ... for arrays with enough blocks to fill the GPU
-constexpr uint32_t kDecT1MaxBlock = 1024;    // batched decode: blocks decoded one per thread
 
 // Geometry for a given team size and CTA size.
 inline Plan plan_geometry(uint32_t N, uint64_t nb, uint32_t pkt_words, uint32_t ebuf_words, int ts,
