@@ -452,28 +452,34 @@ __device__ __forceinline__ bool fits_t1(const TBlock<DT> &b, int code, int s, ui
 {
     constexpr int H = DT_<DT>::H;
     const Quant<DT> Q(code, b.Eb);
-    TokCount tc;
-    tc.init();
+    // the greedy JEE count of one whole block in one thread: the first
+    // exponent is absolute (2 nibbles), then the TokCount transitions
+    int nib = 0, sume = 0, e_last = 0;
+    bool st = false;
     const uint32_t limit = 8u * budget;  // bits; budget is a multiple of 4 bytes
     bool over = false;
     with_quant<DT>(Q, [&](const auto &qf) {
-        Stream1 st(s, carry_in<DT>(b, qf, 0));
+        Stream1 sm(s, carry_in<DT>(b, qf, 0));
 #pragma unroll 1
         for (int g = 0; g < b.G; ++g) {
             typename LaneT<DT>::t xv[4];
             load4<DT, true>(b, 4 * g, xv);
             int32_t u[4];
-            tc.push(exp_from_or(group1<DT>(qf, xv, st, u)), true);
-            if ((g & 7) == 7 &&
-                (uint32_t)H + 4u * (2u + (uint32_t)tc.nib) + 4u * (uint32_t)tc.sume > limit) {
+            const int e = exp_from_or(group1<DT>(qf, xv, sm, u));
+            const int d = e - e_last;
+            const bool small = (unsigned)(d + 1) <= 2u;
+            const int inc = small ? (st ? 0 : 1) : ((unsigned)(d + 2) <= 4u ? 1 : 2);
+            nib += g == 0 ? 2 : inc;
+            st = g != 0 && small && !st;
+            sume += e;
+            e_last = e;
+            if ((g & 7) == 7 && (uint32_t)H + 4u * (uint32_t)nib + 4u * (uint32_t)sume > limit) {
                 over = true;
                 break;
             }
         }
     });
     if (over) return false;
-    int nib, sume;
-    team_tokens<1>(tc, true, nib, sume);
     return pad32_bytes((uint32_t)H + 4u * (uint32_t)nib + 4u * (uint32_t)sume) <= budget;
 }
 

@@ -171,12 +171,8 @@ struct Quant {
     int mode;     // 0 exact integer, 1 fused (k >= 1), 2 convert (k = 0, m = 0),
                   // 3 small int, 4 fused signed (k = 0, m > 0)
     float scale;  // b
-    int32_t mul, sh, bias;
     __device__ __forceinline__ Quant(int code, int eb) : c(code), Eb(eb), mode(0), scale(0.f)
     {
-        mul = 0;
-        sh = 1;
-        bias = 0;
         if constexpr (DT == 4) {
             const int se = 15 - eb - c.k;  // b = (256 - m) 2^se; 2^(se+8) for m = 0
             if (!c.zero && se + 8 >= -126 && se + 8 <= 127 && se >= -126) {
@@ -185,12 +181,11 @@ struct Quant {
             }
         }
         if constexpr (DT == 1 || DT == 2) {
-            // |x (256 - m)| < 2^23: a shift of 25 or more rounds to 0
+            // a = (256 - m) 2^-(8+k) as a float (exact, normal for k <= 31);
+            // x a has at most 24 significant bits and |x a| <= 2^15, so one
+            // FMA with 1.5 2^23 rounds it to the nearest integer, ties to even
             mode = 3;
-            const int s0 = 8 + c.k;
-            mul = (c.zero || s0 >= 25) ? 0 : 256 - c.m;
-            sh = s0 >= 25 ? 24 : s0;
-            bias = (1 << (sh - 1)) - 1;
+            scale = c.zero ? 0.f : __fmul_rn((float)(256 - c.m), __int_as_float((119 - c.k) << 23));
         }
     }
     __device__ __forceinline__ int32_t operator()(typename LaneT<DT>::t v) const
@@ -209,8 +204,8 @@ struct Quant {
             }
         }
         if constexpr (DT == 1 || DT == 2) {
-            const int32_t t = (int32_t)v * mul;
-            return (t + bias + ((t >> sh) & 1)) >> sh;
+            const float t = __fmaf_rn((float)(int32_t)v, scale, 12582912.0f);
+            return __float_as_int(t) - 0x4B400000;
         }
         return quantise<DT>(v, c, Eb);
     }
@@ -238,8 +233,8 @@ struct QuantM {
             const int32_t a = (__float_as_int(t) & 0x7fffffff) - 0x4B000000;
             return sg ? -a : a;
         } else if constexpr ((DT == 1 || DT == 2) && M == 3) {
-            const int32_t t = (int32_t)v * Q.mul;
-            return (t + Q.bias + ((t >> Q.sh) & 1)) >> Q.sh;
+            const float t = __fmaf_rn((float)(int32_t)v, Q.scale, 12582912.0f);
+            return __float_as_int(t) - 0x4B400000;
         } else {
             return quantise<DT>(v, Q.c, Q.Eb);
         }
