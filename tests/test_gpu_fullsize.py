@@ -161,3 +161,32 @@ def test_large_array_block_range_and_corruption():
         _, r = A.decode(torch.frombuffer(bad, dtype=torch.uint8).cuda(), torch.float32, x.size,
                         check=False)
         assert r.status == -9
+
+
+@pytest.mark.parametrize("kind", ["noise", "walk", "sine"])
+def test_block_per_thread_decode_selector_loops(kind):
+    # 40,000 blocks of 64 int16 samples (the block-per-thread decoder): white
+    # noise, a random walk and a slow sinusoid make nearly every block take
+    # stream 0, 1 and 2 respectively, so warps see one selector (the
+    # per-selector loops); the few others mix within their warps
+    rng = np.random.default_rng({"noise": 51, "walk": 52, "sine": 53}[kind])
+    nb, n64 = 40000, 64
+    n = nb * n64 - 17  # ragged last block
+    if kind == "noise":
+        x = rng.integers(-3000, 3000, n).astype(np.int16)
+    elif kind == "walk":
+        x = np.clip(np.cumsum(rng.integers(-300, 301, n)), -32768, 32767).astype(np.int16)
+    else:
+        t = np.arange(n)
+        x = np.rint(20000 * np.sin(t * 0.002) + rng.normal(0, 0.3, n)).astype(np.int16)
+    xt = torch.from_numpy(x).cuda()
+    c = A.encode(xt, n64, A.FIXED_QUALITY, (1, 1), 0)
+    cont = c.cpu().numpy().tobytes()
+    pk = _packets(cont, nb, 1)
+    sel = np.array([p[0] & 3 for p in pk])
+    want_s = {"noise": 0, "walk": 1, "sine": 2}[kind]
+    assert (sel == want_s).mean() > 0.9, np.bincount(sel, minlength=3)
+    y = A.decode(c, torch.int16, n).cpu().numpy()
+    np.testing.assert_array_equal(y, x)  # code 0 is lossless for int16
+    for j in (1, 2, 777, 31999, nb - 1):
+        assert pk[j] == O.encode_blocks(x, n64, O.MODE_FQ, 1, 1, 0, j, j + 1)[0], j
