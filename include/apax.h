@@ -182,6 +182,23 @@ int apax_profile(const void *x, int dtype, uint64_t n, uint32_t block_size,
                  void *workspace, uint64_t workspace_bytes, apax_profile_point *points,
                  apax_profile_summary *summary, void *stream);
 
+/* apax_profile for an array in page-locked host memory (x_host, e.g. from
+ * cudaHostAlloc), leaving its copy in x_dev (device, n elements of dtype):
+ * the array goes to the device in `chunks` pieces (1..64, whole runs of 16
+ * blocks each) with cudaMemcpyAsync on copy_stream, and each piece is swept
+ * as soon as it is there, on one of four library-owned streams (created on
+ * first use per device), so the copy hides behind the sweep.  The copies and
+ * sweeps first wait for the work queued on `stream` before the call; work
+ * queued on `stream` after it sees x_dev, points and summary.  Results are
+ * identical to apax_profile on x_dev.  copy_stream must differ from stream.
+ * Asynchronous: no host synchronisation; the events it uses are released by
+ * the driver once complete. */
+int apax_profile_from_host(const void *x_host, void *x_dev, int dtype, uint64_t n,
+                           uint32_t block_size, const uint16_t *candidates /* host */, int ncand,
+                           double target, int chunks, void *workspace, uint64_t workspace_bytes,
+                           apax_profile_point *points, apax_profile_summary *summary,
+                           void *stream, void *copy_stream);
+
 /* Derived metrics of one profile point (host call): r, centred Pearson r,
  * time-domain SNR in dB = 10 log10(sum x^2 / sum d^2), RMS residual in
  * percent and in dB (Table 3's two RMS columns), and means and population

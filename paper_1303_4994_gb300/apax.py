@@ -111,7 +111,8 @@ _lib = None
 
 EXPORTS = ("apax_encoded_size", "apax_workspace_size", "apax_encode", "apax_encode_recommended",
            "apax_decode_workspace_size", "apax_decode", "apax_decode_blocks",
-           "apax_profile_workspace_size", "apax_profile", "apax_derived_metrics",
+           "apax_profile_workspace_size", "apax_profile", "apax_profile_from_host",
+           "apax_derived_metrics",
            "apax_encode_test_stall", "apax_status_string", "apax_build_info",
            "apax_encode_noalloc", "apax_batch_encode_workspace_size", "apax_batch_encode_create",
            "apax_batch_run", "apax_batch_get_config", "apax_batch_set_config", "apax_batch_tune",
@@ -144,6 +145,8 @@ def lib():
         L.apax_profile_workspace_size.argtypes = [i32, u64, u32, i32, p64]
         L.apax_profile.argtypes = [vp, i32, u64, u32, vp, i32, ctypes.c_double, vp, u64, vp, vp,
                                    vp]
+        L.apax_profile_from_host.argtypes = [vp, vp, i32, u64, u32, vp, i32, ctypes.c_double, i32,
+                                             vp, u64, vp, vp, vp, vp]
         L.apax_derived_metrics.argtypes = [ctypes.POINTER(Point), u64, vp]
         L.apax_derived_metrics.restype = None
         L.apax_encode_test_stall.argtypes = [vp, i32, u64, pP, vp, u64, vp, u64, vp,
@@ -189,6 +192,17 @@ def _stream(stream) -> int:
     if stream is None:
         stream = torch.cuda.current_stream()
     return stream.cuda_stream
+
+
+_SIDE = {}
+
+
+def _side_stream(device) -> torch.cuda.Stream:
+    """One non-default stream per device for host-to-device copies."""
+    key = torch.device(device).index
+    if key not in _SIDE:
+        _SIDE[key] = torch.cuda.Stream(device=device)
+    return _SIDE[key]
 
 
 def _dtype_code(t: torch.Tensor) -> int:
@@ -578,6 +592,30 @@ def profile_into(x: torch.Tensor, block_size: int, candidates, target: float,
     _check(lib().apax_profile(xf.data_ptr(), code, xf.numel(), block_size, cptr, nc, target,
                               workspace.data_ptr(), workspace.numel(), points.data_ptr(),
                               summary.data_ptr(), _stream(stream)), "profile")
+
+
+def profile_from_host_into(x_host: torch.Tensor, x_dev: torch.Tensor, block_size: int,
+                           candidates, target: float, workspace: torch.Tensor,
+                           points: torch.Tensor, summary: torch.Tensor, stream=None,
+                           copy_stream=None, chunks: int = 8):
+    """apax_profile_from_host: x_host (pinned CPU tensor) is copied into x_dev
+    in `chunks` pieces on copy_stream (default: a side stream of this module)
+    while the sweep runs on stream."""
+    xf, xd = x_host.reshape(-1), x_dev.reshape(-1)
+    if copy_stream is None:
+        copy_stream = _side_stream(xd.device)
+    assert not xf.is_cuda and xd.is_cuda and (xf.numel() == 0 or xf.is_pinned())
+    assert xf.dtype == xd.dtype and xf.numel() == xd.numel()
+    if candidates is None:
+        cptr, nc = None, 16
+    else:
+        arr = (ctypes.c_uint16 * len(candidates))(*candidates)
+        cptr, nc = ctypes.cast(arr, ctypes.c_void_p), len(candidates)
+    _check(lib().apax_profile_from_host(xf.data_ptr(), xd.data_ptr(), _dtype_code(xd), xd.numel(),
+                                        block_size, cptr, nc, target, chunks,
+                                        workspace.data_ptr(), workspace.numel(),
+                                        points.data_ptr(), summary.data_ptr(), _stream(stream),
+                                        copy_stream.cuda_stream), "profile_from_host")
 
 
 def profile_buffers(x: torch.Tensor, block_size: int, ncand: int):

@@ -3,6 +3,10 @@
 #include <math.h>
 #include <string.h>
 
+#include <array>
+#include <map>
+#include <mutex>
+
 #include "apax_team.cuh"
 #include "apax_kernels.h"
 #include "apax_plan.h"
@@ -207,6 +211,44 @@ int decode_impl(const void *in, uint64_t in_bytes, uint64_t b0, uint64_t b1, boo
     return cuda_fail(launch_decode(a, s));
 }
 
+// Streams on which the host-input sweep runs its pieces: created once per
+// device (non-blocking, for the life of the process) and reused.
+constexpr int kSweepStreams = 4;
+static bool sweep_streams(cudaStream_t (&out)[kSweepStreams])
+{
+    static std::mutex mu;
+    static std::map<int, std::array<cudaStream_t, kSweepStreams>> pool;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = pool.find(dev);
+    if (it == pool.end()) {
+        std::array<cudaStream_t, kSweepStreams> a{};
+        for (int k = 0; k < kSweepStreams; ++k) {
+            if (cudaStreamCreateWithFlags(&a[k], cudaStreamNonBlocking) != cudaSuccess) {
+                for (int i = 0; i < k; ++i) cudaStreamDestroy(a[i]);
+                return false;
+            }
+        }
+        it = pool.emplace(dev, a).first;
+    }
+    for (int k = 0; k < kSweepStreams; ++k) out[k] = it->second[k];
+    return true;
+}
+
+// Workspace layout of a profile: head (done, status), per-candidate byte
+// counters, the run sums, then the tree scratch.
+static void place_profile_workspace(ProfArgs &a, void *workspace)
+{
+    uint8_t *w = (uint8_t *)workspace;
+    a.done = (unsigned *)(w + 4);
+    a.status = (int *)(w + 8);
+    a.bytes = (unsigned long long *)(w + kWsHead);
+    const uint64_t Qn = 2 + 4 * (uint64_t)a.ncand;
+    a.run_sums = (double *)(w + kWsHead + 8 * 32);
+    a.scratch = a.run_sums + Qn * (a.nruns ? a.nruns : 1);
+}
+
 }  // namespace
 
 namespace apax {
@@ -338,17 +380,96 @@ int apax_profile(const void *x, int dtype, uint64_t n, uint32_t block_size,
     st = apax_profile_workspace_size(dtype, n, block_size, ncand, &need);
     if (st) return st;
     if (workspace_bytes < need) return APAX_ERR_CAPACITY;
-    uint8_t *w = (uint8_t *)workspace;
-    a.done = (unsigned *)(w + 4);
-    a.status = (int *)(w + 8);
-    a.bytes = (unsigned long long *)(w + kWsHead);
-    const uint64_t Qn = 2 + 4 * (uint64_t)ncand;
-    a.run_sums = (double *)(w + kWsHead + 8 * 32);
-    a.scratch = a.run_sums + Qn * (a.nruns ? a.nruns : 1);
+    place_profile_workspace(a, workspace);
     cudaStream_t s = (cudaStream_t)stream;
     st = cuda_fail(cudaMemsetAsync(workspace, 0, kWsHead + 8 * 32, s));
     if (st) return st;
     return cuda_fail(launch_profile(a, s));
+}
+
+int apax_profile_from_host(const void *x_host, void *x_dev, int dtype, uint64_t n,
+                           uint32_t block_size, const uint16_t *candidates, int ncand,
+                           double target, int chunks, void *workspace, uint64_t workspace_bytes,
+                           apax_profile_point *points, apax_profile_summary *summary,
+                           void *stream, void *copy_stream)
+{
+    ProfArgs a;
+    int st = fill_prof_args(x_dev, dtype, n, block_size, candidates, ncand, target, points,
+                            summary, a);
+    if (st) return st;
+    if ((!x_host && n) || chunks < 1 || chunks > 64 || stream == copy_stream)
+        return APAX_ERR_INVALID_ARG;
+    if (!workspace || ((uintptr_t)workspace & 15)) return APAX_ERR_INVALID_ARG;
+    uint64_t need;
+    st = apax_profile_workspace_size(dtype, n, block_size, ncand, &need);
+    if (st) return st;
+    if (workspace_bytes < need) return APAX_ERR_CAPACITY;
+    place_profile_workspace(a, workspace);
+    Fmt f;
+    fmt_of(dtype, f);
+    cudaStream_t s = (cudaStream_t)stream, cs = (cudaStream_t)copy_stream;
+    st = cuda_fail(cudaMemsetAsync(workspace, 0, kWsHead + 8 * 32, s));
+    if (st) return st;
+    // Fork: the copies and the sweep streams wait for the work already
+    // queued on `stream` (which may still read x_dev).  Piece c goes over on
+    // copy_stream; its runs go on sweep stream c mod kSweepStreams once the
+    // piece is there, so pieces' sweeps overlap one another as well as the
+    // later copies (a piece is a fraction of a wave).  Join: `stream` waits
+    // for every sweep stream, then sums the tree.
+    cudaStream_t ss[kSweepStreams];
+    if (!sweep_streams(ss)) return APAX_ERR_CUDA;
+    cudaEvent_t ev[2 + 64 + kSweepStreams];
+    int nev = 0;
+    auto fail = [&](cudaError_t e) {
+        for (int i = 0; i < nev; ++i) cudaEventDestroy(ev[i]);
+        return cuda_fail(e);
+    };
+    auto event = [&](cudaEvent_t *out) {
+        const cudaError_t e = cudaEventCreateWithFlags(&ev[nev], cudaEventDisableTiming);
+        if (e == cudaSuccess) *out = ev[nev++];
+        return e;
+    };
+    cudaEvent_t fork;
+    cudaError_t e = event(&fork);
+    if (e != cudaSuccess) return fail(e);
+    if ((e = cudaEventRecord(fork, s)) != cudaSuccess || (e = cudaStreamWaitEvent(cs, fork, 0)) != cudaSuccess)
+        return fail(e);
+    const int nss = chunks < kSweepStreams ? chunks : kSweepStreams;
+    for (int k = 0; k < nss; ++k)
+        if ((e = cudaStreamWaitEvent(ss[k], fork, 0)) != cudaSuccess) return fail(e);
+    const uint64_t R = a.nruns, per_run = 16ull * block_size;
+    for (int c = 0; c < chunks; ++c) {
+        const uint64_t r0 = R * (uint64_t)c / (uint64_t)chunks, r1 = R * (uint64_t)(c + 1) / (uint64_t)chunks;
+        if (r1 <= r0) continue;
+        const uint64_t e0 = r0 * per_run, e1 = r1 * per_run < n ? r1 * per_run : n;
+        e = cudaMemcpyAsync((uint8_t *)x_dev + e0 * f.size, (const uint8_t *)x_host + e0 * f.size,
+                            (e1 - e0) * f.size, cudaMemcpyHostToDevice, cs);
+        if (e != cudaSuccess) return fail(e);
+        cudaEvent_t landed;
+        if ((e = event(&landed)) != cudaSuccess) return fail(e);
+        cudaStream_t sk = ss[c % nss];
+        if ((e = cudaEventRecord(landed, cs)) != cudaSuccess || (e = cudaStreamWaitEvent(sk, landed, 0)) != cudaSuccess)
+            return fail(e);
+        ProfArgs b = a;
+        b.run0 = r0;
+        b.run1 = r1;
+        if ((e = launch_profile_runs(b, sk)) != cudaSuccess) return fail(e);
+    }
+    // join: the copy stream (every piece is on the device) and the sweeps
+    cudaEvent_t jc;
+    if ((e = event(&jc)) != cudaSuccess) return fail(e);
+    if ((e = cudaEventRecord(jc, cs)) != cudaSuccess || (e = cudaStreamWaitEvent(s, jc, 0)) != cudaSuccess)
+        return fail(e);
+    for (int k = 0; k < nss; ++k) {
+        cudaEvent_t j;
+        if ((e = event(&j)) != cudaSuccess) return fail(e);
+        if ((e = cudaEventRecord(j, ss[k])) != cudaSuccess || (e = cudaStreamWaitEvent(s, j, 0)) != cudaSuccess)
+            return fail(e);
+    }
+    e = launch_profile_tree(a, s);
+    // events recorded and waited on are released by the driver once complete
+    for (int i = 0; i < nev; ++i) cudaEventDestroy(ev[i]);
+    return cuda_fail(e);
 }
 
 static double corr_host(double sxx, double sxy, double syy)

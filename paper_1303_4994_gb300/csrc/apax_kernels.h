@@ -95,6 +95,7 @@ struct ProfArgs {
     int ncand;
     uint32_t codes[32];
     uint64_t nruns;     // level-1 nodes (16 blocks each)
+    uint64_t run0, run1; // runs swept by one launch of the run kernel
     uint32_t stage_off; // byte offset of the staged run in shared memory (0: none)
     int gp;             // groups per team thread
     double *run_sums;   // [nruns][2 + 4*ncand]: sx, sxx, then (sy, sxy, syy, sdd) per candidate
@@ -116,7 +117,9 @@ cudaError_t launch_decode(const DecArgs &a, cudaStream_t s);
 cudaError_t launch_decode_batch(const DecBatchArgs &b, int ts, int threads, unsigned ctas,
                                cudaStream_t s);
 int decode_batch_occupancy(int ts, int threads);
-cudaError_t launch_profile(const ProfArgs &a, cudaStream_t s);
+cudaError_t launch_profile(const ProfArgs &a, cudaStream_t s);       // all runs, then the tree
+cudaError_t launch_profile_runs(const ProfArgs &a, cudaStream_t s);  // runs [a.run0, a.run1)
+cudaError_t launch_profile_tree(const ProfArgs &a, cudaStream_t s);  // tree and finalisation
 
 // Many arrays' profiler sweeps in one launch: jobs[i] owns global runs
 // [run_prefix[i], run_prefix[i + 1]) (at least one, to finalise empty arrays).

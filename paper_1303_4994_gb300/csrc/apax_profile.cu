@@ -675,7 +675,7 @@ template <int DT>
 __global__ void __launch_bounds__(128) k_profile(ProfArgs a)
 {
     extern __shared__ __align__(16) uint8_t psm[];
-    profile_run<DT>(a, blockIdx.x, psm);
+    profile_run<DT>(a, a.run0 + blockIdx.x, psm);
 }
 
 // One level of the fan-in-16 tree: out[m][q] = in[16m][q] + ... (in order).
@@ -864,7 +864,7 @@ cudaError_t launch_prof_dt(const ProfArgs &a, cudaStream_t s)
     auto k = k_profile<DT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    if (a.nruns) k<<<(unsigned)a.nruns, threads, smem, s>>>(b);
+    if (a.run1 > a.run0) k<<<(unsigned)(a.run1 - a.run0), threads, smem, s>>>(b);
     return cudaGetLastError();
 }
 
@@ -902,17 +902,31 @@ int profile_batch_occupancy(int max_ncand)
     return nb;
 }
 
+cudaError_t launch_profile_runs(const ProfArgs &a, cudaStream_t s)
+{
+    if (a.run0 > a.run1 || a.run1 > a.nruns) return cudaErrorInvalidValue;
+    switch (a.dtype) {
+    case 1: return launch_prof_dt<1>(a, s);
+    case 2: return launch_prof_dt<2>(a, s);
+    case 3: return launch_prof_dt<3>(a, s);
+    case 4: return launch_prof_dt<4>(a, s);
+    default: return launch_prof_dt<5>(a, s);
+    }
+}
+
 cudaError_t launch_profile(const ProfArgs &a, cudaStream_t s)
 {
-    cudaError_t e;
-    switch (a.dtype) {
-    case 1: e = launch_prof_dt<1>(a, s); break;
-    case 2: e = launch_prof_dt<2>(a, s); break;
-    case 3: e = launch_prof_dt<3>(a, s); break;
-    case 4: e = launch_prof_dt<4>(a, s); break;
-    default: e = launch_prof_dt<5>(a, s); break;
-    }
+    ProfArgs b = a;
+    b.run0 = 0;
+    b.run1 = a.nruns;
+    cudaError_t e = launch_profile_runs(b, s);
     if (e != cudaSuccess) return e;
+    return launch_profile_tree(b, s);
+}
+
+cudaError_t launch_profile_tree(const ProfArgs &a, cudaStream_t s)
+{
+    cudaError_t e;
     // upper levels of the fan-in-16 tree
     const int Qn = 2 + 4 * a.ncand;
     uint64_t cnt = a.nruns;

@@ -290,3 +290,34 @@ def test_encode_recommended_matches_host_code():
     s = A.read_summary(summ)
     want = O.encode(x, 256, 1, 1, 1, s.recommended_code)
     assert r.status == 0 and out[:r.bytes].cpu().numpy().tobytes() == want
+
+
+@pytest.mark.parametrize("dt", [2, 4, 5])
+def test_profile_from_host_matches_device(dt):
+    # the host-input sweep (copy in pieces on a side stream, sweep beside it)
+    # gives the device sweep's points and summary byte for byte, and leaves
+    # the array on the device
+    rng = np.random.default_rng(60 + dt)
+    N = 256
+    x = _data(dt, 256 * 16 * 37 + 75, rng, 1)  # 37 runs and a ragged tail
+    xt = torch.from_numpy(x).cuda()
+    nc = 16
+    ws, pts, summ = A.profile_buffers(xt, N, nc)
+    A.profile_into(xt, N, list(A.DEFAULT_CANDIDATES), 0.9999, ws, pts, summ)
+    torch.cuda.synchronize()
+    want_p, want_s = pts.cpu().clone(), summ.cpu().clone()
+    xh = torch.from_numpy(x).pin_memory()
+    for chunks in (1, 3, 8, 64):
+        xd = torch.empty_like(xt).fill_(0)
+        ws2, pts2, summ2 = A.profile_buffers(xt, N, nc)
+        A.profile_from_host_into(xh, xd, N, list(A.DEFAULT_CANDIDATES), 0.9999, ws2, pts2, summ2,
+                                 chunks=chunks)
+        torch.cuda.synchronize()
+        assert torch.equal(pts2.cpu(), want_p) and torch.equal(summ2.cpu(), want_s), chunks
+        assert torch.equal(xd.view(torch.uint8), xt.view(torch.uint8)), chunks
+    # empty array
+    e = torch.empty(0, dtype=xt.dtype)
+    ws3, pts3, summ3 = A.profile_buffers(e.cuda(), N, nc)
+    A.profile_from_host_into(e.pin_memory(), e.cuda(), N, None, 0.9999, ws3, pts3, summ3)
+    torch.cuda.synchronize()
+    assert A.read_summary(summ3).status == 0 and A.read_summary(summ3).n == 0
