@@ -133,7 +133,7 @@ int encode_impl(const void *x, int dtype, uint64_t n, const apax_params *p,
         pl = plan_geometry(a.N, a.nb, 0, 0, 1, 128);
         pl.smem = (size_t)128 * (a.N / 4);
     } else {
-        default_geometry((size_t)(pw + ew) * 4, ts, threads);
+        default_geometry((size_t)(pw + ew) * 4, a.nb, ts, threads);
         pl = plan_geometry(a.N, a.nb, pw, ew, ts, threads);
     }
     a.pkt_words = pl.pkt_words;

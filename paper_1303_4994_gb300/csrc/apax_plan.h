@@ -106,12 +106,21 @@ inline Plan plan_geometry(uint32_t N, uint64_t nb, uint32_t pkt_words, uint32_t 
     return pl;
 }
 
-// Teams of 8 (16 per 128-thread CTA) when their packets fit, else teams of
-// 32 (one per warp, as many warps as fit).
-inline void default_geometry(size_t per_team_bytes, int &ts, int &threads)
+// Arrays of at most this many blocks are encoded by teams of 32 (a block per
+// warp): they do not fill the GPU, so the search's sequential chain per lane
+// (8 samples instead of 32) sets the time.  Measured on the int16 sensor
+// trace at 4:1: 1024 blocks 52 -> 32 us, 4096 blocks 54 -> 47 us, while
+// 8192 blocks already favour teams of 8 (66 vs 74 us).
+constexpr uint64_t kTeam32MaxBlocks = 4096;
+
+// Team size and CTA size of a single-array encode (the workspace size and
+// the launch both come from here): teams of 8, 16 per 128-thread CTA, when
+// their packets fit and the array is large; teams of 32 for small arrays (4
+// per CTA) and for packets too large for 16 teams (as many warps as fit).
+inline void default_geometry(size_t per_team_bytes, uint64_t nb, int &ts, int &threads)
 {
     if (16 * per_team_bytes <= kEncSmemCap) {
-        ts = 8;
+        ts = nb <= kTeam32MaxBlocks ? 32 : 8;
         threads = 128;
     } else {
         ts = 32;
@@ -150,7 +159,7 @@ inline Plan plan_encode(const Fmt &f, uint32_t N, uint64_t nb, uint64_t fr_budge
     uint32_t pw, ew;
     team_words(f, N, fr_budget_bytes, pw, ew);
     int ts, threads;
-    default_geometry((size_t)(pw + ew) * 4, ts, threads);
+    default_geometry((size_t)(pw + ew) * 4, nb, ts, threads);
     return plan_geometry(N, nb, pw, ew, ts, threads);
 }
 
