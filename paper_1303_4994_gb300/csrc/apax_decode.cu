@@ -711,13 +711,16 @@ __device__ __forceinline__ void decode_block_t1(const DecArgs &a, const DecHdr &
     }
 }
 
-// Size class of a container: teams of 32 for blocks above 4096 samples
-// (header errors are reported by the small class).
+// Size class of a container: teams of 32 for blocks above 4096 samples and
+// for ranges of at most kTeam32MaxBlocks blocks, else teams of 8 (or a block
+// per thread); header errors are reported by the small class.
 template <int EB>
-__device__ __forceinline__ bool my_class(const DecHdr &h)
+__device__ __forceinline__ bool my_class(const DecArgs &a, const DecHdr &h)
 {
     constexpr bool LARGE = EB > 1024;
-    return h.err == 0 ? ((h.N / 4 > 1024) == LARGE) : !LARGE;
+    if (h.err) return !LARGE;
+    const uint64_t blocks = a.ranged ? a.b1 - a.b0 : h.nb;
+    return (h.N / 4 > 1024 || blocks <= kTeam32MaxBlocks) == LARGE;
 }
 
 // One array: CTAs stride over tiles of the requested block range.  Both
@@ -731,7 +734,7 @@ __global__ void __launch_bounds__(128) k_decode(DecArgs a)
     __syncthreads();
     const DecHdr hd = s_h;
     constexpr bool LARGE = EB > 1024;
-    if (my_class<EB>(hd)) {
+    if (my_class<EB>(a, hd)) {
         if (hd.err) {
             if (threadIdx.x == 0) set_status(a.status, hd.err);
         } else if (!LARGE && hd.N <= kT1MaxBlock &&
@@ -767,7 +770,7 @@ __global__ void __launch_bounds__(128) k_decode(DecArgs a)
         __threadfence();
         unsigned *done = LARGE ? a.done + 1 : a.done;
         const unsigned prev = atomicAdd(done, 1u);
-        if (prev == gridDim.x - 1 && my_class<EB>(hd)) {
+        if (prev == gridDim.x - 1 && my_class<EB>(a, hd)) {
             __threadfence();
             volatile int *st = a.status;
             if (a.res) {

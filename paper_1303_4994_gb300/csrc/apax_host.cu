@@ -200,7 +200,10 @@ int decode_impl(const void *in, uint64_t in_bytes, uint64_t b0, uint64_t b1, boo
     if (ctas > cap) ctas = cap;
     if (ctas == 0) ctas = 1;
     a.nctas = (unsigned)ctas;
-    const uint64_t lblocks = ranged ? (b1 - b0) : (n + 4095) / 4096;
+    // the teams-of-32 launch: blocks above 4096 samples, or at most
+    // kTeam32MaxBlocks blocks of any size (n / 64 bounds the block count)
+    const uint64_t few = (n + 63) / 64 < kTeam32MaxBlocks ? (n + 63) / 64 : kTeam32MaxBlocks;
+    const uint64_t lblocks = ranged ? (b1 - b0) : ((n + 4095) / 4096 > few ? (n + 4095) / 4096 : few);
     uint64_t lctas = (lblocks + 3) / 4;
     if (lctas > (uint64_t)sms * 4) lctas = (uint64_t)sms * 4;
     if (lctas == 0) lctas = 1;

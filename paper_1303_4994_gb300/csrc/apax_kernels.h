@@ -16,6 +16,13 @@ namespace apax {
 constexpr uint32_t kT1MaxBlock = 1024;
 constexpr uint64_t kT1MinBlocks = 32768;
 
+// Arrays (or decoded block ranges) of at most this many blocks run with
+// teams of 32, a block per warp: they do not fill the GPU, so the per-lane
+// sequential chain (8 samples of a 256-sample block instead of 32) sets the
+// time.  Measured on the int16 sensor trace (1024 blocks at 4:1): encode
+// 52 -> 33 us; at 8192 blocks teams of 8 are faster again (66 vs 74 us).
+constexpr uint64_t kTeam32MaxBlocks = 4096;
+
 struct EncArgs {
     const void *x;
     uint64_t n;

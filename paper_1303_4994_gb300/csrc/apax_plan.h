@@ -106,13 +106,6 @@ inline Plan plan_geometry(uint32_t N, uint64_t nb, uint32_t pkt_words, uint32_t 
     return pl;
 }
 
-// Arrays of at most this many blocks are encoded by teams of 32 (a block per
-// warp): they do not fill the GPU, so the search's sequential chain per lane
-// (8 samples instead of 32) sets the time.  Measured on the int16 sensor
-// trace at 4:1: 1024 blocks 52 -> 32 us, 4096 blocks 54 -> 47 us, while
-// 8192 blocks already favour teams of 8 (66 vs 74 us).
-constexpr uint64_t kTeam32MaxBlocks = 4096;
-
 // Team size and CTA size of a single-array encode (the workspace size and
 // the launch both come from here): teams of 8, 16 per 128-thread CTA, when
 // their packets fit and the array is large; teams of 32 for small arrays (4
