@@ -99,6 +99,30 @@ def test_profile_argument_checks(lib):
     assert lib.apax_profile_workspace_size(4, 1000, 256, 33, ctypes.byref(out)) == -1
 
 
+def test_profile_from_host_argument_checks(lib):
+    # every check returns before any CUDA call (the pointers are never
+    # dereferenced on these paths)
+    ws_need = ctypes.c_uint64()
+    assert lib.apax_profile_workspace_size(4, 100000, 256, 16, ctypes.byref(ws_need)) == 0
+    xh, xd, ws, pts, summ = 0x100000, 0x200000, 0x300000, 0x400000, 0x500000
+    s1, s2 = 0x1000, 0x2000
+
+    def call(**kw):
+        a = dict(x_host=xh, x_dev=xd, dtype=4, n=100000, N=256, chunks=8, ws=ws,
+                 wsb=ws_need.value, s=s1, cs=s2)
+        a.update(kw)
+        return lib.apax_profile_from_host(a["x_host"], a["x_dev"], a["dtype"], a["n"], a["N"], None,
+                                          16, 0.9999, a["chunks"], a["ws"], a["wsb"], pts, summ,
+                                          a["s"], a["cs"])
+    assert call(N=66) == -2                # block size not a multiple of 4
+    assert call(dtype=9) == -3             # unknown type
+    assert call(x_host=0) == -1            # no input
+    assert call(chunks=0) == -1 and call(chunks=65) == -1
+    assert call(cs=s1) == -1               # copy stream must differ from the stream
+    assert call(ws=0) == -1 and call(ws=ws + 8) == -1  # missing or misaligned workspace
+    assert call(wsb=ws_need.value - 8) == -5
+
+
 def _job(dt=4, n=1000, p=None, x=0x10000, out=0x20000, cap=1 << 20, res=0x30000):
     p = p or A.params(256, A.FIXED_QUALITY, (1, 1), 0)
     return A.EncodeJob(x, dt, 0, n, p, None, out, cap, res)
