@@ -13,7 +13,7 @@ namespace apax {
 namespace host {
 
 struct Fmt {
-    int size, W, F, H;
+    int size = 0, W = 0, F = 0, H = 0;  // zero until fmt_of fills them
 };
 
 inline int fmt_of(int dtype, Fmt &f)

@@ -261,7 +261,7 @@ __device__ __forceinline__ void profile_run(const ProfArgs &a, uint64_t run, uin
     using T = DT_<DT>;
     using raw = typename T::raw;
     using lt = typename LaneT<DT>::t;
-    constexpr int W = T::W, H = T::H;
+    constexpr int H = T::H;
     const int team = threadIdx.x / TS, t = tlane<TS>();
     const int nteams = blockDim.x / TS;  // = kRun
     const int nc = a.ncand;
@@ -467,7 +467,7 @@ __device__ __forceinline__ void profile_run(const ProfArgs &a, uint64_t run, uin
         i128 wq = 0, wA = 0, wB = 0, wD = 0;     // 128-bit partials (f64, i32)
         with_quant<DT>(Q, [&](const auto &qf) {
             Stream1 sm(s, carry_in<DT>(b, qf, 4 * b.g0));
-            const int cD = -103 - b.Eb - k;  // f32: D' shift = bexp + cD
+            [[maybe_unused]] const int cD = -103 - b.Eb - k;  // f32: D' shift = bexp + cD
             constexpr int QM = std::remove_reference_t<decltype(qf)>::kMode;
             if constexpr (DT == 4 && QM == 1) {
                 // FMA form (k >= 1): T = x b + 1.5 2^23 rounded gives q; then
@@ -498,8 +498,7 @@ __device__ __forceinline__ void profile_run(const ProfArgs &a, uint64_t run, uin
                     }
                     tc.push(exp_from_or(o), true);
                 }
-                return;
-            }
+            } else {
 #pragma unroll 1
             for (int g = b.g0; g < ge; ++g) {
                 lt xv[4];
@@ -550,6 +549,7 @@ __device__ __forceinline__ void profile_run(const ProfArgs &a, uint64_t run, uin
                         }
                     }
                 }
+            }
             }
         });
         int nib, sume;
