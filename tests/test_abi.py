@@ -99,6 +99,22 @@ def test_profile_argument_checks(lib):
     assert lib.apax_profile_workspace_size(4, 1000, 256, 33, ctypes.byref(out)) == -1
 
 
+def test_workspace_follows_team_geometry(lib):
+    # fixed quality keeps one look-back word per tile: tiles of 4 blocks
+    # (teams of 32) up to 4096 blocks, of 16 blocks (teams of 8) above;
+    # fixed rate needs only the 64-byte head
+    out = ctypes.c_uint64()
+    for nb in (1, 5, 1024, 4095, 4096, 4097, 65536):
+        n = nb * 256 - 3
+        p = A.params(256, A.FIXED_QUALITY, (1, 1), 0)
+        assert lib.apax_workspace_size(4, n, ctypes.byref(p), ctypes.byref(out)) == 0
+        per = 4 if nb <= 4096 else 16
+        assert out.value == 64 + 8 * ((nb + per - 1) // per), nb
+        p = A.params(256, A.FIXED_RATE, (4, 1), 0)
+        assert lib.apax_workspace_size(4, n, ctypes.byref(p), ctypes.byref(out)) == 0
+        assert out.value == 64, nb
+
+
 def test_profile_from_host_argument_checks(lib):
     # every check returns before any CUDA call (the pointers are never
     # dereferenced on these paths)
