@@ -192,7 +192,7 @@ int apax_profile(const void *x, int dtype, uint64_t n, uint32_t block_size,
  * queued on `stream` after it sees x_dev, points and summary.  Results are
  * identical to apax_profile on x_dev.  copy_stream must differ from stream.
  * Asynchronous: no host synchronisation; the events it uses are released by
- * the driver once complete. */
+ * CUDA once complete. */
 int apax_profile_from_host(const void *x_host, void *x_dev, int dtype, uint64_t n,
                            uint32_t block_size, const uint16_t *candidates /* host */, int ncand,
                            double target, int chunks, void *workspace, uint64_t workspace_bytes,
@@ -209,7 +209,7 @@ void apax_derived_metrics(const apax_profile_point *pt, uint64_t n, double *out 
 /* Encode without any allocation (no counterpart in the paper: this entry
  * exists for callers that cannot allocate device memory at all -- code
  * running inside another runtime's allocator or memory-pool hook, paths that
- * must never block on the driver's allocator, or plug-ins whose host owns
+ * must never block on the CUDA driver's allocator, or plug-ins whose host owns
  * every device buffer).  Same arguments and results as apax_encode, minus
  * the workspace: the scratch lives in one fixed device array of
  * APAX_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until

@@ -470,7 +470,7 @@ int apax_profile_from_host(const void *x_host, void *x_dev, int dtype, uint64_t 
             return fail(e);
     }
     e = launch_profile_tree(a, s);
-    // events recorded and waited on are released by the driver once complete
+    // events recorded and waited on are released by CUDA once complete
     for (int i = 0; i < nev; ++i) cudaEventDestroy(ev[i]);
     return cuda_fail(e);
 }

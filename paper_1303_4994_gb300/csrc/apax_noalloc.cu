@@ -3,7 +3,7 @@
 // Some callers cannot call cudaMalloc or any allocating routine: code that
 // runs inside another runtime's memory pool or allocator hook (where a
 // nested allocation would re-enter that allocator or break its accounting),
-// signal-safe or real-time paths that must not block on the driver's
+// signal-safe or real-time paths that must not block on the CUDA driver's
 // allocator, and plug-ins whose host application owns all device memory and
 // forbids allocations behind its back.  apax_encode already takes its
 // workspace from the caller; this variant needs no workspace at all: its
