@@ -885,7 +885,7 @@ static cudaError_t launch_one(const DecArgs &a, unsigned ctas, cudaStream_t s)
     size_t smem = (size_t)(threads / TS) * EB;
     if (EB <= 1024 && smem < (size_t)threads * (kT1MaxBlock / 4)) smem = (size_t)threads * (kT1MaxBlock / 4);
     auto k = k_decode<DT, TS, EB>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t e = smem_limit<k_decode<DT, TS, EB>>(smem);
     if (e != cudaSuccess) return e;
     k<<<ctas, threads, smem, s>>>(a);
     return cudaGetLastError();

@@ -691,7 +691,8 @@ template <int DT, int TS>
 static cudaError_t launch_ts(const EncArgs &a, int threads, size_t smem, cudaStream_t s)
 {
     auto k = a.mode == 1 ? k_encode<DT, TS, 1> : k_encode<DT, TS, 0>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t e =
+        a.mode == 1 ? smem_limit<k_encode<DT, TS, 1>>(smem) : smem_limit<k_encode<DT, TS, 0>>(smem);
     if (e != cudaSuccess) return e;
     k<<<(unsigned)a.ntiles, threads, smem, s>>>(a);
     return cudaGetLastError();
@@ -701,7 +702,7 @@ template <int DT>
 static cudaError_t launch_t1(const EncArgs &a, int threads, size_t smem, cudaStream_t s)
 {
     auto k = k_encode_t1<DT>;  // fixed rate only
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t e = smem_limit<k_encode_t1<DT>>(smem);
     if (e != cudaSuccess) return e;
     k<<<(unsigned)a.ntiles, threads, smem, s>>>(a);
     return cudaGetLastError();

@@ -188,9 +188,7 @@ int decode_impl(const void *in, uint64_t in_bytes, uint64_t b0, uint64_t b1, boo
     a.ticket = (unsigned long long *)(w + 24);
     a.status = (int *)(w + 8);
     a.res = res;
-    int dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int sms = sm_count();
     // Grid-stride over blocks.  The small-block launch (16 teams of 8 per
     // CTA) sizes its grid for the smallest legal block size; the large-block
     // launch (4 teams of 32) for blocks of more than 4096 samples.

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <stdint.h>
+#include <atomic>
 #include <cuda_runtime.h>
 
 #include "../../include/apax.h"
@@ -22,6 +23,47 @@ constexpr uint64_t kT1MinBlocks = 32768;
 // time.  Measured on the int16 sensor trace (1024 blocks at 4:1): encode
 // 52 -> 33 us; at 8192 blocks teams of 8 are faster again (66 vs 74 us).
 constexpr uint64_t kTeam32MaxBlocks = 4096;
+
+// Raises kernel K's dynamic shared-memory limit on the current device to at
+// least `bytes`, calling the runtime only when the limit has to grow: the
+// attribute call costs host time between a call's first and last launch,
+// which single small calls feel.
+template <auto K>
+inline cudaError_t smem_limit(size_t bytes)
+{
+    constexpr int kDevs = 64;
+    static std::atomic<int> have[kDevs];  // static storage: starts at zero
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const bool known = dev >= 0 && dev < kDevs;
+    if (known && have[dev].load(std::memory_order_acquire) >= (int)bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess && known) {
+        int cur = have[dev].load(std::memory_order_relaxed);
+        while (cur < (int)bytes && !have[dev].compare_exchange_weak(cur, (int)bytes)) {
+        }
+    }
+    return e;
+}
+
+// Multiprocessor count of the current device, read once per device.
+inline int sm_count()
+{
+    constexpr int kDevs = 64;
+    static std::atomic<int> count[kDevs];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 152;
+    if (dev >= 0 && dev < kDevs) {
+        const int c = count[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+        return 152;
+    if (dev >= 0 && dev < kDevs) count[dev].store(sms, std::memory_order_relaxed);
+    return sms;
+}
 
 struct EncArgs {
     const void *x;

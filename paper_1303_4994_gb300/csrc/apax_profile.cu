@@ -862,7 +862,7 @@ cudaError_t launch_prof_dt(const ProfArgs &a, cudaStream_t s)
     b.stage_off = sb ? (uint32_t)((smem + 15) / 16 * 16) : 0;
     if (sb) smem = b.stage_off + sb;
     auto k = k_profile<DT>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t e = smem_limit<k_profile<DT>>(smem);
     if (e != cudaSuccess) return e;
     if (a.run1 > a.run0) k<<<(unsigned)(a.run1 - a.run0), threads, smem, s>>>(b);
     return cudaGetLastError();
