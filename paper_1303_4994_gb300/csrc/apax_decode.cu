@@ -718,7 +718,7 @@ template <int EB>
 __device__ __forceinline__ bool my_class(const DecArgs &a, const DecHdr &h)
 {
     constexpr bool LARGE = EB > 1024;
-    if (h.err) return !LARGE;
+    if (h.err) return a.small_launched ? !LARGE : LARGE;  // reported once
     const uint64_t blocks = a.ranged ? a.b1 - a.b0 : h.nb;
     return (h.N / 4 > 1024 || blocks <= kTeam32MaxBlocks) == LARGE;
 }
@@ -894,8 +894,10 @@ static cudaError_t launch_one(const DecArgs &a, unsigned ctas, cudaStream_t s)
 template <int DT>
 static cudaError_t launch_dt(const DecArgs &a, cudaStream_t s)
 {
-    cudaError_t e = launch_one<DT, 8, 1024>(a, a.nctas, s);
-    if (e != cudaSuccess) return e;
+    if (a.small_launched) {
+        const cudaError_t e = launch_one<DT, 8, 1024>(a, a.nctas, s);
+        if (e != cudaSuccess) return e;
+    }
     return launch_one<DT, 32, 4096>(a, a.nctas_large, s);
 }
 

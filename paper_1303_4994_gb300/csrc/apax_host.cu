@@ -206,6 +206,9 @@ int decode_impl(const void *in, uint64_t in_bytes, uint64_t b0, uint64_t b1, boo
     if (lctas > (uint64_t)sms * 4) lctas = (uint64_t)sms * 4;
     if (lctas == 0) lctas = 1;
     a.nctas_large = (unsigned)lctas;
+    // at most kTeam32MaxBlocks blocks whatever the block size: every
+    // container is the teams-of-32 launch's, so the other one is not enqueued
+    a.small_launched = blocks > kTeam32MaxBlocks;
     cudaStream_t s = (cudaStream_t)stream;
     st = cuda_fail(cudaMemsetAsync(ws, 0, apax_decode_workspace_size(), s));
     if (st) return st;

@@ -117,6 +117,8 @@ struct DecArgs {
     unsigned long long *ticket;  // tile counter of the block-per-thread mode
     int *status;
     unsigned nctas, nctas_large;
+    bool small_launched;  // the teams-of-8 / block-per-thread launch runs (else
+                          // every container belongs to the teams-of-32 one)
     apax_result *res;
 };
 
