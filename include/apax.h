@@ -187,7 +187,8 @@ int apax_profile(const void *x, int dtype, uint64_t n, uint32_t block_size,
  * the array goes to the device in `chunks` pieces (1..64, whole runs of 16
  * blocks each) with cudaMemcpyAsync on copy_stream, and each piece is swept
  * as soon as it is there, on one of four library-owned streams (created on
- * first use per device), so the copy hides behind the sweep.  The copies and
+ * first use per device and kept for the process's CUDA context, so not
+ * valid across cudaDeviceReset), so the copy hides behind the sweep.  The copies and
  * sweeps first wait for the work queued on `stream` before the call; work
  * queued on `stream` after it sees x_dev, points and summary.  Results are
  * identical to apax_profile on x_dev.  copy_stream must differ from stream.

@@ -27,7 +27,8 @@ constexpr uint64_t kTeam32MaxBlocks = 4096;
 // Raises kernel K's dynamic shared-memory limit on the current device to at
 // least `bytes`, calling the runtime only when the limit has to grow: the
 // attribute call costs host time between a call's first and last launch,
-// which single small calls feel.
+// which single small calls feel.  The cache assumes one CUDA context per
+// device for the life of the process (no cudaDeviceReset in between).
 template <auto K>
 inline cudaError_t smem_limit(size_t bytes)
 {
