@@ -5,10 +5,15 @@ profiler sweep (16 power-of-two attenuation codes, exact sizes and
 reconstruction sums, recommendation at r >= 0.9999) -> fixed-quality encode
 at the recommended code (read on the device) -> decode.  Workload: the
 float32 4096x4096 k^-3 random field.  `value` is GB/s of uncompressed data
-through the step; encode, decode and profile are also timed on their own.
+through the step, which is captured once as a CUDA graph and replayed (L2
+flushed before each timed replay); encode, decode and profile are also timed
+on their own.  `e2e` runs the step from pinned host memory through the
+public calls: the host-input sweep (the array crosses in pieces on a copy
+stream while pieces already there are swept), encode, decode, and the copy
+of the container and profile points back.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload field|batched|serving]
+                  [--workload field|sensor|field3d|batched|serving]
 
 With N > 1 (torchrun), every rank codes its own array (weak scaling, no
 data-path collective); rank 0 prints max-over-ranks timing.
