@@ -46,3 +46,24 @@ def test_two_gloo_ranks_take_max_and_aggregate():
             got, gbs = out[r]
             assert got == [2.0, 10.0, 6.0]
             assert gbs == pytest.approx(2 * 1e9 / 2.0 / 1e6)
+
+
+def test_reference_arm_line(monkeypatch):
+    # the reference arm (the oracle on host cores) prints one line with the
+    # contract's keys on rank 0 and nothing elsewhere; the oracle timing is
+    # replaced by fixed samples so the test stays fast
+    import types
+
+    samples = iter([{"value": v, "sample": "stub"} for v in (1.0, 2.0, 4.0, 6.0)])
+    monkeypatch.setattr(bench, "cpu_baseline", lambda rows=256: next(samples))
+    args = types.SimpleNamespace(steps=2, warmup=2)
+    assert bench.run_reference(args, 1, 2) is None
+    line = bench.run_reference(args, 0, 2)
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC
+    assert line["value"] == 5.0 and line["n_gpus"] == 2 and line["steps"] == 2
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == 5.0
+    assert line["e2e"] == {"value": 5.0, "unit": "GB/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    for k in ("unit", "warmup", "higher_is_better", "scaling", "vs_baseline", "dtype", "data",
+              "config"):
+        assert k in line
