@@ -121,8 +121,8 @@ int apax_encode_recommended(const void *x, int dtype, uint64_t n, const apax_par
                             uint64_t out_capacity, void *workspace, uint64_t workspace_bytes,
                             apax_result *res, void *stream);
 
-/* Device workspace bytes of apax_decode / apax_decode_blocks (a status word
- * and a completion counter). */
+/* Device workspace bytes of apax_decode / apax_decode_blocks (a status word,
+ * one completion counter per launch and the block-per-thread tile counter). */
 uint64_t apax_decode_workspace_size(void);
 
 /* Decode a container of in_bytes bytes into y (n elements of dtype).  The
