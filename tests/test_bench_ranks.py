@@ -67,3 +67,15 @@ def test_reference_arm_line(monkeypatch):
     for k in ("unit", "warmup", "higher_is_better", "scaling", "vs_baseline", "dtype", "data",
               "config"):
         assert k in line
+
+
+def test_committed_traffic_figures_are_read():
+    # the roofline's `traffic` comes from the committed ncu summary: each
+    # kernel of the step has a per-launch DRAM figure, and the sweep's is
+    # close to one read of the 64 MiB input (no re-reads)
+    xb = 4096 * 4096 * 4
+    for k in ("profile", "encode", "decode"):
+        t = bench._traffic(k)
+        assert isinstance(t, int) and t > 0, k
+    assert xb <= bench._traffic("profile") < 1.1 * xb
+    assert bench._traffic("no_such_kernel") is None
