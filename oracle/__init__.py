@@ -37,7 +37,7 @@ def build(force: bool = False) -> str:
         tmp = _LIB + f".{os.getpid()}.tmp"
         subprocess.check_call([
             "gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off",
-            "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+            "-fno-fast-math", "-o", tmp, _SRC, "-lm", "-lpthread"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -89,6 +89,13 @@ def lib():
         _lib.oracle_fr_budget.argtypes = [i32, u32, i32, u32, u32, p64]
         _lib.oracle_min_packet.argtypes = [i32, u32, i32, p64]
         _lib.oracle_derived.argtypes = [vp, u64, vp]
+        _lib.oracle_threads.argtypes = [i32]
+        _lib.oracle_encode_mt.argtypes = [vp, i32, u64, u32, i32, u32, u32, i32, vp, u64, p64,
+                                          i32]
+        _lib.oracle_decode_mt.argtypes = [vp, u64, vp, i32, u64, i32]
+        _lib.oracle_metrics_mt.argtypes = [vp, vp, i32, u64, u32, vp, i32]
+        _lib.oracle_profile_mt.argtypes = [vp, i32, u64, u32, vp, i32, ctypes.c_double, vp,
+                                           ctypes.POINTER(ctypes.c_int), i32]
     return _lib
 
 
@@ -116,24 +123,40 @@ def encoded_size(dtype, n: int, N: int = 256, mode: int = MODE_FQ, num: int = 1,
     return out.value
 
 
+def threads(t: int = 0) -> int:
+    """Threads the threaded drivers use for `t` (0: one per online core)."""
+    return lib().oracle_threads(t)
+
+
 def encode(x: np.ndarray, N: int = 256, mode: int = MODE_FQ, num: int = 1, den: int = 1,
-           code: int = 0) -> bytes:
-    """Encode a C-contiguous array; returns the container bytes."""
+           code: int = 0, threads: int | None = None) -> bytes:
+    """Encode a C-contiguous array; returns the container bytes.  threads:
+    None runs the plain sequential encoder; an int runs the same per-block
+    code on that many threads over block ranges (0 = all cores)."""
     x = np.ascontiguousarray(x).reshape(-1)
     cap = encoded_size(x.dtype, x.size, N, mode, num, den, code)
     buf = np.zeros(cap, dtype=np.uint8)
     out = ctypes.c_uint64()
-    st = lib().oracle_encode(_ptr(x), _code(x), x.size, N, mode, num, den, code, _ptr(buf), cap,
-                             ctypes.byref(out))
+    if threads is None:
+        st = lib().oracle_encode(_ptr(x), _code(x), x.size, N, mode, num, den, code, _ptr(buf),
+                                 cap, ctypes.byref(out))
+    else:
+        st = lib().oracle_encode_mt(_ptr(x), _code(x), x.size, N, mode, num, den, code,
+                                    _ptr(buf), cap, ctypes.byref(out), threads)
     if st:
         raise OracleError(st, "encode")
     return buf[:out.value].tobytes()
 
 
-def decode(stream: bytes, dtype, n: int) -> np.ndarray:
-    s = np.frombuffer(stream, dtype=np.uint8).copy()
+def decode(stream: bytes, dtype, n: int, threads: int | None = None) -> np.ndarray:
+    """Decode a container (threads as for encode)."""
+    s = np.frombuffer(stream, dtype=np.uint8)
     y = np.zeros(max(n, 1), dtype=dtype)
-    st = lib().oracle_decode(_ptr(s), s.size, _ptr(y), DTYPE_CODE[np.dtype(dtype)], n)
+    if threads is None:
+        st = lib().oracle_decode(_ptr(s), s.size, _ptr(y), DTYPE_CODE[np.dtype(dtype)], n)
+    else:
+        st = lib().oracle_decode_mt(_ptr(s), s.size, _ptr(y), DTYPE_CODE[np.dtype(dtype)], n,
+                                    threads)
     if st:
         raise OracleError(st, "decode")
     return y[:n]
@@ -145,12 +168,15 @@ def decode_status(stream: bytes, dtype, n: int) -> int:
     return lib().oracle_decode(_ptr(s), s.size, _ptr(y), DTYPE_CODE[np.dtype(dtype)], n)
 
 
-def metrics(x: np.ndarray, y: np.ndarray, N: int = 256) -> np.ndarray:
+def metrics(x: np.ndarray, y: np.ndarray, N: int = 256, threads: int | None = None) -> np.ndarray:
     """[sum x, sum y, sum x^2, sum xy, sum y^2, sum d^2] (binary64)."""
     x = np.ascontiguousarray(x).reshape(-1)
     y = np.ascontiguousarray(y).reshape(-1)
     out = np.zeros(6, dtype=np.float64)
-    st = lib().oracle_metrics(_ptr(x), _ptr(y), _code(x), x.size, N, _ptr(out))
+    if threads is None:
+        st = lib().oracle_metrics(_ptr(x), _ptr(y), _code(x), x.size, N, _ptr(out))
+    else:
+        st = lib().oracle_metrics_mt(_ptr(x), _ptr(y), _code(x), x.size, N, _ptr(out), threads)
     if st:
         raise OracleError(st, "metrics")
     return out
@@ -184,14 +210,20 @@ def corr(sxx: float, sxy: float, syy: float) -> float:
 DEFAULT_CANDIDATES = tuple(256 * i for i in range(16))
 
 
-def profile(x: np.ndarray, N: int = 256, candidates=DEFAULT_CANDIDATES, target: float = 0.99999):
-    """Returns (points, recommended_index, target_missed)."""
+def profile(x: np.ndarray, N: int = 256, candidates=DEFAULT_CANDIDATES, target: float = 0.99999,
+            threads: int | None = None):
+    """Returns (points, recommended_index, target_missed); threads as for
+    encode."""
     x = np.ascontiguousarray(x).reshape(-1)
     c = np.asarray(candidates, dtype=np.uint16)
     pts = (Point * len(c))()
     rec = ctypes.c_int()
-    st = lib().oracle_profile(_ptr(x), _code(x), x.size, N, _ptr(c), len(c), target, pts,
-                              ctypes.byref(rec))
+    if threads is None:
+        st = lib().oracle_profile(_ptr(x), _code(x), x.size, N, _ptr(c), len(c), target, pts,
+                                  ctypes.byref(rec))
+    else:
+        st = lib().oracle_profile_mt(_ptr(x), _code(x), x.size, N, _ptr(c), len(c), target, pts,
+                                     ctypes.byref(rec), threads)
     if st < 0:
         raise OracleError(st, "profile")
     return list(pts), rec.value, st == 1

@@ -583,6 +583,26 @@ int oracle_min_packet(int dtype, uint32_t N, int L, uint64_t *bytes)
 /* Exported: encoder                                                         */
 /* ------------------------------------------------------------------------ */
 
+/* The 40-byte container header (reading 11): magic "APX1", version 1,
+ * dtype, mode, flags (bit 0: offset table), N, the fixed-quality code, the
+ * fixed-rate budget B, n; the payload size at bytes 28..35 is written once
+ * the packets are placed. */
+static void write_container_header(uint8_t *out, int dtype, uint32_t N, int mode, int cfq,
+                                   uint64_t B, uint64_t n)
+{
+    memset(out, 0, 40);
+    out[0] = 'A'; out[1] = 'P'; out[2] = 'X'; out[3] = '1';
+    out[4] = 1;
+    out[5] = (uint8_t)dtype;
+    out[6] = (uint8_t)mode;
+    out[7] = (mode == MODE_FQ) ? 1 : 0;
+    put_le(out + 8, N, 4);
+    put_le(out + 12, mode == MODE_FQ ? (uint64_t)cfq : 0, 2);
+    put_le(out + 16, B, 4);
+    put_le(out + 20, n, 8);
+}
+
+
 /* Fixed-rate search (reading of the adaptive loop, policy BISECT): c = 0 if
  * it fits; else bisection on [0, 4095] keeping hi fitting (4095 always fits). */
 static int fr_search(const fmt_t *F, const void *x, uint64_t n, uint64_t j, int s,
@@ -612,17 +632,8 @@ int oracle_encode(const void *x, int dtype, uint64_t n, uint32_t N, int mode, ui
     if (st) return st;
     uint64_t nb = nblocks_of(n, N);
     if (cap < 40) return ST_CAPACITY;
-    memset(out, 0, 40);
-    out[0] = 'A'; out[1] = 'P'; out[2] = 'X'; out[3] = '1';
-    out[4] = 1;
-    out[5] = (uint8_t)dtype;
-    out[6] = (uint8_t)mode;
-    out[7] = (mode == MODE_FQ) ? 1 : 0;
-    put_le(out + 8, N, 4);
-    put_le(out + 12, mode == MODE_FQ ? (uint64_t)cfq : 0, 2);
     uint64_t B = (mode == MODE_FR) ? fr_budget(&F, (int)N, num, den) : 0;
-    put_le(out + 16, B, 4);
-    put_le(out + 20, n, 8);
+    write_container_header(out, dtype, N, mode, cfq, B, n);
 
     blk_t *b = (blk_t *)malloc(sizeof(blk_t));
     if (!b) return ST_INVALID_ARG;
@@ -730,38 +741,61 @@ static int decode_packet(const fmt_t *F, const uint8_t *p, uint64_t avail, int L
     return ST_OK;
 }
 
-int oracle_decode(const uint8_t *in, uint64_t in_bytes, void *y, int dtype, uint64_t n)
+/* Parsed container header (reading 11). */
+typedef struct {
+    fmt_t F;
+    int mode;
+    uint64_t B, payload, nb, poff;
+} cont_t;
+
+static int parse_container(const uint8_t *in, uint64_t in_bytes, int dtype, uint64_t n, cont_t *c)
 {
     if (in_bytes < 40) return ST_CORRUPT;
     if (in[0] != 'A' || in[1] != 'P' || in[2] != 'X' || in[3] != '1' || in[4] != 1)
         return ST_CORRUPT;
     if (in[5] != dtype) return ST_INVALID_ARG;
-    int mode = in[6];
+    c->mode = in[6];
     uint32_t N = (uint32_t)get_le(in + 8, 4);
     uint64_t hn = get_le(in + 20, 8);
     if (hn != n) return ST_INVALID_ARG;
-    fmt_t F;
-    int st = fmt_init(&F, dtype, N);
-    if (st) return ST_CORRUPT;
-    if (mode != MODE_FR && mode != MODE_FQ) return ST_CORRUPT;
-    uint64_t B = get_le(in + 16, 4);
-    uint64_t payload = get_le(in + 28, 8);
-    uint64_t nb = nblocks_of(n, N);
-    uint64_t poff = 40 + ((mode == MODE_FQ) ? table_bytes(nb) : 0);
-    if (poff > in_bytes || payload > in_bytes - poff) return ST_CORRUPT;
-    blk_t *b = (blk_t *)malloc(sizeof(blk_t));
-    if (!b) return ST_INVALID_ARG;
-    for (uint64_t j = 0; j < nb; ++j) {
-        uint64_t start = (mode == MODE_FQ) ? 4 * get_le(in + 40 + 4 * j, 4) : j * B;
-        if (start >= payload) { free(b); return ST_CORRUPT; }
+    if (fmt_init(&c->F, dtype, N)) return ST_CORRUPT;
+    if (c->mode != MODE_FR && c->mode != MODE_FQ) return ST_CORRUPT;
+    c->B = get_le(in + 16, 4);
+    c->payload = get_le(in + 28, 8);
+    c->nb = nblocks_of(n, N);
+    c->poff = 40 + ((c->mode == MODE_FQ) ? table_bytes(c->nb) : 0);
+    if (c->poff > in_bytes || c->payload > in_bytes - c->poff) return ST_CORRUPT;
+    return ST_OK;
+}
+
+/* Decodes blocks [b0, b1) of a parsed container into y (at their places). */
+static int decode_range(const cont_t *c, const uint8_t *in, void *y, uint64_t n, uint64_t b0,
+                        uint64_t b1, blk_t *b)
+{
+    const uint32_t N = c->F.N;
+    for (uint64_t j = b0; j < b1; ++j) {
+        uint64_t start = (c->mode == MODE_FQ) ? 4 * get_le(in + 40 + 4 * j, 4) : j * c->B;
+        if (start >= c->payload) return ST_CORRUPT;
         int L = (int)((n - j * N) < N ? (n - j * N) : N);
         uint64_t plen;
-        st = decode_packet(&F, in + poff + start, payload - start, L, y, j * N, &plen, b);
-        if (st) { free(b); return st; }
-        if (mode == MODE_FR && j + 1 < nb && plen != B) { free(b); return ST_CORRUPT; }
+        int st = decode_packet(&c->F, in + c->poff + start, c->payload - start, L, y, j * N,
+                               &plen, b);
+        if (st) return st;
+        if (c->mode == MODE_FR && j + 1 < c->nb && plen != c->B) return ST_CORRUPT;
     }
-    free(b);
     return ST_OK;
+}
+
+int oracle_decode(const uint8_t *in, uint64_t in_bytes, void *y, int dtype, uint64_t n)
+{
+    cont_t c;
+    int st = parse_container(in, in_bytes, dtype, n, &c);
+    if (st) return st;
+    blk_t *b = (blk_t *)malloc(sizeof(blk_t));
+    if (!b) return ST_INVALID_ARG;
+    st = decode_range(&c, in, y, n, 0, c.nb, b);
+    free(b);
+    return st;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1177,4 +1211,280 @@ int oracle_derived(const double *s, uint64_t n, double *out)
     t = syy / nn - my * my; out[9] = sqrt(t > 0.0 ? t : 0.0);
     t = sdd / nn - md * md; out[10] = sqrt(t > 0.0 ? t : 0.0);
     return ST_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Threaded drivers over contiguous block ranges                             */
+/* ------------------------------------------------------------------------ */
+/* The same per-block routines as above (oracle_encode_blocks for the
+ * packets, decode_range for decoding, block_sums for the metrics), run by
+ * POSIX threads on contiguous ranges of blocks; the container, the decoded
+ * array and the sums are identical to the single-threaded calls because
+ * every block is coded on its own (Sec. 6; the one-block lag only reads the
+ * predecessor block's samples) and the ranges are assembled in block order.
+ * They exist so that whole arrays of benchmark size can be checked and timed
+ * on all host cores.  threads <= 0 means one per online core. */
+#include <pthread.h>
+#include <unistd.h>
+
+static int mt_threads(int threads, uint64_t nb)
+{
+    if (threads <= 0) {
+        long c = sysconf(_SC_NPROCESSORS_ONLN);
+        threads = c > 0 ? (int)c : 1;
+    }
+    if (threads > 256) threads = 256;
+    if ((uint64_t)threads > nb) threads = nb ? (int)nb : 1;
+    return threads;
+}
+
+int oracle_threads(int threads) { return mt_threads(threads, (uint64_t)1 << 40); }
+
+typedef struct {
+    /* encode */
+    const void *x;
+    int dtype, mode, cfq;
+    uint64_t n;
+    uint32_t N, num, den;
+    uint64_t b0, b1;
+    uint8_t *buf;
+    uint64_t cap;
+    uint64_t *lens;
+    /* decode */
+    const cont_t *c;
+    const uint8_t *in;
+    void *y;
+    /* block sums */
+    const void *yy;
+    double *sums;
+    int st;
+} mt_job;
+
+static void *enc_worker(void *p)
+{
+    mt_job *J = (mt_job *)p;
+    J->st = oracle_encode_blocks(J->x, J->dtype, J->n, J->N, J->mode, J->num, J->den, J->cfq,
+                                 J->b0, J->b1, J->buf, J->cap, J->lens);
+    return NULL;
+}
+
+static void *dec_worker(void *p)
+{
+    mt_job *J = (mt_job *)p;
+    blk_t *b = (blk_t *)malloc(sizeof(blk_t));
+    J->st = b ? decode_range(J->c, J->in, J->y, J->n, J->b0, J->b1, b) : ST_INVALID_ARG;
+    free(b);
+    return NULL;
+}
+
+static void *sums_worker(void *p)
+{
+    mt_job *J = (mt_job *)p;
+    J->st = oracle_block_sums(J->x, J->yy, J->dtype, J->n, J->N, J->b0, J->b1, J->sums);
+    return NULL;
+}
+
+/* Runs fn on T jobs (the first in the calling thread); returns the status of
+ * the lowest-numbered failing range, as the sequential loop would. */
+static int mt_run(mt_job *jobs, int T, void *(*fn)(void *))
+{
+    pthread_t tid[256];
+    int started[256];
+    for (int i = 1; i < T; ++i) started[i] = pthread_create(&tid[i], NULL, fn, &jobs[i]) == 0;
+    fn(&jobs[0]);
+    for (int i = 1; i < T; ++i) {
+        if (started[i]) pthread_join(tid[i], NULL);
+        else fn(&jobs[i]);
+    }
+    for (int i = 0; i < T; ++i)
+        if (jobs[i].st) return jobs[i].st;
+    return ST_OK;
+}
+
+static void mt_split(mt_job *jobs, int T, uint64_t nb)
+{
+    for (int i = 0; i < T; ++i) {
+        jobs[i].b0 = nb * (uint64_t)i / (uint64_t)T;
+        jobs[i].b1 = nb * (uint64_t)(i + 1) / (uint64_t)T;
+        jobs[i].st = ST_OK;
+    }
+}
+
+/* oracle_encode, block ranges on `threads` threads. */
+int oracle_encode_mt(const void *x, int dtype, uint64_t n, uint32_t N, int mode, uint32_t num,
+                     uint32_t den, int cfq, uint8_t *out, uint64_t cap, uint64_t *bytes,
+                     int threads)
+{
+    fmt_t F;
+    int st = fmt_init(&F, dtype, N);
+    if (st) return st;
+    st = check_params(&F, mode, num, den, cfq);
+    if (st) return st;
+    const uint64_t nb = nblocks_of(n, N);
+    if (cap < 40) return ST_CAPACITY;
+    const uint64_t B = (mode == MODE_FR) ? fr_budget(&F, (int)N, num, den) : 0;
+    write_container_header(out, dtype, N, mode, cfq, B, n);
+    const uint64_t payload_off = 40 + ((mode == MODE_FQ) ? table_bytes(nb) : 0);
+    if (payload_off > cap) return ST_CAPACITY;
+    if (mode == MODE_FQ) memset(out + 40, 0, payload_off - 40);
+    const int T = mt_threads(threads, nb);
+    /* largest packet of one block: the budget, or every exponent absolute at
+     * the full width (the worst case the size bound also uses) */
+    const uint64_t maxp = mode == MODE_FR
+                              ? fr_budget(&F, (int)N, num, den)
+                              : pad32_bytes((uint64_t)F.hbits + 8ull * (N / 4) + (uint64_t)F.width * N);
+    mt_job jobs[256];
+    memset(jobs, 0, sizeof jobs);
+    mt_split(jobs, T, nb);
+    uint64_t *lens = (uint64_t *)malloc(sizeof(uint64_t) * (nb ? nb : 1));
+    int fail = lens == NULL;
+    for (int i = 0; i < T && !fail; ++i) {
+        mt_job *J = &jobs[i];
+        J->x = x; J->dtype = dtype; J->n = n; J->N = N; J->mode = mode;
+        J->num = num; J->den = den; J->cfq = cfq;
+        J->cap = maxp * (J->b1 - J->b0);
+        /* the last block's fixed-rate budget may exceed B (minimum packet) */
+        if (mode == MODE_FR && J->b1 == nb && nb) {
+            int L = (int)(n - (nb - 1) * N);
+            uint64_t bl = fr_budget(&F, L, num, den);
+            if (bl > maxp) J->cap += bl - maxp;
+        }
+        J->buf = (uint8_t *)malloc(J->cap ? J->cap : 1);
+        J->lens = lens + J->b0;
+        if (!J->buf) fail = 1;
+    }
+    if (fail) {
+        for (int i = 0; i < T; ++i) free(jobs[i].buf);
+        free(lens);
+        return ST_INVALID_ARG;
+    }
+    st = mt_run(jobs, T, enc_worker);
+    uint64_t pos = 0;
+    for (int i = 0; i < T && !st; ++i) {
+        const mt_job *J = &jobs[i];
+        uint64_t q = 0;
+        for (uint64_t j = J->b0; j < J->b1; ++j) {
+            if (mode == MODE_FQ) {
+                if ((pos + q) / 4 > 0xffffffffull) { st = ST_TOO_LARGE; break; }
+                put_le(out + 40 + 4 * j, (pos + q) / 4, 4);
+            }
+            q += lens[j];
+        }
+        if (st) break;
+        if (payload_off + pos + q > cap) { st = ST_CAPACITY; break; }
+        memcpy(out + payload_off + pos, J->buf, q);
+        pos += q;
+    }
+    for (int i = 0; i < T; ++i) free(jobs[i].buf);
+    free(lens);
+    if (st) return st;
+    put_le(out + 28, pos, 8);
+    *bytes = payload_off + pos;
+    return ST_OK;
+}
+
+/* oracle_decode, block ranges on `threads` threads. */
+int oracle_decode_mt(const uint8_t *in, uint64_t in_bytes, void *y, int dtype, uint64_t n,
+                     int threads)
+{
+    cont_t c;
+    int st = parse_container(in, in_bytes, dtype, n, &c);
+    if (st) return st;
+    const int T = mt_threads(threads, c.nb);
+    mt_job jobs[256];
+    memset(jobs, 0, sizeof jobs);
+    mt_split(jobs, T, c.nb);
+    for (int i = 0; i < T; ++i) {
+        jobs[i].c = &c;
+        jobs[i].in = in;
+        jobs[i].y = y;
+        jobs[i].n = n;
+    }
+    return mt_run(jobs, T, dec_worker);
+}
+
+/* oracle_metrics, the block sums on `threads` threads (the fan-in-16 tree
+ * over the block values is the same sequential loop). */
+int oracle_metrics_mt(const void *x, const void *y, int dtype, uint64_t n, uint32_t N,
+                      double *out, int threads)
+{
+    fmt_t F;
+    int st = fmt_init(&F, dtype, N);
+    if (st) return st;
+    const uint64_t nb = nblocks_of(n, N);
+    double *bs = (double *)malloc(sizeof(double) * 6 * (nb ? nb : 1));
+    double *col = (double *)malloc(sizeof(double) * (nb ? nb : 1));
+    if (!bs || !col) {
+        free(bs);
+        free(col);
+        return ST_INVALID_ARG;
+    }
+    const int T = mt_threads(threads, nb);
+    mt_job jobs[256];
+    memset(jobs, 0, sizeof jobs);
+    mt_split(jobs, T, nb);
+    for (int i = 0; i < T; ++i) {
+        jobs[i].x = x;
+        jobs[i].yy = y;
+        jobs[i].dtype = dtype;
+        jobs[i].n = n;
+        jobs[i].N = N;
+        jobs[i].sums = bs + 6 * jobs[i].b0;
+    }
+    st = mt_run(jobs, T, sums_worker);
+    for (int k = 0; k < 6 && !st; ++k) {
+        for (uint64_t j = 0; j < nb; ++j) col[j] = bs[6 * j + k];
+        out[k] = tree16(col, nb);
+    }
+    free(bs);
+    free(col);
+    return st;
+}
+
+/* oracle_profile with the threaded encode, decode and sums. */
+int oracle_profile_mt(const void *x, int dtype, uint64_t n, uint32_t N, const uint16_t *cand,
+                      int ncand, double target, oracle_point *pts, int *recommended, int threads)
+{
+    fmt_t F;
+    int st = fmt_init(&F, dtype, N);
+    if (st) return st;
+    if (ncand < 1) return ST_INVALID_ARG;
+    for (int i = 0; i < ncand; ++i) {
+        if (cand[i] > 4095 || (cand[i] & 127) != 0) return ST_INVALID_ARG;
+        if (i > 0 && cand[i] <= cand[i - 1]) return ST_INVALID_ARG;
+    }
+    uint64_t cap;
+    st = oracle_encoded_size(dtype, n, N, MODE_FQ, 1, 1, 0, &cap);
+    if (st) return st;
+    uint8_t *buf = (uint8_t *)malloc(cap);
+    void *y = malloc((size_t)(n ? n : 1) * F.size);
+    if (!buf || !y) {
+        free(buf);
+        free(y);
+        return ST_INVALID_ARG;
+    }
+    int rec = -1, ok_prefix = 1;
+    for (int i = 0; i < ncand; ++i) {
+        uint64_t bytes;
+        st = oracle_encode_mt(x, dtype, n, N, MODE_FQ, 1, 1, cand[i], buf, cap, &bytes, threads);
+        if (st) break;
+        st = oracle_decode_mt(buf, bytes, y, dtype, n, threads);
+        if (st) break;
+        double s[6];
+        st = oracle_metrics_mt(x, y, dtype, n, N, s, threads);
+        if (st) break;
+        pts[i].code = cand[i];
+        pts[i].flags = 0;
+        pts[i].bytes = bytes;
+        pts[i].sx = s[0]; pts[i].sy = s[1]; pts[i].sxx = s[2];
+        pts[i].sxy = s[3]; pts[i].syy = s[4]; pts[i].sdd = s[5];
+        pts[i].r = oracle_corr(s[2], s[3], s[4]);
+        if (ok_prefix && pts[i].r >= target) rec = i;
+        else ok_prefix = 0;
+    }
+    free(buf);
+    free(y);
+    if (st) return st;
+    *recommended = rec < 0 ? 0 : rec;
+    return rec < 0 ? 1 : ST_OK;
 }
