@@ -996,7 +996,10 @@ typedef struct {
 } oracle_point;
 
 /* Sec. 4: for each candidate code, encode (fixed quality) and decode the
- * array, then compare the decoded y with the original x.  The recommended
+ * array, then compare the decoded y with the original x.  Candidates are any
+ * strictly increasing codes of 0..4095 (Sec. 6: the attenuator's
+ * multiplier is a floating-point value, not only a power of two).  The
+ * recommended
  * point is the largest i with r_j >= target for all j <= i (candidates in
  * increasing attenuation); 0 if even r_0 misses the target. */
 int oracle_profile(const void *x, int dtype, uint64_t n, uint32_t N, const uint16_t *cand,
@@ -1007,7 +1010,7 @@ int oracle_profile(const void *x, int dtype, uint64_t n, uint32_t N, const uint1
     if (st) return st;
     if (ncand < 1) return ST_INVALID_ARG;
     for (int i = 0; i < ncand; ++i) {
-        if (cand[i] > 4095 || (cand[i] & 127) != 0) return ST_INVALID_ARG;
+        if (cand[i] > 4095) return ST_INVALID_ARG;
         if (i > 0 && cand[i] <= cand[i - 1]) return ST_INVALID_ARG;
     }
     uint64_t cap;
@@ -1450,7 +1453,7 @@ int oracle_profile_mt(const void *x, int dtype, uint64_t n, uint32_t N, const ui
     if (st) return st;
     if (ncand < 1) return ST_INVALID_ARG;
     for (int i = 0; i < ncand; ++i) {
-        if (cand[i] > 4095 || (cand[i] & 127) != 0) return ST_INVALID_ARG;
+        if (cand[i] > 4095) return ST_INVALID_ARG;
         if (i > 0 && cand[i] <= cand[i - 1]) return ST_INVALID_ARG;
     }
     uint64_t cap;

@@ -508,12 +508,66 @@ def test_profile_consistency():
     assert pts[0].sdd == 0.0 and pts[0].r == 1.0
 
 
-def test_profile_rejects_non_power_of_two_codes():
+def test_profile_rejects_bad_candidate_lists():
     x = np.zeros(64, dtype=np.float32)
     with pytest.raises(O.OracleError):
-        O.profile(x, N=64, candidates=[0, 130])
+        O.profile(x, N=64, candidates=[256, 0])  # not increasing
     with pytest.raises(O.OracleError):
-        O.profile(x, N=64, candidates=[256, 0])
+        O.profile(x, N=64, candidates=[0, 0])
+    with pytest.raises(O.OracleError):
+        O.profile(x, N=64, candidates=[0, 4096])
+
+
+def _python_decoded(x, N, code):
+    """y of a fixed-quality round trip at `code`, from the Python codec's
+    quantiser and the decoder arithmetic of Sec. 6 restated with exact
+    rationals: R[m] = RNE(2^32/(256-m)); ints y = clamp(RNE(q R[m] 2^(k-24))),
+    floats y = q R[m] 2^(Eb-Q+k-24) rounded once to the format."""
+    dt = x.dtype.type
+    Q = P.INFO[x.dtype][3]
+    k, m = code >> 7, code & 127
+    R = round(Fraction(1 << 32, 256 - m))
+    out = []
+    for j in range(0, x.size, N):
+        xb = x[j:j + N].tolist()
+        Eb = P.block_exp(xb) if Q else 0
+        for q in P.quant(xb, x.dtype, code, Eb):
+            if Q is None:
+                info = np.iinfo(dt)
+                v = round(Fraction(q * R) * Fraction(2) ** (k - 24)) if code != 4095 else 0
+                out.append(min(max(v, info.min), info.max))
+            else:
+                v = Fraction(q * R) * Fraction(2) ** (Eb - Q + k - 24) if code != 4095 else 0
+                out.append(_round_fraction_to(Fraction(v), dt) if v else dt(0.0))
+    return np.array(out, dtype=dt)
+
+
+@pytest.mark.parametrize("dt", [np.int16, np.int32, np.float32, np.float64])
+def test_profile_general_codes_vs_python_codec(dt):
+    """Profile points at codes with m != 0 (attenuations that are not powers
+    of two) against a second implementation: packet sizes from the Python
+    codec, y from exact-rational dequantisation, sums exact per block and
+    added in the fan-in-16 tree, r by the Sec. 4 formula."""
+    rng = np.random.default_rng(17)
+    N, n = 64, 64 * 5 + 21
+    w = np.cumsum(rng.standard_normal(n))
+    if np.dtype(dt).kind == "i":
+        x = np.round(w * (900 if dt == np.int16 else 4e6)).astype(dt)
+    else:
+        x = (w * 2.5).astype(dt)
+    cands = [0, 130, 701, 1153, 1999, 2900, 4095]
+    pts, _, _ = O.profile(x, N=N, candidates=cands, target=0.999)
+    for p, code in zip(pts, cands):
+        assert p.code == code
+        assert p.bytes == len(P.encode(x, N, O.MODE_FQ, 1, 1, code))
+        y = _python_decoded(x, N, code)
+        bs = _exact_block_sums(x, y, N)
+        want = [_tree16([b[i] for b in bs]) for i in range(6)]
+        assert [p.sx, p.sy, p.sxx, p.sxy, p.syy, p.sdd] == want, code
+        sxx, sxy, syy = want[2], want[3], want[4]
+        r = 1.0 if sxx == 0 and syy == 0 else (0.0 if sxx == 0 or syy == 0
+                                                 else sxy / math.sqrt(sxx * syy))
+        assert p.r == r
 
 
 def test_edge_cases_and_errors():
