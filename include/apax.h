@@ -172,8 +172,10 @@ int apax_profile_workspace_size(int dtype, uint64_t n, uint32_t block_size, int 
                                 uint64_t *bytes /* host */);
 
 /* Sweep ncand candidate codes over x.  candidates (host) must be strictly
- * increasing multiples of 128 (power-of-two attenuations a = 2^-k); NULL
- * selects the default ladder (ncand must then be 16).  The recommended
+ * increasing codes of 0..4095; NULL selects the default ladder (ncand must
+ * then be 16).  Power-of-two attenuations (codes that are multiples of 128)
+ * take the fast exact-sum path; float candidates with m != 0 are summed by
+ * an exact superaccumulator per block and sweep markedly slower.  The recommended
  * candidate is the largest i with r_j >= target for every j <= i, else 0
  * with summary->flags bit 0 set.  points (ncand entries) and summary are
  * written by the device; the call is asynchronous. */

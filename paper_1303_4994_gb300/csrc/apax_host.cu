@@ -84,8 +84,8 @@ int fill_prof_args(const void *x, int dtype, uint64_t n, uint32_t block_size,
     if (((uintptr_t)x % f.size) || ((uintptr_t)points & 7) || ((uintptr_t)summary & 7))
         return APAX_ERR_INVALID_ARG;
     for (int i = 0; i < ncand; ++i) {
-        // power-of-two attenuations only (m = 0), strictly increasing
-        if (candidates[i] > 4095 || (candidates[i] & 127)) return APAX_ERR_INVALID_ARG;
+        // strictly increasing codes of 0..4095
+        if (candidates[i] > 4095) return APAX_ERR_INVALID_ARG;
         if (i && candidates[i] <= candidates[i - 1]) return APAX_ERR_INVALID_ARG;
     }
     if (!(target == target)) return APAX_ERR_INVALID_ARG;

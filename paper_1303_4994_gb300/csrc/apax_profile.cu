@@ -8,16 +8,20 @@
 // Sec. 6), then per candidate the chosen stream's exponents and JEE token
 // count (packet size) and the exact block sums.
 //
-// Candidates are power-of-two attenuations a = 2^-k (codes with m = 0).  For
-// floats the decoded value is then exactly y = q 2^s with s = Eb - Q + k, so
-// with the quantiser remainder d = x - y = D' 2^(s-P):
+// Candidates are any increasing codes.  For the power-of-two attenuations
+// a = 2^-k (codes with m = 0) and floats the decoded value is exactly
+// y = q 2^s with s = Eb - Q + k, so with the quantiser remainder
+// d = x - y = D' 2^(s-P):
 //   sum y    = 2^s  sum q
 //   sum y^2  = 2^2s A,               A = sum q^2
 //   sum xy   = 2^2s A + 2^(2s-P) B,  B = sum q D'
 //   sum d^2  = sum x^2 - 2^2s A - 2^(2s-P+1) B
 // all exact in 64/128/256-bit integers.  Blocks with values too small for
-// the fixed-point window of sum x^2, and candidates whose y leaves the normal
-// range, take an exact fallback with a shared-memory superaccumulator.  Each
+// the fixed-point window of sum x^2, candidates whose y leaves the normal
+// range, and float candidates with m != 0 (y = q R[m] 2^(s-24) rounded to
+// the format, the decoder's reciprocal table) take an exact fallback with a
+// shared-memory superaccumulator.  Integer candidates dequantise with the
+// decoder's formula directly.  Each
 // block sum is rounded once to binary64 and added into the run's partial in
 // block order.
 #include <type_traits>
@@ -152,9 +156,10 @@ __device__ void fallback_team(const TBlock<DT> &b, int code, bool want_block,
                 }
                 if (want_cand) {
                     const int32_t q = Q(xv[k]);
-                    typename T::bits yb = q ? round_to_format<DT>((int64_t)q * (1ll << 24),
-                                                                   b.Eb - T::Q + (code >> 7) - 24)
-                                            : 0;
+                    typename T::bits yb =
+                        q ? round_to_format<DT>((int64_t)q * (int64_t)recip_entry(code & 127),
+                                                b.Eb - T::Q + (code >> 7) - 24)
+                          : 0;
                     FDec<DT> dy = fdec<DT>(yb);
                     if (!q) dy.M = 0;
                     const u128 xy = (u128)dx.M * dy.M, yy = (u128)dy.M * dy.M;
@@ -445,7 +450,8 @@ __device__ __forceinline__ void profile_run(const ProfArgs &a, uint64_t run, uin
 #pragma unroll
                 for (int jj = 0; jj < 3; ++jj) {
                     const int cd = (int)a.codes[ci + jj];
-                    ok &= Quant<DT>(cd, b.Eb).mode == 1 && b.Eb + (cd >> 7) <= 127;
+                    ok &= Quant<DT>(cd, b.Eb).mode == 1 && b.Eb + (cd >> 7) <= 127 &&
+                          (cd & 127) == 0;
                 }
                 if (__all_sync(kFull, ok || !b.active)) {
                     profile_chunk3(b, s, ge, &a.codes[ci], cs + ci, t);
@@ -458,9 +464,13 @@ __device__ __forceinline__ void profile_run(const ProfArgs &a, uint64_t run, uin
         const int k = code >> 7;
         const Quant<DT> Q(code, b.Eb);
         const int s_exp = b.Eb - T::Q + k;
+        const bool pow2 = (code & 127) == 0;
         bool fast = true;
-        if constexpr (DT == 4) fast = !tiny && b.Eb >= -80 && b.Eb + k <= 127 && Q.mode != 0;
-        if constexpr (DT == 5) fast = !tiny && s_exp >= T::EMIN_U && b.Eb + k <= T::EMAXV;
+        if constexpr (DT == 4) fast = pow2 && !tiny && b.Eb >= -80 && b.Eb + k <= 127 && Q.mode != 0;
+        if constexpr (DT == 5) fast = pow2 && !tiny && s_exp >= T::EMIN_U && b.Eb + k <= T::EMAXV;
+        // integers: the decoder's y = clamp(RNE(q R[m] 2^(k-24))), which is
+        // q 2^k for m = 0
+        [[maybe_unused]] const int64_t Rm = (int64_t)recip_entry(code & 127);
         TokCount tc;
         tc.init();
         int64_t sq = 0, sA = 0, sB = 0, sD = 0;  // 64-bit partials (f32, i8, i16)
@@ -531,9 +541,26 @@ __device__ __forceinline__ void profile_run(const ProfArgs &a, uint64_t run, uin
                         }
                     } else {
                         const int64_t xi = (int64_t)xv[i];
-                        int64_t yv = (int64_t)qi * ((int64_t)1 << k);
                         constexpr int64_t lo = DT == 1 ? -128 : (DT == 2 ? -32768 : -2147483648ll);
                         constexpr int64_t hi = DT == 1 ? 127 : (DT == 2 ? 32767 : 2147483647ll);
+                        int64_t yv;
+                        if (pow2) {
+                            yv = (int64_t)qi * ((int64_t)1 << k);
+                        } else if (qi == 0 || code == 4095) {
+                            yv = 0;
+                        } else {
+                            // the decoder's arithmetic: |q| < 2^31 and R[m] < 2^25, so
+                            // V fits 56 bits; k >= 24 scales up with saturation
+                            const int64_t V = (int64_t)qi * Rm;
+                            if (k <= 23) {
+                                yv = rne_shift_s64(V, 24 - k);
+                            } else {
+                                const int sh2 = k - 24;
+                                const int64_t lim = (int64_t)1 << (62 - sh2);
+                                yv = V >= lim ? INT64_MAX
+                                              : (V <= -lim ? INT64_MIN : V * ((int64_t)1 << sh2));
+                            }
+                        }
                         yv = yv < lo ? lo : (yv > hi ? hi : yv);
                         const int64_t dd = xi - yv;
                         if constexpr (DT == 3) {

@@ -263,6 +263,20 @@ def test_profile_parity_tiny_values(dt):
     _profile_parity(x, 1000, [0, 128, 1024, 2944], 0.99)
 
 
+@pytest.mark.parametrize("dt", [1, 2, 3, 4, 5])
+def test_profile_parity_general_codes(dt):
+    # attenuations that are not powers of two (m != 0): integers dequantise
+    # with the decoder's reciprocal table, floats go through the exact
+    # superaccumulator; points must equal the oracle's bit for bit
+    rng = np.random.default_rng(80 + dt)
+    x = _data(dt, 256 * 21 + 37, rng, 1)
+    _profile_parity(x, 256, [0, 1, 130, 701, 1153, 1999, 2900, 4095], 0.9999)
+    _profile_parity(x, 64, [5, 256, 300, 1280, 1333], 0.99)
+    if dt >= 4:
+        xa = _data(dt, 256 * 5 + 3, rng, 2)
+        _profile_parity(xa, 256, [64, 1100, 2049], 0.9)
+
+
 def test_profile_parity_image_field():
     x = synth.grf2d(512, 512, seed=11)
     pts, summ = _profile_parity(x, 256, list(A.DEFAULT_CANDIDATES), 0.9999)
