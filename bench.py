@@ -5,12 +5,17 @@ profiler sweep (16 power-of-two attenuation codes, exact sizes and
 reconstruction sums, recommendation at r >= 0.9999) -> fixed-quality encode
 at the recommended code (read on the device) -> decode.  Workload: the
 float32 4096x4096 k^-3 random field.  `value` is GB/s of uncompressed data
-through the step, which is captured once as a CUDA graph and replayed (L2
-flushed before each timed replay); encode, decode and profile are also timed
-on their own.  `e2e` runs the step from pinned host memory through the
-public calls: the host-input sweep (the array crosses in pieces on a copy
-stream while pieces already there are swept), encode, decode, and the copy
-of the container and profile points back.
+through the step (median of K steps), which is captured once as a CUDA
+graph and replayed (L2 flushed before each timed replay); encode, decode and
+profile are also timed on their own (medians of max(K, 20) calls), and
+`roofline` gives the HBM fraction of the one with the largest time.  `e2e`
+runs the step from pinned host memory through the public calls: the
+host-input sweep (the array crosses in pieces on a copy stream while pieces
+already there are swept), encode, decode, and the copy of the container, the
+profile points and the decoded array back.  `cpu_baseline` is the oracle on
+every host core (threads over block ranges) and, beside it, on one core.
+At N = 1 the default run also measures the int16 sensor trace at 4:1 and
+the float64 512^3 field (`workloads`).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                   [--workload field|sensor|field3d|batched|serving]
@@ -52,26 +57,68 @@ N_BLOCK = 256
 E2E_CHUNKS = 8  # pieces of the host-to-device copy that the sweep overlaps
 
 
-# Profiler sweep, integer operations per sample of the algorithm (16
-# candidates x (quantise 2, derivative 2, width 2, exact sums 7, exponent
-# and JEE 2) + stream decision 17 + block sums 6 + maximum 2).
-PROFILE_OPS_PER_SAMPLE = 16 * 15 + 17 + 6 + 2
-ALU_PEAK_TOPS = 152 * 4 * 32 * 2.070e9 / 1e12
+CPU_ROWS = 1024  # rows of the field in the oracle's timed sample (16 MiB)
+CPU_ROWS_1CORE = 256  # rows in the single-core sample (4 MiB)
 
 
-def _traffic(kernel):
-    """DRAM bytes per launch of `kernel` on this workload, from the committed
-    ncu summary (profiles/traffic_f32_4096x4096.txt: 'kernel bytes' lines)."""
+def _profile_figure(kernel, key=None):
+    """Figures of the committed ncu summary of this workload
+    (profiles/traffic_f32_4096x4096.txt): 'kernel bytes' lines give the DRAM
+    read + write bytes of one launch, 'issue_active kernel frac' lines the
+    issue-active fraction per scheduler."""
     path = os.path.join(ROOT, "profiles", "traffic_f32_4096x4096.txt")
     try:
         with open(path) as f:
             for ln in f:
                 parts = ln.split()
-                if len(parts) == 2 and parts[0] == kernel:
+                if key is None and len(parts) == 2 and parts[0] == kernel:
                     return int(parts[1])
+                if key is not None and len(parts) == 3 and parts[0] == key and parts[1] == kernel:
+                    return float(parts[2])
     except OSError:
         pass
     return None
+
+
+def _traffic(kernel):
+    return _profile_figure(kernel)
+
+
+def _issue_active(kernel):
+    return _profile_figure(kernel, "issue_active")
+
+
+def _events(fn, reps, stream, flush=None):
+    """CUDA-event times (ms) of `reps` calls of fn on `stream`, each after an
+    optional L2 flush (outside the events)."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(reps)]
+    for a, b in ev:
+        if flush is not None:
+            flush.zero_()
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def _median(v):
+    return float(np.median(np.asarray(v, dtype=np.float64)))
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu), or the machine type."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
 
 
 def _peaks():
@@ -235,30 +282,21 @@ def run_ours(args, rank, world, local_rank):
     ratio = xb / er.bytes
     met = A.derived(pt, n)
 
-    def timed(fn, k):
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(k)]
-        for a, b in ev:
-            flush.zero_()
-            a.record(stream)
-            fn()
-            b.record(stream)
-        torch.cuda.synchronize()
-        return [a.elapsed_time(b) for a, b in ev]
-
+    # per-call timings: at least 20 runs each (median), on the launching stream
+    reps = max(args.steps, 20)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     with Clocks(local_rank) as clk:
-        t_step = timed(graph.replay, args.steps)
-        t_prof = timed(prof, args.steps)
-        t_enc = timed(enc, args.steps)
-        t_dec = timed(dec, args.steps)
+        t_step = _events(graph.replay, args.steps, stream, flush)
+        t_prof = _events(prof, reps, stream, flush)
+        t_enc = _events(enc, reps, stream, flush)
+        t_dec = _events(dec, reps, stream, flush)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    ms = float(np.mean(t_step))
-    ms_prof, ms_enc, ms_dec = (float(np.mean(t)) for t in (t_prof, t_enc, t_dec))
+    ms = _median(t_step)
+    ms_prof, ms_enc, ms_dec = (_median(t) for t in (t_prof, t_enc, t_dec))
 
     # end to end through the C ABI with host buffers: the host-input sweep
     # (H2D of x in pieces on a copy stream, hidden behind the sweep), encode,
@@ -266,6 +304,7 @@ def run_ours(args, rank, world, local_rank):
     xh = torch.from_numpy(x_host.reshape(-1)).pin_memory()
     outh = torch.empty(cap, dtype=torch.uint8).pin_memory()
     ptsh = torch.empty_like(pts, device="cpu").pin_memory()
+    yh = torch.empty_like(y, device="cpu").pin_memory()
     copy_stream = torch.cuda.Stream(device=dev)
     e2e_ms = []
     for i in range(args.steps + 2):
@@ -279,10 +318,12 @@ def run_ours(args, rank, world, local_rank):
         er_len = A.read_result(eres).bytes  # sync point: the container size
         outh[:er_len].copy_(out[:er_len], non_blocking=True)
         ptsh.copy_(pts, non_blocking=True)
+        yh.copy_(y, non_blocking=True)
         torch.cuda.synchronize()
         if i >= 2:
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e = float(np.mean(e2e_ms))
+    e2e = _median(e2e_ms)
+    assert torch.equal(yh.view(torch.int32), y.view(torch.int32).cpu())
 
     ms, ms_prof, ms_enc, ms_dec, e2e = max_over_ranks([ms, ms_prof, ms_enc, ms_dec, e2e], dev, world)
 
@@ -297,22 +338,17 @@ def run_ours(args, rank, world, local_rank):
     }
     for k in kern.values():
         k["frac_hbm"] = k["gbs"] / peak
+    # the roofline of the kernel with the largest share of the step: its
+    # algorithmic bytes (read s per element, plus the container for encode
+    # and decode) over its CUDA-event time, against the measured copy peak;
+    # ncu's issue-active fraction of the same kernel sits beside it
     dom = max(kern, key=lambda k: kern[k]["ms"])
-    traffic = _traffic(dom)
-    if dom == "profile":
-        # the sweep is bound by integer issue: algorithmic operations per
-        # sample (the model stated with the design notes) over the issue peak
-        ops = PROFILE_OPS_PER_SAMPLE * n / (ms_prof * 1e-3)
-        roof = {"bound": "alu", "kernel": dom, "achieved": ops / 1e12,
-                "peak": ALU_PEAK_TOPS, "unit": "Tops/s", "frac": ops / 1e12 / ALU_PEAK_TOPS,
-                "traffic": traffic, "ops_per_sample": PROFILE_OPS_PER_SAMPLE,
-                "peak_source": "152 SMs x 4 schedulers x 32 lanes x 2070 MHz (one warp "
-                               "instruction per scheduler per clock)",
-                "hbm_frac": kern[dom]["gbs"] / peak}
-    else:
-        roof = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["gbs"], "peak": peak,
-                "unit": "GB/s", "frac": kern[dom]["gbs"] / peak, "traffic": traffic,
-                "peak_source": f"{peak_kind} hbm_gbs"}
+    alg = {"profile": prof_bytes, "encode": enc_bytes, "decode": dec_bytes}[dom]
+    roof = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["gbs"], "peak": peak,
+            "unit": "GB/s", "frac": kern[dom]["gbs"] / peak, "traffic": _traffic(dom),
+            "algorithmic_bytes": alg, "ms": kern[dom]["ms"],
+            "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
+            "ncu_issue_active": _issue_active(dom)}
     line = {
         "metric": METRIC,
         "value": round(aggregate_gbs(xb, world, ms), 3),
@@ -329,6 +365,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": WORKLOAD, "elements": n, "block_size": N_BLOCK, "candidates": nc,
                    "target_corr": TARGET, "l2": "flushed (512 MB write) before every timed step",
                    "launch": "each step replays one CUDA graph of the three calls",
+                   "timing": "median of K step times; per-call medians of max(K, 20) runs",
                    "parallelism": f"independent arrays per GPU x{world}"},
         "ratio": round(ratio, 4),
         "corr": pt.r,
@@ -339,51 +376,72 @@ def run_ours(args, rank, world, local_rank):
         "kernels": kern,
         "roofline": roof,
         "e2e": {"value": round(world * xb / e2e / 1e6, 3), "unit": "GB/s",
-                "h2d_bytes_per_step": xb, "d2h_bytes_per_step": er.bytes + pts.numel(),
-                "ms_per_step": round(e2e, 4)},
-        # timed region: K steps, then K profile, K encode, K decode sweeps
-        "gpu_launches": args.steps * (2 * launches_per_step),
+                "h2d_bytes_per_step": xb,
+                "d2h_bytes_per_step": er.bytes + pts.numel() + y.numel() * y.element_size(),
+                "ms_per_step": round(e2e, 4),
+                "path": "apax_profile_from_host (H2D in 8 pieces under the sweep) -> "
+                        "apax_encode_recommended -> apax_decode -> D2H of container, points "
+                        "and decoded array; median of K steps"},
+        # timed region: K graph replays of the step, then max(K, 20) profile,
+        # encode and decode calls each
+        "gpu_launches": (args.steps + reps) * launches_per_step,
         "clocks": clk.summary(),
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"]["single_core"] = cpu_baseline(rows=CPU_ROWS_1CORE, threads=None)
+    if world == 1 and rank == 0 and not args.no_extra:
+        # the other single-GPU workloads, measured in the same run
+        line["workloads"] = {"sensor_i16_fr4": run_sensor(args, compact=True),
+                             "field3d_f64_512": run_field3d(args, compact=True)}
     return line
 
 
-def cpu_baseline(rows: int = 1024):
+def cpu_baseline(rows: int = CPU_ROWS, threads=0, x=None):
     """The oracle, as it stands, on a bounded slice of the same workload:
     profile (16 codes) + fixed-quality encode at the recommended code +
-    decode of the first `rows` rows of the field, single-threaded."""
+    decode of the first `rows` rows of the field; threads=0 runs its
+    threaded drivers on every host core (contiguous block ranges), None its
+    plain sequential calls on one core."""
     import oracle as O
     from paper_1303_4994_gb300 import synth
 
-    x = synth.grf2d(4096, 4096, seed=1)[:rows].copy()
+    if x is None:
+        x = synth.grf2d(4096, 4096, seed=1)[:rows].copy()
+    cores = 1 if threads is None else O.threads(threads)
     t0 = time.perf_counter()
-    pts, rec, _ = O.profile(x, N=N_BLOCK, target=TARGET)
-    c = O.encode(x, N_BLOCK, O.MODE_FQ, 1, 1, pts[rec].code)
-    O.decode(c, np.float32, x.size)
+    pts, rec, _ = O.profile(x, N=N_BLOCK, target=TARGET, threads=threads)
+    c = O.encode(x, N_BLOCK, O.MODE_FQ, 1, 1, pts[rec].code, threads=threads)
+    O.decode(c, np.float32, x.size, threads=threads)
     dt = time.perf_counter() - t0
-    return {"value": round(x.nbytes / dt / 1e9, 6), "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {rows} rows ({x.nbytes >> 20} MiB) of the field: profile+encode+decode",
+    return {"value": round(x.nbytes / dt / 1e9, 6), "unit": "GB/s", "cores": cores,
+            "kind": "oracle", "cpu": cpu_model(), "nproc": os.cpu_count(),
+            "sample": f"first {rows} rows ({x.nbytes >> 20} MiB) of the field: profile 16 codes "
+                      f"+ encode + decode, {'all cores, threads over block ranges' if cores > 1 else 'one core'}",
             "seconds": round(dt, 2)}
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the oracle (the paper has no code to install) on
+    the host cores, on the same sample as cpu_baseline, one sample per step."""
     if rank != 0:
         return None
+    from paper_1303_4994_gb300 import synth
+    x = synth.grf2d(4096, 4096, seed=1)[:CPU_ROWS].copy()
     steps = []
-    cb = None
     for i in range(max(args.warmup, 0) + args.steps):
-        cb = cpu_baseline(rows=256)
+        cb = cpu_baseline(rows=CPU_ROWS, x=x)
         if i >= args.warmup:
             steps.append(cb)
-    v = float(np.mean([s["value"] for s in steps]))
+    v = _median([s["value"] for s in steps])
+    ms = _median([s["seconds"] * 1e3 for s in steps])
     return {"impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": "GB/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "sample": steps[-1]["sample"]},
-            "cpu_baseline": {"value": round(v, 6), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": round(v, 6), "unit": "GB/s", "cores": steps[-1]["cores"],
+                             "kind": "oracle", "cpu": steps[-1]["cpu"],
                              "sample": steps[-1]["sample"]},
             "e2e": {"value": round(v, 6), "unit": "GB/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -464,16 +522,7 @@ def run_batched(args):
             A.profile_into(x, N_BLOCK, list(A.DEFAULT_CANDIDATES), TARGET, pws, pt, sm, stream)
 
     def timed(fn, reps):
-        ts = []
-        for _ in range(reps):
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            fn()
-            b.record(stream)
-            torch.cuda.synchronize()
-            ts.append(a.elapsed_time(b))
-        return float(np.mean(ts))
+        return _median(_events(fn, reps, stream))
 
     runs = {"batched_encode": lambda: eplan.run(stream), "plain_encode": plain_enc,
             "batched_decode": lambda: dplan.run(stream), "plain_decode": plain_dec,
@@ -520,7 +569,7 @@ def run_batched(args):
     }
 
 
-def run_sensor(args):
+def run_sensor(args, compact=False):
     """int16 sensor trace at 4:1: single-call latency of the 262,144-sample
     trace, and throughput on a 4 GiB array of 8,192 copies (cold L2)."""
     import torch
@@ -544,16 +593,7 @@ def run_sensor(args):
                 torch.empty_like(x), A.new_result(dev), A.new_result(dev))
 
     def timed(fn, reps):
-        ts = []
-        for _ in range(reps):
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            fn()
-            b.record(stream)
-            torch.cuda.synchronize()
-            ts.append(a.elapsed_time(b))
-        return float(np.mean(ts))
+        return _median(_events(fn, max(reps, 20), stream))
 
     out, ews, dws, y, er, dr = bufs(t)
     for _ in range(max(args.warmup, 3)):
@@ -573,8 +613,17 @@ def run_sensor(args):
         ms_enc = timed(lambda: A.encode_into(xr, p, out, ews, er, stream), args.steps)
         ms_dec = timed(lambda: A.decode_into(out, y, dws, dr, stream), args.steps)
     xb, cb = xr.numel() * 2, A.read_result(er).bytes
+    assert A.read_result(er).status == 0 and A.read_result(dr).status == 0
     peak, peak_kind = _peaks()
     enc_gbs, dec_gbs = (xb + cb) / ms_enc / 1e6, (xb + cb) / ms_dec / 1e6
+    if compact:
+        return {"workload": "int16 sensor trace (262,144 samples, seed 0), fixed rate 4:1, N=256, "
+                            "BISECT; 4 GiB = 8,192 copies for throughput",
+                "single_call_us": {"encode": round(lat_enc * 1e3, 2), "decode": round(lat_dec * 1e3, 2)},
+                "replica_gbs_uncompressed": {"encode": round(xb / ms_enc / 1e6, 2),
+                                             "decode": round(xb / ms_dec / 1e6, 2)},
+                "hbm_frac": {"encode": round(enc_gbs / peak, 4), "decode": round(dec_gbs / peak, 4)},
+                "ratio": round(xb / cb, 4), "clocks": clk.summary()}
     return {
         "metric": METRIC, "value": round(xb / (ms_enc + ms_dec) / 1e6, 3), "unit": "GB/s",
         "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 3),
@@ -594,7 +643,7 @@ def run_sensor(args):
     }
 
 
-def run_field3d(args):
+def run_field3d(args, compact=False):
     """float64 512^3 k^-4 field with blobs (1 GiB), whole array in one call:
     profile (16 codes, r >= 0.99999) -> fixed quality at the recommended code
     -> decode."""
@@ -631,16 +680,7 @@ def run_field3d(args):
         A.decode_into(out, y, dws, dr, stream)
 
     def timed(fn, reps):
-        ts = []
-        for _ in range(reps):
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            fn()
-            b.record(stream)
-            torch.cuda.synchronize()
-            ts.append(a.elapsed_time(b))
-        return float(np.mean(ts))
+        return _median(_events(fn, max(reps, 20), stream))
 
     for _ in range(max(args.warmup, 3)):
         prof()
@@ -654,6 +694,17 @@ def run_field3d(args):
         ms = {k: timed(f, args.steps) for k, f in (("profile", prof), ("encode", enc), ("decode", dec))}
     peak, peak_kind = _peaks()
     step = sum(ms.values())
+    if compact:
+        return {"workload": f"float64 {args.field3d_n}^3 k^-4 field + 4 blobs (seed 2, 1 GiB): "
+                            "profile 16 codes -> fixed quality at r>=0.99999 -> decode",
+                "gbs_step_uncompressed": round(xb / step / 1e6, 2),
+                "ms": {k: round(v, 3) for k, v in ms.items()},
+                "gbs_uncompressed": {k: round(xb / v / 1e6, 2) for k, v in ms.items()},
+                "hbm_frac": {"profile": round(xb / ms["profile"] / 1e6 / peak, 4),
+                             "encode": round((xb + r.bytes) / ms["encode"] / 1e6 / peak, 4),
+                             "decode": round((xb + r.bytes) / ms["decode"] / 1e6 / peak, 4)},
+                "ratio": round(xb / r.bytes, 4), "corr": pt.r,
+                "recommended_code": int(sm.recommended_code), "clocks": clk.summary()}
     return {
         "metric": METRIC, "value": round(xb / step / 1e6, 3), "unit": "GB/s", "n_gpus": 1,
         "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(step, 3),
@@ -791,6 +842,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the sensor and float64 field workloads of the default run")
     ap.add_argument("--workload", default="field",
                     choices=["field", "batched", "serving", "sensor", "field3d"])
     ap.add_argument("--field3d-n", type=int, default=512)

@@ -54,19 +54,35 @@ def test_reference_arm_line(monkeypatch):
     # replaced by fixed samples so the test stays fast
     import types
 
-    samples = iter([{"value": v, "sample": "stub"} for v in (1.0, 2.0, 4.0, 6.0)])
-    monkeypatch.setattr(bench, "cpu_baseline", lambda rows=256: next(samples))
+    samples = iter([{"value": v, "sample": "stub", "cores": 8, "cpu": "stub cpu", "seconds": 1.0}
+                    for v in (1.0, 2.0, 4.0, 6.0)])
+    seen = []
+
+    def stub(rows=bench.CPU_ROWS, threads=0, x=None):
+        seen.append((rows, threads, None if x is None else x.shape))
+        return next(samples)
+
+    monkeypatch.setattr(bench, "cpu_baseline", stub)
     args = types.SimpleNamespace(steps=2, warmup=2)
     assert bench.run_reference(args, 1, 2) is None
     line = bench.run_reference(args, 0, 2)
     assert line["impl"] == "reference" and line["metric"] == bench.METRIC
     assert line["value"] == 5.0 and line["n_gpus"] == 2 and line["steps"] == 2
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == 5.0
+    assert line["cpu_baseline"]["cores"] == 8
+    # the same sample as the GPU arm's cpu_baseline: the field's first rows,
+    # on all cores
+    assert all(r == bench.CPU_ROWS and t == 0 and shp == (bench.CPU_ROWS, 4096)
+               for r, t, shp in seen)
     assert line["e2e"] == {"value": 5.0, "unit": "GB/s", "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
     for k in ("unit", "warmup", "higher_is_better", "scaling", "vs_baseline", "dtype", "data",
               "config"):
         assert k in line
+
+
+def test_cpu_model_named():
+    assert isinstance(bench.cpu_model(), str) and bench.cpu_model()
 
 
 def test_committed_traffic_figures_are_read():

@@ -1,26 +1,25 @@
 """Parity at the benchmark's full sizes, in the launch configuration bench.py
-times: the GPU runs the whole array; the oracle checks sampled blocks one by
-one, and properties that hold at any size are checked on everything.
+times.  The GPU runs the whole array; the oracle's threaded drivers (the same
+per-block routines on every host core, contiguous block ranges) produce the
+whole expected result, compared byte for byte and bit for bit:
 
 * float32 4096 x 4096 k^-3 field: profile (16 codes, r >= 0.9999) ->
   fixed-quality encode at the recommended code read on the device -> decode.
-  Sampled blocks: packet bytes equal the oracle's, decoded values equal the
-  oracle's decode of the same block (encoded with its predecessor, which
-  fixes the lag decision).  Whole array: the recommended point's byte count
-  is the container size, and its r matches an fp64 recomputation from the
-  decoded array.
-* int16 sensor trace replicated 64 times, fixed rate 4:1: every copy after
-  the first repeats the first copy's packets, except its first packet,
-  whose lag decision sees the previous copy's last block (checked against
-  the oracle).
-* float64 512^3 field (1 GiB, one call): profile (16 codes, r >= 0.99999)
-  -> fixed-quality encode at the recommended code -> decode, checked as the
-  float32 field is (sampled packets and decoded blocks against the oracle,
-  exact size prediction, r against an fp64 recomputation).
+  All 16 profile points (bytes, the six sums, r) and the recommendation equal
+  the oracle's profile of the whole array; the container equals the oracle's
+  container; the decoded array equals the oracle's decode.
+* float64 512^3 field (1 GiB, one call each): the same at r >= 0.99999.
+* int16 sensor trace replicated 64 times, fixed rate 4:1: the container
+  equals the oracle's container of the whole replica, and every copy after
+  the first repeats the first copy's packets except its first packet, whose
+  lag decision sees the previous copy's last block; the decode is lossless
+  against the oracle's.
 * 40,000 blocks of float32 (the block-per-thread decoder's size): block
-  ranges decode to the whole array's values, sampled packets equal the
+  ranges decode to the whole array's values, the containers equal the
   oracle's, and a reserved stream selector is reported as corrupt.
 """
+import struct
+
 import numpy as np
 import pytest
 import torch
@@ -57,9 +56,9 @@ def _packets(container: bytes, nb: int, mode: int, budget: int = 0):
     return out
 
 
-def _profiled_fq_parity(x, dtype, target, seed):
+def _profiled_fq_parity(x, dtype, target):
     """Profile -> fixed-quality encode at the recommended code -> decode on
-    the whole array; sampled blocks against the oracle."""
+    the whole array, each result against the oracle's whole-array result."""
     n = x.size
     xt = torch.from_numpy(x).cuda()
     nc = 16
@@ -76,40 +75,39 @@ def _profiled_fq_parity(x, dtype, target, seed):
     r = A.read_result(res)
     assert sm.status == 0 and r.status == 0
     code = int(sm.recommended_code)
-    point = A.read_points(pts, nc)[sm.recommended]
+    gpts = A.read_points(pts, nc)
+    point = gpts[sm.recommended]
     assert point.code == code and point.r >= target
     assert point.bytes == r.bytes  # exact size prediction
     del ws, pws
+    # every profile point of the whole array, bit for bit
+    opts, orec, omiss = O.profile(x, N, list(A.DEFAULT_CANDIDATES), target, threads=0)
+    assert sm.recommended == orec and bool(sm.flags & 1) == omiss
+    for g, o in zip(gpts, opts):
+        assert (g.code, g.bytes) == (o.code, o.bytes)
+        for f in ("sx", "sy", "sxx", "sxy", "syy", "sdd", "r"):
+            assert struct.pack("<d", getattr(g, f)) == struct.pack("<d", getattr(o, f)), (g.code, f)
+    # the whole container and the whole decoded array
     cont = out[:r.bytes].cpu().numpy().tobytes()
+    want = O.encode(x, N, O.MODE_FQ, 1, 1, code, threads=0)
+    assert len(cont) == len(want)
+    assert cont == want
     y = A.decode(out[:r.bytes], torch.float32 if dtype == np.float32 else torch.float64, n)
     del out
-    xd = xt.double()
-    yd = y.double()
-    r64 = float((xd * yd).sum() / torch.sqrt((xd * xd).sum() * (yd * yd).sum()))
-    assert abs(r64 - point.r) < 1e-12
-    del xd, yd
-    nb = n // N
-    pk = _packets(cont, nb, 1)
     ui = np.uint32 if dtype == np.float32 else np.uint64
-    rng = np.random.default_rng(seed)
-    for j in [1, 2, nb - 1] + [int(v) for v in rng.integers(1, nb, 40)]:
-        want = O.encode_blocks(x, N, O.MODE_FQ, 1, 1, code, j, j + 1)[0]
-        assert pk[j] == want, j
-        sub = x[(j - 1) * N:(j + 1) * N]
-        ysub = O.decode(O.encode(sub, N, O.MODE_FQ, 1, 1, code), dtype, 2 * N)
-        got = y[j * N:(j + 1) * N].cpu().numpy()
-        np.testing.assert_array_equal(got.view(ui), ysub[N:].view(ui))
+    yo = O.decode(want, dtype, n, threads=0)
+    assert np.array_equal(y.cpu().numpy().view(ui), yo.view(ui))
     return point
 
 
-def test_field_4096_full_size_sampled_parity():
-    _profiled_fq_parity(synth.grf2d(4096, 4096, seed=1).reshape(-1), np.float32, 0.9999, 41)
+def test_field_4096_full_size_parity():
+    _profiled_fq_parity(synth.grf2d(4096, 4096, seed=1).reshape(-1), np.float32, 0.9999)
 
 
-def test_field3d_512_full_size_sampled_parity():
+def test_field3d_512_full_size_parity():
     # the 1 GiB float64 simulation field, encoded and decoded in one call each
     x = synth.field3d(512, seed=2).reshape(-1)
-    point = _profiled_fq_parity(x, np.float64, 0.99999, 42)
+    point = _profiled_fq_parity(x, np.float64, 0.99999)
     assert point.code > 0  # a lossy setting was chosen
 
 
@@ -118,7 +116,11 @@ def test_sensor_replica_repeats_packets():
     reps = 64
     x = np.tile(trace, reps)
     xt = torch.from_numpy(x).cuda()
-    c = A.encode(xt, N, A.FIXED_RATE, (4, 1), 0).cpu().numpy().tobytes()
+    ct = A.encode(xt, N, A.FIXED_RATE, (4, 1), 0)
+    c = ct.cpu().numpy().tobytes()
+    assert c == O.encode(x, N, O.MODE_FR, 4, 1, 0, threads=0)  # the whole replica
+    y = A.decode(ct, torch.int16, x.size).cpu().numpy()
+    np.testing.assert_array_equal(y, O.decode(c, np.int16, x.size, threads=0))
     single = O.encode(trace, N, O.MODE_FR, 4, 1, 0)
     budget = 128  # 256 int16 samples at 4:1
     nb1 = trace.size // N
@@ -146,12 +148,11 @@ def test_large_array_block_range_and_corruption():
         for b0, b1 in ((0, nb), (1000, 35000), (nb - 33000, nb)):
             part = A.decode_blocks(c, torch.float32, x.size, b0, b1, N)
             assert torch.equal(part.view(torch.int32), full[b0 * N:b1 * N].view(torch.int32))
-        # sampled blocks against the oracle
+        # the whole container and decode against the oracle
         cont = c.cpu().numpy().tobytes()
-        pk = _packets(cont, nb, mode, 256 if mode == A.FIXED_RATE else 0)
-        for j in (1, 777, nb - 1):
-            want = O.encode_blocks(x, N, mode, rate[0], rate[1], code, j, j + 1)[0]
-            assert pk[j] == want, (mode, j)
+        assert cont == O.encode(x, N, mode, rate[0], rate[1], code, threads=0), mode
+        yo = O.decode(cont, np.float32, x.size, threads=0)
+        assert np.array_equal(full.cpu().numpy().view(np.uint32), yo.view(np.uint32))
         # packet 12345's selector set to the reserved value 3
         bad = bytearray(cont)
         poff = 40 + (((4 * nb + 7) // 8) * 8 if mode == A.FIXED_QUALITY else 0)
@@ -188,5 +189,4 @@ def test_block_per_thread_decode_selector_loops(kind):
     assert (sel == want_s).mean() > 0.9, np.bincount(sel, minlength=3)
     y = A.decode(c, torch.int16, n).cpu().numpy()
     np.testing.assert_array_equal(y, x)  # code 0 is lossless for int16
-    for j in (1, 2, 777, 31999, nb - 1):
-        assert pk[j] == O.encode_blocks(x, n64, O.MODE_FQ, 1, 1, 0, j, j + 1)[0], j
+    assert cont == O.encode(x, n64, O.MODE_FQ, 1, 1, 0, threads=0)
