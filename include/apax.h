@@ -222,7 +222,12 @@ void apax_derived_metrics(const apax_profile_point *pt, uint64_t n, double *out 
  * at block size 256; fixed rate always fits); larger calls return
  * APAX_ERR_CAPACITY without touching the device.  The first call on each
  * device looks up the array's device address (once, with that device
- * current), so make it before capturing any stream into a graph.  Each call
+ * current); with CUDA's lazy module loading that first call may also load
+ * the library's device code and so allocate the fixed array itself, which
+ * can block on the driver.  Make the first call at start-up, outside any
+ * allocator hook and before capturing any stream into a graph.  The address
+ * is kept for the life of the process: do not call this entry point after
+ * cudaDeviceReset on that device.  Each call
  * clears the scratch words it uses on its stream; all calls share the one
  * array, so calls that overlap on the GPU (other streams, other threads)
  * race and must be serialised by the caller. */

@@ -110,10 +110,9 @@ size_t pkt_smem_of(const apax_batch *b, const Geo &g)
 // batch, or 0.
 size_t stage_of(const apax_batch *b, const Geo &g)
 {
-    const int pol = stage_policy();
     bool any_fr = false;
     for (const EncArgs &a : b->jobs) any_fr |= a.mode == APAX_FIXED_RATE && !t1_job(a);
-    if (pol == 0 || (pol < 0 && !any_fr)) return 0;
+    if (!any_fr) return 0;
     uint64_t mx = 0;
     for (const EncArgs &a : b->jobs) {
         Fmt f;

@@ -275,9 +275,11 @@ __device__ __forceinline__ void encode_tile(const EncArgs &a, uint64_t tile, uin
         const uint64_t jb0 = tile * (uint64_t)nteams;
         base = jb0 ? jb0 - 1 : 0;
         const uint64_t bend = min(jb0 + (uint64_t)nteams, a.nb);
-        stage_blocks<DT>(xs, x, a.n, a.N, base, bend > base ? bend : base, a.status, a.spin_limit);
+        if (stage_blocks<DT>(xs, x, a.n, a.N, base, bend > base ? bend : base, a.status, a.spin_limit))
+            x = xs;  // else (a wait ran out) read the blocks from global memory
+        else
+            base = 0;
         __syncthreads();
-        x = xs;
     }
     // stream decision: best(j-1) at code 0 (block 0 uses its own)
     int s;

@@ -125,8 +125,7 @@ int encode_impl(const void *x, int dtype, uint64_t n, const apax_params *p,
     if (wsb < need_ws) return APAX_ERR_CAPACITY;
     int ts, threads;
     Plan pl;
-    if (p->mode == APAX_FIXED_RATE && a.N <= kT1MaxBlock && a.nb >= kT1MinBlocks &&
-        stage_policy() != 1) {
+    if (p->mode == APAX_FIXED_RATE && a.N <= kT1MaxBlock && a.nb >= kT1MinBlocks) {
         // fixed rate, a block per thread: its 13-step search runs without
         // team exchanges (measured faster); fixed quality keeps teams, whose
         // packets leave through coalesced stores
@@ -140,8 +139,10 @@ int encode_impl(const void *x, int dtype, uint64_t n, const apax_params *p,
     a.ebuf_words = pl.ebuf_words;
     Fmt f;
     fmt_of(dtype, f);
-    const int pol = stage_policy();
-    const bool want = pol < 0 ? p->mode == APAX_FIXED_RATE : pol == 1;
+    // staging of the tile in shared memory: on for the fixed-rate search by
+    // teams (13 passes over a block), off for fixed quality, whose occupancy
+    // matters more than its few L2 re-reads (measured on GB300)
+    const bool want = p->mode == APAX_FIXED_RATE;
     const size_t sb = (want && pl.ts != 1) ? stage_bytes(f.size, a.N, pl.threads / pl.ts, pl.smem) : 0;
     a.stage_off = sb ? (uint32_t)((pl.smem + 15) / 16 * 16) : 0;
     if (sb) pl.smem = a.stage_off + sb;

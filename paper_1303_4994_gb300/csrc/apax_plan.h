@@ -123,20 +123,6 @@ inline void default_geometry(size_t per_team_bytes, uint64_t nb, int &ts, int &t
     }
 }
 
-// Staging policy: APAX_STAGE=0 or 1 in the environment forces shared-memory
-// staging of the input off or on (for measurement); otherwise each path
-// uses its default: on for the profiler sweep (17 passes over a block) and
-// the fixed-rate search by teams (13 passes), off for fixed quality, whose
-// occupancy matters more than its few L2 re-reads (measured on GB300).
-inline int stage_policy()
-{
-    static int p = [] {
-        const char *e = getenv("APAX_STAGE");
-        return e && (e[0] == '0' || e[0] == '1') ? e[0] - '0' : -1;
-    }();
-    return p;
-}
-
 // Shared-memory staging of a tile (its blocks and the one before): the
 // bytes, or 0 when it would not leave room for enough CTAs per SM.
 constexpr size_t kStageCap = 48 * 1024, kStageTotalCap = 100 * 1024;

@@ -289,9 +289,11 @@ __device__ __forceinline__ void profile_run(const ProfArgs &a, uint64_t run, uin
         const uint64_t jb0 = run * (uint64_t)nteams;
         base = jb0 ? jb0 - 1 : 0;
         const uint64_t bend = min(jb0 + (uint64_t)nteams, a.nb);
-        stage_blocks<DT>(xs, x, a.n, a.N, base, bend > base ? bend : base, a.status, 1ll << 31);
+        if (stage_blocks<DT>(xs, x, a.n, a.N, base, bend > base ? bend : base, a.status, 1ll << 31))
+            x = xs;  // else (a wait ran out) read the blocks from global memory
+        else
+            base = 0;
         __syncthreads();
-        x = xs;
     }
     int s;
     {
@@ -883,9 +885,8 @@ cudaError_t launch_prof_dt(const ProfArgs &a, cudaStream_t s)
     size_t smem = (size_t)kRun * a.ncand * sizeof(CandStage<DT>) + (size_t)kRun * Qn * 8 +
                   (DT_<DT>::F ? (size_t)6 * PS<DT>::ND * 8 : 0);
     ProfArgs b = a;
-    const size_t sb = host::stage_policy() != 0
-                          ? profile_stage_bytes(sizeof(typename DT_<DT>::raw), a.N, smem)
-                          : 0;
+    // the run and its halo block in shared memory (17 passes over a block)
+    const size_t sb = profile_stage_bytes(sizeof(typename DT_<DT>::raw), a.N, smem);
     b.stage_off = sb ? (uint32_t)((smem + 15) / 16 * 16) : 0;
     if (sb) smem = b.stage_off + sb;
     auto k = k_profile<DT>;

@@ -642,9 +642,13 @@ __device__ __forceinline__ void mbar_inval(uint64_t *m)
 // range moves with one TMA bulk copy; the rest (an unaligned source, the
 // ragged tail, the zeros past n) with vector loads.  The wait on the copy is
 // bounded: past `spin` clock cycles the status becomes APAX_ERR_TIMEOUT and
-// the copy is waited for once more (bounded) before the CTA goes on.
+// the copy is waited for once more (bounded).  Returns true (the same value
+// in every thread) when the staged copy is complete; false when a wait ran
+// out, in which case the caller must not read xs (it reads the array from
+// global memory instead) and the barrier, which may still expect bytes, is
+// left as it is.
 template <int DT>
-__device__ __forceinline__ void stage_blocks(typename DT_<DT>::raw *xs, const typename DT_<DT>::raw *x,
+__device__ __forceinline__ bool stage_blocks(typename DT_<DT>::raw *xs, const typename DT_<DT>::raw *x,
                                              uint64_t n, uint32_t N, uint64_t b0, uint64_t b1,
                                              int *status, long long spin)
 {
@@ -668,20 +672,19 @@ __device__ __forceinline__ void stage_blocks(typename DT_<DT>::raw *xs, const ty
     // the rest, element by element (disjoint from the bulk part)
     for (uint64_t i = s0 + bulk_elems + threadIdx.x; i < send; i += blockDim.x)
         xs[i - s0] = i < s1 ? x[i] : (raw)0;
-    if (bulk_bytes) {
-        __syncthreads();  // the barrier is initialised before anyone waits on it
-        const long long t0 = clock64();
-        bool done = mbar_try_wait(&s_mbar, 0);
-        while (!done && clock64() - t0 <= spin) done = mbar_try_wait(&s_mbar, 0);
-        if (!done) {
-            atomicMin(status, -10);
-            const long long t1 = clock64();
-            while (!mbar_try_wait(&s_mbar, 0) && clock64() - t1 <= spin) {
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) mbar_inval(&s_mbar);
+    if (!bulk_bytes) return true;
+    __syncthreads();  // the barrier is initialised before anyone waits on it
+    const long long t0 = clock64();
+    bool done = mbar_try_wait(&s_mbar, 0);
+    while (!done && clock64() - t0 <= spin) done = mbar_try_wait(&s_mbar, 0);
+    if (!done) {
+        atomicMin(status, -10);
+        const long long t1 = clock64();
+        while (!done && clock64() - t1 <= spin) done = mbar_try_wait(&s_mbar, 0);
     }
+    const bool all = __syncthreads_and(done) != 0;
+    if (all && threadIdx.x == 0) mbar_inval(&s_mbar);
+    return all;
 }
 
 // Largest packet of a block of N samples (all widths W, all tokens absolute).
