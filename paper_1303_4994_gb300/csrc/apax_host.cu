@@ -253,6 +253,7 @@ static void place_profile_workspace(ProfArgs &a, void *workspace)
     const uint64_t Qn = 2 + 4 * (uint64_t)a.ncand;
     a.run_sums = (double *)(w + kWsHead + 8 * 32);
     a.scratch = a.run_sums + Qn * (a.nruns ? a.nruns : 1);
+    a.run_flags = (uint8_t *)(a.scratch + Qn * 2 * (((a.nruns + 15) / 16) + 1));
 }
 
 }  // namespace
@@ -369,7 +370,8 @@ int apax_profile_workspace_size(int dtype, uint64_t n, uint32_t block_size, int 
     const uint64_t head = kWsHead + 8 * 32;
     const uint64_t runs = 8 * Qn * (nruns ? nruns : 1);
     const uint64_t scratch = 8 * Qn * 2 * (((nruns + 15) / 16) + 1);
-    *bytes = head + runs + scratch;
+    const uint64_t flags = (nruns + 15) / 16 * 16;  // runs left to the team sweep
+    *bytes = head + runs + scratch + flags;
     return APAX_OK;
 }
 

@@ -159,7 +159,16 @@ struct ProfArgs {
     double *scratch;    // tree levels
     apax_profile_point *points;
     apax_profile_summary *summary;
+    uint8_t *run_flags;  // [nruns] runs left to the team kernel by the one-block-per-thread
+                         // sweep (NULL: that sweep is not used)
 };
+
+// The one-block-per-thread float32 sweep (apax_profile_t1.cu): arrays of at
+// least this many blocks of at most 256 samples, candidates 0 then
+// power-of-two attenuations.
+constexpr uint64_t kProfT1MinBlocks = 16384;
+bool profile_t1_eligible(const ProfArgs &a);
+cudaError_t launch_profile_t1(const ProfArgs &a, cudaStream_t s);
 
 cudaError_t launch_encode(const EncArgs &a, int ts, int threads, size_t smem, cudaStream_t s);
 cudaError_t launch_encode_batch(const EncBatchArgs &b, int ts, int threads, size_t smem,

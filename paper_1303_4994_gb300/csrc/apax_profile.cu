@@ -707,6 +707,19 @@ __global__ void __launch_bounds__(128) k_profile(ProfArgs a)
     profile_run<DT>(a, a.run0 + blockIdx.x, psm);
 }
 
+// The runs of [run0, run1) that the one-block-per-thread sweep marked (rare
+// blocks it does not cover exactly): the team sweep, CTAs striding over the
+// range.
+template <int DT>
+__global__ void __launch_bounds__(128) k_profile_fix(ProfArgs a)
+{
+    extern __shared__ __align__(16) uint8_t psm[];
+    for (uint64_t r = a.run0 + blockIdx.x; r < a.run1; r += gridDim.x) {
+        if (a.run_flags[r]) profile_run<DT>(a, r, psm);
+        __syncthreads();
+    }
+}
+
 // One level of the fan-in-16 tree: out[m][q] = in[16m][q] + ... (in order).
 __global__ void k_tree(const double *in, double *out, uint64_t cnt, int Qn)
 {
@@ -889,6 +902,17 @@ cudaError_t launch_prof_dt(const ProfArgs &a, cudaStream_t s)
     const size_t sb = profile_stage_bytes(sizeof(typename DT_<DT>::raw), a.N, smem);
     b.stage_off = sb ? (uint32_t)((smem + 15) / 16 * 16) : 0;
     if (sb) smem = b.stage_off + sb;
+    if constexpr (DT == 4) {
+        if (profile_t1_eligible(a)) {
+            cudaError_t e = launch_profile_t1(b, s);
+            if (e != cudaSuccess) return e;
+            e = smem_limit<k_profile_fix<DT>>(smem);
+            if (e != cudaSuccess) return e;
+            const uint64_t runs = a.run1 - a.run0, cap = 2ull * (uint64_t)sm_count();
+            if (runs) k_profile_fix<DT><<<(unsigned)(runs < cap ? runs : cap), threads, smem, s>>>(b);
+            return cudaGetLastError();
+        }
+    }
     auto k = k_profile<DT>;
     const cudaError_t e = smem_limit<k_profile<DT>>(smem);
     if (e != cudaSuccess) return e;
