@@ -62,6 +62,7 @@ def lib():
         u32, p64 = ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64)
         _lib.oracle_encoded_size.argtypes = [i32, u64, u32, i32, u32, u32, i32, p64]
         _lib.oracle_encode.argtypes = [vp, i32, u64, u32, i32, u32, u32, i32, vp, u64, p64]
+        _lib.oracle_encode_s.argtypes = [vp, i32, u64, u32, i32, u32, u32, i32, i32, vp, u64, p64]
         _lib.oracle_decode.argtypes = [vp, u64, vp, i32, u64]
         _lib.oracle_metrics.argtypes = [vp, vp, i32, u64, u32, vp]
         _lib.oracle_block_sums.argtypes = [vp, vp, i32, u64, u32, u64, u64, vp]
@@ -82,16 +83,16 @@ def lib():
         _lib.oracle_block_exponent.argtypes = [vp, i32, u64, i32, ctypes.POINTER(ctypes.c_int)]
         _lib.oracle_packet_bits.argtypes = [vp, i32, u64, u32, u64, i32, i32, p64]
         _lib.oracle_streams.argtypes = [vp, i32, u64, u32, u64, u64, vp]
-        _lib.oracle_fr_code.argtypes = [vp, i32, u64, u32, u64, i32, u64,
+        _lib.oracle_fr_code.argtypes = [vp, i32, u64, u32, u64, i32, u64, i32,
                                         ctypes.POINTER(ctypes.c_int)]
-        _lib.oracle_encode_blocks.argtypes = [vp, i32, u64, u32, i32, u32, u32, i32, u64, u64,
-                                              vp, u64, vp]
+        _lib.oracle_encode_blocks.argtypes = [vp, i32, u64, u32, i32, u32, u32, i32, i32, u64,
+                                              u64, vp, u64, vp]
         _lib.oracle_fr_budget.argtypes = [i32, u32, i32, u32, u32, p64]
         _lib.oracle_min_packet.argtypes = [i32, u32, i32, p64]
         _lib.oracle_derived.argtypes = [vp, u64, vp]
         _lib.oracle_threads.argtypes = [i32]
-        _lib.oracle_encode_mt.argtypes = [vp, i32, u64, u32, i32, u32, u32, i32, vp, u64, p64,
-                                          i32]
+        _lib.oracle_encode_mt.argtypes = [vp, i32, u64, u32, i32, u32, u32, i32, i32, vp, u64,
+                                          p64, i32]
         _lib.oracle_decode_mt.argtypes = [vp, u64, vp, i32, u64, i32]
         _lib.oracle_metrics_mt.argtypes = [vp, vp, i32, u64, u32, vp, i32]
         _lib.oracle_profile_mt.argtypes = [vp, i32, u64, u32, vp, i32, ctypes.c_double, vp,
@@ -128,20 +129,24 @@ def threads(t: int = 0) -> int:
     return lib().oracle_threads(t)
 
 
+SEARCH_BISECT, SEARCH_PREDICT = 0, 1
+
+
 def encode(x: np.ndarray, N: int = 256, mode: int = MODE_FQ, num: int = 1, den: int = 1,
-           code: int = 0, threads: int | None = None) -> bytes:
+           code: int = 0, threads: int | None = None, search: int = SEARCH_BISECT) -> bytes:
     """Encode a C-contiguous array; returns the container bytes.  threads:
     None runs the plain sequential encoder; an int runs the same per-block
-    code on that many threads over block ranges (0 = all cores)."""
+    code on that many threads over block ranges (0 = all cores).  search:
+    the fixed-rate search policy (BISECT or PREDICT)."""
     x = np.ascontiguousarray(x).reshape(-1)
     cap = encoded_size(x.dtype, x.size, N, mode, num, den, code)
     buf = np.zeros(cap, dtype=np.uint8)
     out = ctypes.c_uint64()
     if threads is None:
-        st = lib().oracle_encode(_ptr(x), _code(x), x.size, N, mode, num, den, code, _ptr(buf),
-                                 cap, ctypes.byref(out))
+        st = lib().oracle_encode_s(_ptr(x), _code(x), x.size, N, mode, num, den, code, search,
+                                   _ptr(buf), cap, ctypes.byref(out))
     else:
-        st = lib().oracle_encode_mt(_ptr(x), _code(x), x.size, N, mode, num, den, code,
+        st = lib().oracle_encode_mt(_ptr(x), _code(x), x.size, N, mode, num, den, code, search,
                                     _ptr(buf), cap, ctypes.byref(out), threads)
     if st:
         raise OracleError(st, "encode")
@@ -298,10 +303,11 @@ def streams(x: np.ndarray, N: int, b0: int, b1: int) -> list:
     return out.tolist()
 
 
-def fr_code(x: np.ndarray, N: int, j: int, s: int, budget: int) -> int:
+def fr_code(x: np.ndarray, N: int, j: int, s: int, budget: int, search: int = SEARCH_BISECT) -> int:
     x = np.ascontiguousarray(x).reshape(-1)
     out = ctypes.c_int()
-    st = lib().oracle_fr_code(_ptr(x), _code(x), x.size, N, j, s, budget, ctypes.byref(out))
+    st = lib().oracle_fr_code(_ptr(x), _code(x), x.size, N, j, s, budget, search,
+                              ctypes.byref(out))
     if st:
         raise OracleError(st, "fr_code")
     return out.value
@@ -324,15 +330,15 @@ def min_packet(dtype, N: int, L: int) -> int:
 
 
 def encode_blocks(x: np.ndarray, N: int, mode: int, num: int, den: int, code: int, b0: int,
-                  b1: int):
+                  b1: int, search: int = SEARCH_BISECT):
     """Packets of blocks [b0, b1) as a list of bytes objects."""
     x = np.ascontiguousarray(x).reshape(-1)
     maxp = 4 * ((48 + 8 * (N // 4) + 32 * N + 31) // 32)
     cap = maxp * (b1 - b0)
     buf = np.zeros(cap, dtype=np.uint8)
     lens = np.zeros(b1 - b0, dtype=np.uint64)
-    st = lib().oracle_encode_blocks(_ptr(x), _code(x), x.size, N, mode, num, den, code, b0, b1,
-                                    _ptr(buf), cap, _ptr(lens))
+    st = lib().oracle_encode_blocks(_ptr(x), _code(x), x.size, N, mode, num, den, code, search,
+                                    b0, b1, _ptr(buf), cap, _ptr(lens))
     if st:
         raise OracleError(st, "encode_blocks")
     out, pos = [], 0

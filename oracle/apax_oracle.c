@@ -605,7 +605,7 @@ static void write_container_header(uint8_t *out, int dtype, uint32_t N, int mode
 
 /* Fixed-rate search (reading of the adaptive loop, policy BISECT): c = 0 if
  * it fits; else bisection on [0, 4095] keeping hi fitting (4095 always fits). */
-static int fr_search(const fmt_t *F, const void *x, uint64_t n, uint64_t j, int s,
+static int fr_bisect(const fmt_t *F, const void *x, uint64_t n, uint64_t j, int s,
                      uint64_t budget, blk_t *b, int *st)
 {
     *st = quantise_block(F, x, n, j, 0, b);
@@ -622,8 +622,78 @@ static int fr_search(const fmt_t *F, const void *x, uint64_t n, uint64_t j, int 
     return hi;
 }
 
-int oracle_encode(const void *x, int dtype, uint64_t n, uint32_t N, int mode, uint32_t num,
-                  uint32_t den, int cfq, uint8_t *out, uint64_t cap, uint64_t *bytes)
+/* Fixed-rate search, policy PREDICT (the adaptive loop of Sec. 6 read as a
+ * prediction from the code-0 packet, then a short walk up a ladder of codes).
+ * Attenuating by 2^-k narrows every group of exponent e by min(e, k) bits,
+ * so red(k) = 4 sum_g min(e_g, k) bits are predicted to go; with the excess
+ * D = packet_bits(0) - 8 B_j, k1 is the least k in 1..31 with red(k) >= D
+ * (31 if none), and the fraction f = ceil(16 (D - red(k1-1)) /
+ * (red(k1) - red(k1-1))) clamped to 1..16 (16 if the denominator is 0)
+ * places the start between the power-of-two codes 128(k1-1) and 128 k1:
+ * c = 128(k1-1) + M[f] for f < 16, else 128 k1, where a(128 k + M[f]) is
+ * 2^-(k + f/16) rounded to the attenuator's 8-bit grid,
+ * M[f] = RNE(256 (1 - 2^(-f/16))).  From there c climbs the ladder of codes
+ * 128 k + M[f'] (k = 0..31, f' = 0..15, then 4095, which always fits) until
+ * the packet fits.  As with BISECT, c = 0 when the code-0 packet already
+ * fits. */
+static const int ladder_M[16] = { 0, 11, 21, 31, 41, 50, 59, 67, 75, 83, 90, 97, 104, 110, 116, 122 };
+
+static int ladder_next(int c)
+{
+    int k = c >> 7, m = c & 127;
+    for (int f = 0; f < 16; ++f)
+        if (ladder_M[f] > m) return 128 * k + ladder_M[f];
+    return k < 31 ? 128 * (k + 1) : 4095;
+}
+
+static int fr_predict(const fmt_t *F, const void *x, uint64_t n, uint64_t j, int s,
+                      uint64_t budget, blk_t *b, int *st)
+{
+    *st = quantise_block(F, x, n, j, 0, b);
+    if (*st) return 0;
+    uint64_t bits0 = packet_bits(F, b, s); /* also leaves the code-0 exponents in b->e */
+    if (pad32_bytes(bits0) <= budget) return 0;
+    int64_t D = (int64_t)bits0 - 8 * (int64_t)budget;
+    int64_t red[32];
+    red[0] = 0;
+    for (int k = 1; k < 32; ++k) {
+        int64_t r = 0;
+        for (int g = 0; g < b->G; ++g) r += 4 * (int64_t)(b->e[g] < k ? b->e[g] : k);
+        red[k] = r;
+    }
+    int k1 = 31;
+    for (int k = 1; k < 32; ++k)
+        if (red[k] >= D) { k1 = k; break; }
+    int64_t num = 16 * (D - red[k1 - 1]), den = red[k1] - red[k1 - 1];
+    int64_t f;
+    if (den == 0) {
+        f = 16;
+    } else {
+        f = num / den; /* truncation toward zero, then the ceiling */
+        if (f * den < num) f += 1;
+    }
+    if (f < 1) f = 1;
+    if (f > 16) f = 16;
+    int c = f < 16 ? 128 * (k1 - 1) + ladder_M[f] : 128 * k1;
+    for (;;) {
+        *st = quantise_block(F, x, n, j, c, b);
+        if (*st) return 0;
+        if (c >= 4095 || pad32_bytes(packet_bits(F, b, s)) <= budget) return c;
+        c = ladder_next(c);
+    }
+}
+
+enum { SEARCH_BISECT = 0, SEARCH_PREDICT = 1 };
+
+static int fr_search(const fmt_t *F, const void *x, uint64_t n, uint64_t j, int s,
+                     uint64_t budget, blk_t *b, int *st, int search)
+{
+    return search == SEARCH_PREDICT ? fr_predict(F, x, n, j, s, budget, b, st)
+                                    : fr_bisect(F, x, n, j, s, budget, b, st);
+}
+
+int oracle_encode_s(const void *x, int dtype, uint64_t n, uint32_t N, int mode, uint32_t num,
+                    uint32_t den, int cfq, int search, uint8_t *out, uint64_t cap, uint64_t *bytes)
 {
     fmt_t F;
     int st = fmt_init(&F, dtype, N);
@@ -657,7 +727,7 @@ int oracle_encode(const void *x, int dtype, uint64_t n, uint32_t N, int mode, ui
         } else {
             int L = (int)((n - j * N) < N ? (n - j * N) : N);
             uint64_t budget = fr_budget(&F, L, num, den);
-            c = fr_search(&F, x, n, j, s, budget, b, &st);
+            c = fr_search(&F, x, n, j, s, budget, b, &st, search);
             if (st) { free(b); return st; }
             st = quantise_block(&F, x, n, j, c, b);
             if (st) { free(b); return st; }
@@ -675,6 +745,12 @@ int oracle_encode(const void *x, int dtype, uint64_t n, uint32_t N, int mode, ui
     put_le(out + 28, pos, 8);
     *bytes = payload_off + pos;
     return ST_OK;
+}
+
+int oracle_encode(const void *x, int dtype, uint64_t n, uint32_t N, int mode, uint32_t num,
+                  uint32_t den, int cfq, uint8_t *out, uint64_t cap, uint64_t *bytes)
+{
+    return oracle_encode_s(x, dtype, n, N, mode, num, den, cfq, SEARCH_BISECT, out, cap, bytes);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1118,13 +1194,13 @@ int oracle_streams(const void *x, int dtype, uint64_t n, uint32_t N, uint64_t b0
 
 /* Fixed-rate code that the search picks for block j given stream s. */
 int oracle_fr_code(const void *x, int dtype, uint64_t n, uint32_t N, uint64_t j, int s,
-                   uint64_t budget, int *code)
+                   uint64_t budget, int search, int *code)
 {
     fmt_t F;
     int st = fmt_init(&F, dtype, N);
     if (st) return st;
     blk_t *b = (blk_t *)malloc(sizeof(blk_t));
-    *code = fr_search(&F, x, n, j, s, budget, b, &st);
+    *code = fr_search(&F, x, n, j, s, budget, b, &st, search);
     free(b);
     return st;
 }
@@ -1134,8 +1210,8 @@ int oracle_fr_code(const void *x, int dtype, uint64_t n, uint32_t N, uint64_t j,
  * fixed rate, the packets are padded to their budgets; for fixed quality to
  * 32 bits.  lens[j-b0] receives each packet length. */
 int oracle_encode_blocks(const void *x, int dtype, uint64_t n, uint32_t N, int mode,
-                         uint32_t num, uint32_t den, int cfq, uint64_t b0, uint64_t b1,
-                         uint8_t *out, uint64_t cap, uint64_t *lens)
+                         uint32_t num, uint32_t den, int cfq, int search, uint64_t b0,
+                         uint64_t b1, uint8_t *out, uint64_t cap, uint64_t *lens)
 {
     fmt_t F;
     int st = fmt_init(&F, dtype, N);
@@ -1157,7 +1233,7 @@ int oracle_encode_blocks(const void *x, int dtype, uint64_t n, uint32_t N, int m
             plen = pad32_bytes(packet_bits(&F, b, s));
         } else {
             uint64_t budget = fr_budget(&F, L, num, den);
-            c = fr_search(&F, x, n, j, s, budget, b, &st);
+            c = fr_search(&F, x, n, j, s, budget, b, &st, search);
             if (st) break;
             st = quantise_block(&F, x, n, j, c, b);
             if (st) break;
@@ -1246,7 +1322,7 @@ int oracle_threads(int threads) { return mt_threads(threads, (uint64_t)1 << 40);
 typedef struct {
     /* encode */
     const void *x;
-    int dtype, mode, cfq;
+    int dtype, mode, cfq, search;
     uint64_t n;
     uint32_t N, num, den;
     uint64_t b0, b1;
@@ -1267,7 +1343,7 @@ static void *enc_worker(void *p)
 {
     mt_job *J = (mt_job *)p;
     J->st = oracle_encode_blocks(J->x, J->dtype, J->n, J->N, J->mode, J->num, J->den, J->cfq,
-                                 J->b0, J->b1, J->buf, J->cap, J->lens);
+                                 J->search, J->b0, J->b1, J->buf, J->cap, J->lens);
     return NULL;
 }
 
@@ -1315,8 +1391,8 @@ static void mt_split(mt_job *jobs, int T, uint64_t nb)
 
 /* oracle_encode, block ranges on `threads` threads. */
 int oracle_encode_mt(const void *x, int dtype, uint64_t n, uint32_t N, int mode, uint32_t num,
-                     uint32_t den, int cfq, uint8_t *out, uint64_t cap, uint64_t *bytes,
-                     int threads)
+                     uint32_t den, int cfq, int search, uint8_t *out, uint64_t cap,
+                     uint64_t *bytes, int threads)
 {
     fmt_t F;
     int st = fmt_init(&F, dtype, N);
@@ -1344,7 +1420,7 @@ int oracle_encode_mt(const void *x, int dtype, uint64_t n, uint32_t N, int mode,
     for (int i = 0; i < T && !fail; ++i) {
         mt_job *J = &jobs[i];
         J->x = x; J->dtype = dtype; J->n = n; J->N = N; J->mode = mode;
-        J->num = num; J->den = den; J->cfq = cfq;
+        J->num = num; J->den = den; J->cfq = cfq; J->search = search;
         J->cap = maxp * (J->b1 - J->b0);
         /* the last block's fixed-rate budget may exceed B (minimum packet) */
         if (mode == MODE_FR && J->b1 == nb && nb) {
@@ -1469,7 +1545,8 @@ int oracle_profile_mt(const void *x, int dtype, uint64_t n, uint32_t N, const ui
     int rec = -1, ok_prefix = 1;
     for (int i = 0; i < ncand; ++i) {
         uint64_t bytes;
-        st = oracle_encode_mt(x, dtype, n, N, MODE_FQ, 1, 1, cand[i], buf, cap, &bytes, threads);
+        st = oracle_encode_mt(x, dtype, n, N, MODE_FQ, 1, 1, cand[i], SEARCH_BISECT, buf, cap,
+                              &bytes, threads);
         if (st) break;
         st = oracle_decode_mt(buf, bytes, y, dtype, n, threads);
         if (st) break;

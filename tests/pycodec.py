@@ -161,7 +161,53 @@ def budget(L, size, num, den, H):
     return max((L * size * den // (4 * num)) * 4, minpacket(L, H))
 
 
-def encode(x: np.ndarray, N: int, mode: int, num=1, den=1, code=0) -> bytes:
+LADDER_M = [0, 11, 21, 31, 41, 50, 59, 67, 75, 83, 90, 97, 104, 110, 116, 122]
+
+
+def ladder():
+    """Codes 128 k + M[f], k = 0..31, f = 0..15, then 4095, increasing."""
+    return sorted({128 * k + m for k in range(32) for m in LADDER_M}) + [4095]
+
+
+def predict_start(xb, dt, s, bud):
+    """PREDICT's start code on one block (None when code 0 fits): the excess
+    bits over the budget at code 0 against the bits predicted to go at
+    attenuation 2^-k, interpolated between two powers of two."""
+    W, H = INFO[dt][2], INFO[dt][4]
+    Eb = block_exp(xb) if INFO[dt][3] else 0
+    b0 = pkt_bits(streams(_padded_q(xb, dt, 0, Eb), W)[s], H)
+    if 4 * -(-b0 // 32) <= bud:
+        return None
+    e = exps(streams(_padded_q(xb, dt, 0, Eb), W)[s])
+    D = b0 - 8 * bud
+    red = [4 * sum(min(v, k) for v in e) for k in range(32)]
+    k1 = next((k for k in range(1, 32) if red[k] >= D), 31)
+    num, den = 16 * (D - red[k1 - 1]), red[k1] - red[k1 - 1]
+    f = 16 if den == 0 else -(-num // den)
+    f = min(max(f, 1), 16)
+    return 128 * (k1 - 1) + LADDER_M[f] if f < 16 else 128 * k1
+
+
+def predict_code(xb, dt, s, bud):
+    """PREDICT fixed-rate search on one block: code 0 if it fits, else up
+    the ladder from the predicted start until the packet fits."""
+    W, H = INFO[dt][2], INFO[dt][4]
+    Eb = block_exp(xb) if INFO[dt][3] else 0
+
+    def bits_at(cc):
+        return pkt_bits(streams(_padded_q(xb, dt, cc, Eb), W)[s], H)
+
+    c = predict_start(xb, dt, s, bud)
+    if c is None:
+        return 0
+    lad = ladder()
+    i = lad.index(c)
+    while lad[i] < 4095 and 4 * -(-bits_at(lad[i]) // 32) > bud:
+        i += 1
+    return lad[i]
+
+
+def encode(x: np.ndarray, N: int, mode: int, num=1, den=1, code=0, search=0) -> bytes:
     dt = x.dtype
     code_dt, size, W, Q, H = INFO[dt]
     x = list(x.reshape(-1).tolist())
@@ -180,6 +226,11 @@ def encode(x: np.ndarray, N: int, mode: int, num=1, den=1, code=0) -> bytes:
             plen = 4 * -(-pkt_bits(u, H) // 32)
         else:
             bud = budget(len(xb), size, num, den, H)
+            if search == 1:
+                c = predict_code(xb, dt, s, bud)
+                u = streams(_padded_q(xb, dt, c, Eb), W)[s]
+                packets.append(build_packet(u, s, c, Eb, H, bud))
+                continue
 
             def fits(cc):
                 uu = streams(_padded_q(xb, dt, cc, Eb), W)[s]

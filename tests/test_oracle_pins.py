@@ -347,6 +347,77 @@ def test_fixed_rate_search_vs_exhaustive():
             assert got == want and fits[got]
 
 
+def test_predict_ladder_table_exact():
+    """PREDICT's table M[f] = RNE(256 (1 - 2^(-f/16))), evaluated with 60
+    significant digits (no value is near a rounding tie)."""
+    from decimal import Decimal, getcontext
+    getcontext().prec = 60
+    ln2 = Decimal(2).ln()
+    for f, m in enumerate(P.LADDER_M):
+        v = Decimal(256) * (1 - (-(Decimal(f) / 16) * ln2).exp())
+        r = int(v.to_integral_value())
+        assert abs(v - r) != Decimal("0.5") and abs(v - m) < Decimal("0.5"), (f, v, m)
+        assert r == m
+    lad = P.ladder()
+    assert lad[0] == 0 and lad[-1] == 4095 and lad == sorted(set(lad)) and len(lad) == 32 * 16 + 1
+
+
+def test_fixed_rate_predict_vs_python_and_exhaustive():
+    """PREDICT on tiny blocks: the oracle's code equals the Python codec's,
+    the packet fits, and every ladder code from the predicted start up to
+    the chosen one fails (brute force over the ladder)."""
+    rng = np.random.default_rng(16)
+    N = 64
+    lad = P.ladder()
+    for trial in range(24):
+        dt = [np.int16, np.float32, np.int32, np.float64][trial % 4]
+        scale = float(np.exp(rng.uniform(0, 9)))
+        x = (np.cumsum(rng.standard_normal(N)) * scale).astype(dt)
+        if trial % 3 == 0:
+            x = (rng.standard_normal(N) * scale).astype(dt)
+        for s in range(3):
+            budget = int(rng.choice([12, 24, 40, 64, 100]))
+            got = O.fr_code(x, N, 0, s, budget, search=O.SEARCH_PREDICT)
+            assert got == P.predict_code(x.tolist(), np.dtype(dt), s, budget)
+            fits = lambda c: 4 * -(-O.packet_bits(x, N, 0, c, s) // 32) <= budget
+            assert fits(got)
+            if got and fits(0):
+                raise AssertionError("code 0 fits but PREDICT chose %d" % got)
+            start = P.predict_start(x.tolist(), np.dtype(dt), s, budget)
+            if start is None:
+                assert got == 0
+            else:
+                # the walk climbs the ladder from the start and stops at the
+                # first code that fits
+                assert got in lad and got >= start
+                assert not any(fits(c) for c in lad if start <= c < got)
+
+
+def test_fixed_rate_predict_containers():
+    """Whole fixed-rate containers with PREDICT: byte-identical to the
+    Python codec's, decodable, and of the closed-form size."""
+    rng = np.random.default_rng(18)
+    for trial in range(20):
+        dt = [np.int8, np.int16, np.int32, np.float32, np.float64][trial % 5]
+        N = int(rng.choice([64, 68, 128]))
+        n = int(rng.integers(1, 3 * N + 7))
+        if np.dtype(dt).kind == "i":
+            info = np.iinfo(dt)
+            x = np.clip(np.cumsum(rng.integers(-9, 10, n)) * (info.max // 300), info.min,
+                        info.max).astype(dt)
+        else:
+            x = (np.cumsum(rng.standard_normal(n)) * np.exp(rng.uniform(-9, 9))).astype(dt)
+        num, den = [(2, 1), (3, 1), (4, 1), (6, 1)][trial % 4]
+        try:
+            size = O.encoded_size(dt, n, N, O.MODE_FR, num, den)
+        except O.OracleError:
+            continue
+        c = O.encode(x, N, O.MODE_FR, num, den, search=O.SEARCH_PREDICT)
+        assert len(c) == size
+        assert c == P.encode(x, N, O.MODE_FR, num, den, search=1)
+        O.decode(c, dt, n)
+
+
 def test_stream_decision_one_block_lag():
     """Sec. 6: the best-stream decision of block j is carried by block j+1."""
     N = 64
