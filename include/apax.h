@@ -64,6 +64,20 @@ enum {
     APAX_ERR_TIMEOUT = -10     /* a bounded device wait expired (offset scan) */
 };
 
+/* Fixed-rate search policies (Sec. 6 adaptive loop: the attenuation of each
+ * block is adjusted until its packet meets the rate).  The policy is the
+ * encoder's: it is not stored in the stream, and any decoder reads either.
+ *   APAX_SEARCH_BISECT   code 0 if it fits, else bisection of [0, 4095]
+ *                        keeping the upper end fitting (13 packet sizings).
+ *   APAX_SEARCH_PREDICT  code 0 if it fits, else a start code predicted from
+ *                        the code-0 exponents (the bits an attenuation of
+ *                        2^-k removes from each group, interpolated in 1/16
+ *                        octave steps), then up the ladder of codes
+ *                        128 k + M[f] until the packet fits (usually 1-3
+ *                        sizings).  The codes, and so the bytes, differ
+ *                        from BISECT's. */
+typedef enum { APAX_SEARCH_BISECT = 0, APAX_SEARCH_PREDICT = 1 } apax_search;
+
 /* Encoding parameters.
  *   block_size  N, 64..16384, multiple of 4 (Sec. 6).  256 is the default.
  *   mode        APAX_FIXED_RATE or APAX_FIXED_QUALITY.
@@ -72,6 +86,8 @@ enum {
  *   atten_code  fixed-quality attenuation code c in 0..4095: k = c >> 7,
  *               m = c & 127, a(c) = (256 - m) 2^-(8+k); 4095 zeroes the data;
  *               0 is lossless for integer types.
+ *   search      fixed-rate search policy (apax_search; ignored for fixed
+ *               quality); other values give APAX_ERR_INVALID_ARG.
  */
 typedef struct {
     uint32_t block_size;
@@ -79,7 +95,7 @@ typedef struct {
     uint32_t rate_num;
     uint32_t rate_den;
     uint32_t atten_code;
-    uint32_t reserved;
+    uint32_t search;
 } apax_params;
 
 /* Completion record written by the device when a call's work finishes:

@@ -37,7 +37,7 @@ class ApaxError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("block_size", ctypes.c_uint32), ("mode", ctypes.c_int32),
                 ("rate_num", ctypes.c_uint32), ("rate_den", ctypes.c_uint32),
-                ("atten_code", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("atten_code", ctypes.c_uint32), ("search", ctypes.c_uint32)]
 
 
 class Point(ctypes.Structure):
@@ -212,8 +212,12 @@ def _dtype_code(t: torch.Tensor) -> int:
         raise ApaxError(-3, f"unsupported dtype {t.dtype}") from None
 
 
-def params(block_size: int = 256, mode: int = FIXED_QUALITY, rate=(4, 1), code: int = 0) -> Params:
-    return Params(block_size, mode, rate[0], rate[1], code, 0)
+SEARCH_BISECT, SEARCH_PREDICT = 0, 1
+
+
+def params(block_size: int = 256, mode: int = FIXED_QUALITY, rate=(4, 1), code: int = 0,
+           search: int = SEARCH_BISECT) -> Params:
+    return Params(block_size, mode, rate[0], rate[1], code, search)
 
 
 def encoded_size(dtype_code: int, n: int, p: Params) -> int:
@@ -276,10 +280,10 @@ def encode_into(x: torch.Tensor, p: Params, out: torch.Tensor, workspace: torch.
 
 
 def encode(x: torch.Tensor, block_size: int = 256, mode: int = FIXED_QUALITY, rate=(4, 1),
-           code: int = 0, stream=None) -> torch.Tensor:
+           code: int = 0, stream=None, search: int = SEARCH_BISECT) -> torch.Tensor:
     """Encode x (device tensor); returns the container as a uint8 tensor."""
     assert x.is_cuda and x.is_contiguous()
-    p = params(block_size, mode, rate, code)
+    p = params(block_size, mode, rate, code, search)
     dc = _dtype_code(x)
     cap = encoded_size(dc, x.numel(), p)
     out = torch.empty(cap, dtype=torch.uint8, device=x.device)

@@ -5,7 +5,7 @@
 //   1. decides its stream from the predecessor block at code 0 (the
 //      one-block lag of Sec. 6: block j+1 carries block j's best stream),
 //   2. picks the attenuation code (fixed quality: given; fixed rate: the
-//      BISECT search against the block budget),
+//      BISECT or PREDICT search against the block budget),
 //   3. writes exponents, JEE tokens and mantissas into a shared-memory
 //      packet image, which is then copied out with coalesced word stores.
 // Fixed-rate packets land at j*B.  Fixed-quality packet offsets come from a
@@ -65,6 +65,62 @@ __device__ __forceinline__ uint64_t wait_tile(unsigned long long *tiles, uint64_
 }
 
 __device__ __forceinline__ uint32_t pad32_bytes(uint32_t bits) { return 4u * ((bits + 31u) >> 5); }
+
+// ---------------------------------------------------------------- PREDICT search
+// The ladder of the PREDICT fixed-rate search: codes 128 k + M[f] with
+// M[f] = RNE(256 (1 - 2^(-f/16))), so that a(128 k + M[f]) is 2^-(k + f/16)
+// on the attenuator's grid; 4095 follows the last rung.
+__device__ __forceinline__ int ladder_m(int f)
+{
+    // M[0..15] = 0 11 21 31 41 50 59 67 | 75 83 90 97 104 110 116 122, a byte each
+    const uint64_t lo = 0x433B32291F150B00ull, hi = 0x7A746E68615A534Bull;
+    return (int)(((f < 8 ? lo >> (8 * f) : hi >> (8 * (f - 8)))) & 0xffu);
+}
+
+__device__ __forceinline__ int ladder_next(int c)
+{
+    const int k = c >> 7, m = c & 127;
+#pragma unroll 1
+    for (int f = 0; f < 16; ++f)
+        if (ladder_m(f) > m) return 128 * k + ladder_m(f);
+    return k < 31 ? 128 * (k + 1) : 4095;
+}
+
+// Start code of the PREDICT search: D = packet bits at code 0 minus the
+// budget's bits; red(k) = 4 sum_g min(e_g, k) are the bits an attenuation of
+// 2^-k is predicted to remove; k1 = the least k in 1..31 with red(k) >= D
+// (31 if none); f = ceil(16 (D - red(k1-1)) / (red(k1) - red(k1-1)))
+// clamped to 1..16 (16 for a zero denominator); start = 128 (k1-1) + M[f]
+// for f < 16, else 128 k1.  rprev = red(k1-1), rk = red(k1).
+__device__ __forceinline__ int predict_from_red(int D, int k1, int rprev, int rk)
+{
+    const int num = 16 * (D - rprev), den = rk - rprev;
+    int f = 16;
+    if (den != 0) {
+        f = num / den;  // truncation toward zero, then the ceiling
+        if (f * den < num) ++f;
+    }
+    f = f < 1 ? 1 : (f > 16 ? 16 : f);
+    return f < 16 ? 128 * (k1 - 1) + ladder_m(f) : 128 * k1;
+}
+
+// The start for one thread: red(k) = red(k-1) + 4 cnt_ge(k), where
+// cnt_ge(k) = #{g : e_g >= k}.
+template <class CntGe>
+__device__ __forceinline__ int predict_start(int D, CntGe &&cnt_ge)
+{
+    int rprev = 0, rk = 0, k1 = 31;
+#pragma unroll 1
+    for (int k = 1; k <= 31; ++k) {
+        rk = rprev + 4 * cnt_ge(k);
+        if (rk >= D) {
+            k1 = k;
+            break;
+        }
+        if (k < 31) rprev = rk;
+    }
+    return predict_from_red(D, k1, rprev, rk);
+}
 
 template <int DT>
 __device__ __forceinline__ uint32_t min_packet(int L)
@@ -298,22 +354,58 @@ __device__ __forceinline__ void encode_tile(const EncArgs &a, uint64_t tile, uin
     uint32_t plen = 0;
     if (MODE == 0) {
         const uint32_t budget = b.L == (int)a.N ? a.B : fr_budget<DT>(b.L, a.rate_num, a.rate_den);
-        const bool fits0 = pad32_bytes(team_eval1<DT, TS>(b, 0, s)) <= budget;
-        int lo = 0, hi = 4095;
-        // Teams of one warp share shuffles, so every team runs the same 12
-        // halvings unless all of them already fit at code 0.
-        if (!__all_sync(kFull, fits0)) {
+        if (a.search == APAX_SEARCH_PREDICT) {
+            // the code-0 exponents of stream s into ebuf, the packet bits
+            const uint32_t bits0 = team_exps<DT, TS>(b, s, ebuf);
+            __syncwarp();
+            const bool fits0 = pad32_bytes(bits0) <= budget;
+            // every team of the warp steps through the same loops (their
+            // shuffles are shared); a team that is done follows along
+            const int D = (int)bits0 - 8 * (int)budget;
+            const int ge = b.active ? b.g1 : b.g0;
+            // red(k) for k = 1, 2, ... until every team of the warp has its k1
+            int rprev = 0, rk = 0, k1 = 0;
 #pragma unroll 1
-            for (int it = 0; it < 12; ++it) {  // at most 12 halvings close [0, 4095]
-                const int mid = (lo + hi) >> 1;
-                const uint32_t bm = team_eval1<DT, TS>(b, mid, s);
-                if (hi - lo > 1) {
-                    if (pad32_bytes(bm) <= budget) hi = mid;
-                    else lo = mid;
+            for (int k = 1; k <= 31 && __any_sync(kFull, !fits0 && k1 == 0); ++k) {
+                int cnt = 0;
+                for (int g = b.g0; g < ge; ++g) cnt += ebuf[g] >= k;
+                cnt = team_sum<TS>(cnt);
+                if (k1 == 0) {
+                    rk = rprev + 4 * cnt;
+                    if (rk >= D) k1 = k;
+                    else if (k < 31) rprev = rk;
                 }
             }
+            int c = predict_from_red(D, k1 ? k1 : 31, rprev, rk);
+            bool need = !fits0 && c < 4095;
+#pragma unroll 1
+            while (__any_sync(kFull, need)) {
+                const uint32_t bm = team_eval1<DT, TS>(b, need ? c : 0, s);
+                if (need) {
+                    if (pad32_bytes(bm) <= budget) need = false;
+                    else c = ladder_next(c);
+                    need = need && c < 4095;
+                }
+            }
+            code = fits0 ? 0 : c;
+        } else {
+            const bool fits0 = pad32_bytes(team_eval1<DT, TS>(b, 0, s)) <= budget;
+            int lo = 0, hi = 4095;
+            // Teams of one warp share shuffles, so every team runs the same 12
+            // halvings unless all of them already fit at code 0.
+            if (!__all_sync(kFull, fits0)) {
+#pragma unroll 1
+                for (int it = 0; it < 12; ++it) {  // at most 12 halvings close [0, 4095]
+                    const int mid = (lo + hi) >> 1;
+                    const uint32_t bm = team_eval1<DT, TS>(b, mid, s);
+                    if (hi - lo > 1) {
+                        if (pad32_bytes(bm) <= budget) hi = mid;
+                        else lo = mid;
+                    }
+                }
+            }
+            code = fits0 ? 0 : hi;
         }
-        code = fits0 ? 0 : hi;
         plen = budget;
     }
 
@@ -485,6 +577,36 @@ __device__ __forceinline__ bool fits_t1(const TBlock<DT> &b, int code, int s, ui
     return pad32_bytes((uint32_t)H + 4u * (uint32_t)nib + 4u * (uint32_t)sume) <= budget;
 }
 
+// Exponents of block b at code 0 on stream s into the column eb (stride
+// nt), and the unpadded packet bits (one thread owns the block).
+template <int DT>
+__device__ __forceinline__ uint32_t exps_t1(const TBlock<DT> &b, int s, uint8_t *eb, int nt)
+{
+    constexpr int H = DT_<DT>::H;
+    const Quant<DT> Q(0, b.Eb);
+    int nib = 0, sume = 0, e_last = 0;
+    bool st = false;
+    with_quant<DT>(Q, [&](const auto &qf) {
+        Stream1 sm(s, carry_in<DT>(b, qf, 0));
+#pragma unroll 1
+        for (int g = 0; g < b.G; ++g) {
+            typename LaneT<DT>::t xv[4];
+            load4<DT, true>(b, 4 * g, xv);
+            int32_t u[4];
+            const int e = exp_from_or(group1<DT>(qf, xv, sm, u));
+            eb[(size_t)g * nt] = (uint8_t)e;
+            const int d = e - e_last;
+            const bool small = (unsigned)(d + 1) <= 2u;
+            const int inc = small ? (st ? 0 : 1) : ((unsigned)(d + 2) <= 4u ? 1 : 2);
+            nib += g == 0 ? 2 : inc;
+            st = g != 0 && small && !st;
+            sume += e;
+            e_last = e;
+        }
+    });
+    return (uint32_t)H + 4u * (uint32_t)nib + 4u * (uint32_t)sume;
+}
+
 // ---------------------------------------------------------------- block per thread
 // Fixed rate, a tile of blockDim.x blocks, one per thread (block sizes up to
 // kT1MaxBlock): the team functions run with a team of one, exponents sit in
@@ -517,19 +639,34 @@ __device__ __forceinline__ void encode_tile_t1(const EncArgs &a, uint64_t tile, 
     TBlock<DT> b;
     open_team_block<DT, 1>(b, x, a.n, a.N, a.nb, j, a.gp);
     if (b.active && b.bad) set_status(a.status, -8);
-    // BISECT against the block budget (Sec. 6 adaptive loop)
+    // the search against the block budget (Sec. 6 adaptive loop)
     const uint32_t budget = b.L == (int)a.N ? a.B : fr_budget<DT>(b.L, a.rate_num, a.rate_den);
-    const bool fits0 = fits_t1<DT>(b, 0, s, budget);
-    int lo = 0, hi = 4095;
-    if (!fits0) {
-#pragma unroll 1
-        for (int it = 0; it < 12 && hi - lo > 1; ++it) {  // 12 halvings close [0, 4095]
-            const int mid = (lo + hi) >> 1;
-            if (fits_t1<DT>(b, mid, s, budget)) hi = mid;
-            else lo = mid;
+    int code = 0;
+    if (a.search == APAX_SEARCH_PREDICT) {
+        // the code-0 exponents of stream s into the column, the packet bits
+        const uint32_t bits0 = exps_t1<DT>(b, s, eb, nt);
+        if (pad32_bytes(bits0) > budget) {
+            int c = predict_start((int)bits0 - 8 * (int)budget, [&](int k) {
+                int cnt = 0;
+                for (int g = 0; g < b.G; ++g) cnt += eb[(size_t)g * nt] >= k;
+                return cnt;
+            });
+            while (c < 4095 && !fits_t1<DT>(b, c, s, budget)) c = ladder_next(c);
+            code = c;
         }
+    } else {
+        const bool fits0 = fits_t1<DT>(b, 0, s, budget);
+        int lo = 0, hi = 4095;
+        if (!fits0) {
+#pragma unroll 1
+            for (int it = 0; it < 12 && hi - lo > 1; ++it) {  // 12 halvings close [0, 4095]
+                const int mid = (lo + hi) >> 1;
+                if (fits_t1<DT>(b, mid, s, budget)) hi = mid;
+                else lo = mid;
+            }
+        }
+        code = fits0 ? 0 : hi;
     }
-    const int code = fits0 ? 0 : hi;
     const uint32_t plen = budget;
     // final pass: exponents into the column
     const Quant<DT> Q(code, b.Eb);

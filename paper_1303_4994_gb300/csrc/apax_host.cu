@@ -53,6 +53,7 @@ int fill_enc_args(const void *x, int dtype, uint64_t n, const apax_params *p,
     if (p->mode == APAX_FIXED_RATE) {
         a.rate_num = p->rate_num;
         a.rate_den = p->rate_den;
+        a.search = (int)p->search;
         a.B = (uint32_t)B;
         uint64_t total;
         apax_encoded_size(dtype, n, p, &total);

@@ -77,6 +77,7 @@ struct EncArgs {
     const uint32_t *code_dev;  // if set: code read on the device
     uint32_t B;         // fixed-rate budget of a full block
     uint32_t rate_num, rate_den;
+    int search;         // fixed-rate search policy (APAX_SEARCH_*)
     uint64_t fr_payload; // fixed-rate payload bytes (exact, host computed)
     uint8_t *out;
     uint64_t cap;

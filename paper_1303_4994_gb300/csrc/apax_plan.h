@@ -53,6 +53,7 @@ inline int check(int dtype, const apax_params *p, Fmt &f)
     int st = fmt_of(dtype, f);
     if (st) return st;
     if (!block_size_ok(p->block_size)) return APAX_ERR_BLOCK_SIZE;
+    if (p->search > APAX_SEARCH_PREDICT) return APAX_ERR_INVALID_ARG;
     if (p->mode == APAX_FIXED_RATE) {
         if (p->rate_num == 0 || p->rate_den == 0) return APAX_ERR_RATE;
         uint64_t B = ((uint64_t)p->block_size * f.size * p->rate_den / (4ull * p->rate_num)) * 4;

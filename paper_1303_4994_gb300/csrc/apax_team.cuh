@@ -593,6 +593,31 @@ __device__ __forceinline__ uint32_t team_eval1(const TBlock<DT> &b, int code, in
     return (uint32_t)DT_<DT>::H + 4u * (uint32_t)nib + 4u * (uint32_t)sume;
 }
 
+// team_eval1 at code 0 that also leaves each group's exponent in ebuf[g]
+// (this thread's groups; the team's groups together).
+template <int DT, int TS>
+__device__ __forceinline__ uint32_t team_exps(const TBlock<DT> &b, int s, uint8_t *ebuf)
+{
+    const Quant<DT> Q(0, b.Eb);
+    TokCount tc;
+    tc.init();
+    with_quant<DT>(Q, [&](const auto &qf) {
+        Stream1 st(s, carry_in<DT>(b, qf, 4 * b.g0));
+#pragma unroll 1
+        for (int g = b.g0; g < b.g1; ++g) {
+            typename LaneT<DT>::t xv[4];
+            load4<DT, true>(b, 4 * g, xv);
+            int32_t u[4];
+            const int e = exp_from_or(group1<DT>(qf, xv, st, u));
+            ebuf[g] = (uint8_t)e;
+            tc.push(e, true);
+        }
+    });
+    int nib, sume;
+    team_tokens<TS>(tc, b.g0 == 0, nib, sume);
+    return (uint32_t)DT_<DT>::H + 4u * (uint32_t)nib + 4u * (uint32_t)sume;
+}
+
 // ---------------------------------------------------------------- staging
 // Bulk (TMA) copies global -> shared memory completed on an mbarrier, in
 // inline PTX.

@@ -72,6 +72,11 @@ def test_argument_errors(lib):
     with pytest.raises(A.ApaxError) as e:
         A.encoded_size(4, 1000, A.params(256, A.FIXED_QUALITY, (1, 1), 5000))
     assert e.value.status == -1
+    with pytest.raises(A.ApaxError) as e:  # no third fixed-rate search policy
+        A.encoded_size(2, 1000, A.params(256, A.FIXED_RATE, (4, 1), 0, search=2))
+    assert e.value.status == -1
+    assert A.encoded_size(2, 1000, A.params(256, A.FIXED_RATE, (4, 1), 0, A.SEARCH_PREDICT)) == \
+        A.encoded_size(2, 1000, A.params(256, A.FIXED_RATE, (4, 1), 0, A.SEARCH_BISECT))
     assert lib.apax_status_string(-9) == b"corrupt stream"
     # fixed-rate size of the int16 sensor workload at 4:1
     assert A.encoded_size(2, 262144, A.params(256, A.FIXED_RATE, (4, 1))) == 131112

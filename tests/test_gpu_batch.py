@@ -50,6 +50,8 @@ def _mixed_batch(seed, count, big_blocks=False):
                 p = A.params(N, A.FIXED_QUALITY, (1, 1), int(rng.integers(0, 4096)))
         else:
             p = A.params(N, A.FIXED_QUALITY, (1, 1), int(rng.choice([0, 256, 777, 2048, 4095])))
+        if p.mode == A.FIXED_RATE and i % 3 == 0:
+            p.search = A.SEARCH_PREDICT  # both fixed-rate policies in one batch
         arrays.append(_array(rng, dt, n))
         ps.append(p)
     return arrays, ps
@@ -68,8 +70,8 @@ def _setup(arrays, ps):
 
 
 def _want(arrays, ps):
-    return [O.encode(a, p.block_size, p.mode, p.rate_num, p.rate_den, p.atten_code)
-            for a, p in zip(arrays, ps)]
+    return [O.encode(a, p.block_size, p.mode, p.rate_num, p.rate_den, p.atten_code,
+                     search=p.search) for a, p in zip(arrays, ps)]
 
 
 def _check(outs, results, want):

@@ -103,6 +103,43 @@ def test_parity_small_all_types(dt, mode):
                     _roundtrip(x, N, 0, rate, 0)
 
 
+def _roundtrip_predict(x, N, rate):
+    n = x.size
+    want = O.encode(x, N, O.MODE_FR, rate[0], rate[1], 0, threads=0, search=O.SEARCH_PREDICT)
+    xt = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    got = A.encode(xt, N, A.FIXED_RATE, rate, 0, search=A.SEARCH_PREDICT)
+    gb = got.cpu().numpy().tobytes()
+    assert gb == want, (x.dtype, N, rate, n)
+    y = A.decode(got, TT[O.DTYPE_CODE[x.dtype]], n).cpu().numpy()
+    np.testing.assert_array_equal(_bits(y), _bits(O.decode(want, x.dtype, n)))
+
+
+@pytest.mark.parametrize("dt", [1, 2, 3, 4, 5])
+def test_parity_fixed_rate_predict(dt):
+    # the PREDICT search: teams of 32 (small arrays), teams of 8 and block
+    # sizes above 1024, all five types, rates that make most blocks search
+    rng = np.random.default_rng(90 + dt)
+    for N, n in ((256, 256 * 37 + 13), (64, 64 * 5000 + 3), (2048, 2048 * 40 + 7), (1000, 1000 * 9)):
+        for kind in (0, 1, 2) if dt >= 4 else (0, 1):
+            x = _data(dt, n, rng, kind)
+            for rate in ((2, 1), (4, 1), (6, 1), (5, 2)):
+                try:
+                    O.encoded_size(x.dtype, n, N, 0, rate[0], rate[1])
+                except O.OracleError:
+                    continue
+                _roundtrip_predict(x, N, rate)
+
+
+def test_parity_fixed_rate_predict_block_per_thread():
+    # 40,000 blocks: the one-block-per-thread encoder runs the search
+    rng = np.random.default_rng(95)
+    for dt in (2, 4):
+        x = _data(dt, 256 * 40000 - 5, rng, 1)
+        _roundtrip_predict(x, 256, (4, 1))
+    x = synth.sensor_trace(64 * 40000, seed=3)
+    _roundtrip_predict(x, 64, (4, 1))
+
+
 @pytest.mark.parametrize("dt", [2, 4, 5])
 @pytest.mark.parametrize("N", [64, 68, 1000, 4096, 16384])
 def test_parity_block_sizes(dt, N):
