@@ -225,6 +225,60 @@ int apax_profile_from_host(const void *x_host, void *x_dev, int dtype, uint64_t 
  * order. */
 void apax_derived_metrics(const apax_profile_point *pt, uint64_t n, double *out /* host */);
 
+/* ---------------------------------------------------------------- shards
+ * One array split over several devices (Sec. 6: every block is coded on its
+ * own; only the best-stream decision looks at the block before).  A shard is
+ * a contiguous range of blocks [block_begin, block_end).  Its container is
+ * an ordinary container of the sub-array of those blocks' elements, so it
+ * decodes on its own with apax_decode; its packets are exactly the
+ * whole-array packets of those blocks because the first block's stream
+ * decision reads the block before the range (the halo).  The shards of one
+ * array merge into the whole-array container with apax_merge_shards (one
+ * device), or stay distributed: fixed rate needs no exchange (packet j sits
+ * at j*B); fixed quality needs the payload word counts of the shards before
+ * it (an exclusive scan of one number per shard), which apax_shard_rebase
+ * adds to a shard's offset-table slice. */
+
+/* Elements of the sub-array of blocks [block_begin, block_end) of an array
+ * of n elements (host call). */
+int apax_shard_elements(uint64_t n, uint32_t block_size, uint64_t block_begin, uint64_t block_end,
+                        uint64_t *elements /* host */);
+
+/* Encode blocks [block_begin, block_end) of an array of n elements.  x
+ * (device) holds the shard's elements preceded by the whole halo block
+ * block_begin - 1 when block_begin > 0: x points at element
+ * (block_begin - 1) * N, or at element 0 for the first shard.  out receives
+ * the sub-array's container (apax_encoded_size / apax_workspace_size of
+ * apax_shard_elements() elements give its capacity and workspace); res its
+ * status and size.  Errors as apax_encode; a range outside the array is
+ * APAX_ERR_INVALID_ARG. */
+int apax_encode_shard(const void *x, int dtype, uint64_t n, const apax_params *p,
+                      uint64_t block_begin, uint64_t block_end, void *out, uint64_t out_capacity,
+                      void *workspace, uint64_t workspace_bytes, apax_result *res, void *stream);
+
+/* Adds add_words to the block_count offset-table entries of a fixed-quality
+ * shard container (device), in place on the stream: its packets then sit at
+ * their word offsets in the whole array's payload, add_words being the
+ * payload words of all earlier shards. */
+int apax_shard_rebase(void *container, uint64_t block_count, uint64_t add_words, void *stream);
+
+/* One shard's container: device pointer, its byte count (apax_result.bytes
+ * of its encode) and its block range. */
+typedef struct {
+    const void *container;
+    uint64_t bytes;
+    uint64_t block_begin, block_end;
+} apax_shard;
+
+/* Merge the containers of count shards that tile the blocks of an array of
+ * n elements, in block order (host array of descriptors, containers on this
+ * device, not yet rebased), into out: the container apax_encode writes for
+ * the whole array, byte for byte.  Asynchronous on the stream (kernels and
+ * device-to-device copies); res receives the status and size. */
+int apax_merge_shards(const apax_shard *shards, int count, int dtype, uint64_t n,
+                      const apax_params *p, void *out, uint64_t out_capacity, apax_result *res,
+                      void *stream);
+
 /* Encode without any allocation (no counterpart in the paper: this entry
  * exists for callers that cannot allocate device memory at all -- code
  * running inside another runtime's allocator or memory-pool hook, paths that

@@ -99,6 +99,11 @@ class ServerStats(ctypes.Structure):
                                                 "undelivered")]
 
 
+class Shard(ctypes.Structure):
+    _fields_ = [("container", ctypes.c_void_p), ("bytes", ctypes.c_uint64),
+                ("block_begin", ctypes.c_uint64), ("block_end", ctypes.c_uint64)]
+
+
 class BatchConfig(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32)]
 
@@ -119,7 +124,8 @@ EXPORTS = ("apax_encoded_size", "apax_workspace_size", "apax_encode", "apax_enco
            "apax_batch_tiles", "apax_batch_destroy", "apax_batch_decode_workspace_size",
            "apax_batch_decode_create", "apax_batch_profile_workspace_size",
            "apax_batch_profile_create", "apax_server_create", "apax_server_submit",
-           "apax_server_poll", "apax_server_release", "apax_server_stats", "apax_server_destroy")
+           "apax_server_poll", "apax_server_release", "apax_server_stats", "apax_server_destroy",
+           "apax_shard_elements", "apax_encode_shard", "apax_shard_rebase", "apax_merge_shards")
 OP_ENCODE, OP_DECODE = 0, 1
 NOALLOC_SCRATCH_BYTES = 256 << 10
 
@@ -175,6 +181,10 @@ def lib():
         L.apax_server_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
         L.apax_server_destroy.argtypes = [vp]
         L.apax_server_destroy.restype = None
+        L.apax_shard_elements.argtypes = [u64, u32, u64, u64, p64]
+        L.apax_encode_shard.argtypes = [vp, i32, u64, pP, u64, u64, vp, u64, vp, u64, vp, vp]
+        L.apax_shard_rebase.argtypes = [vp, u64, u64, vp]
+        L.apax_merge_shards.argtypes = [ctypes.POINTER(Shard), i32, i32, u64, pP, vp, u64, vp, vp]
         L.apax_status_string.argtypes = [i32]
         L.apax_status_string.restype = ctypes.c_char_p
         L.apax_build_info.argtypes = []
@@ -661,3 +671,52 @@ def derived(point: Point, n: int) -> dict:
 
 def build_info() -> str:
     return lib().apax_build_info().decode()
+
+
+# ---------------------------------------------------------------- shards
+def shard_elements(n: int, block_size: int, b0: int, b1: int) -> int:
+    out = ctypes.c_uint64()
+    _check(lib().apax_shard_elements(n, block_size, b0, b1, ctypes.byref(out)), "shard_elements")
+    return out.value
+
+
+def encode_shard(x_halo: torch.Tensor, n: int, p: Params, b0: int, b1: int,
+                 stream=None) -> torch.Tensor:
+    """Encode blocks [b0, b1) of an array of n elements; x_halo holds those
+    blocks' elements preceded by the whole block b0 - 1 when b0 > 0.  Returns
+    the shard's container (a container of the sub-array)."""
+    assert x_halo.is_cuda and x_halo.is_contiguous()
+    dc = _dtype_code(x_halo)
+    ns = shard_elements(n, p.block_size, b0, b1)
+    cap = encoded_size(dc, ns, p)
+    out = torch.empty(cap, dtype=torch.uint8, device=x_halo.device)
+    ws = torch.empty(workspace_size(dc, ns, p), dtype=torch.uint8, device=x_halo.device)
+    res = new_result(x_halo.device)
+    _check(lib().apax_encode_shard(x_halo.data_ptr(), dc, n, ctypes.byref(p), b0, b1,
+                                   out.data_ptr(), cap, ws.data_ptr(), ws.numel(), res.data_ptr(),
+                                   _stream(stream)), "encode_shard")
+    r = read_result(res)
+    _check(r.status, "encode_shard (device)")
+    return out[:r.bytes]
+
+
+def shard_rebase(container: torch.Tensor, blocks: int, add_words: int, stream=None):
+    _check(lib().apax_shard_rebase(container.data_ptr(), blocks, add_words, _stream(stream)),
+           "shard_rebase")
+
+
+def merge_shards(containers, ranges, dtype_code: int, n: int, p: Params, stream=None) -> torch.Tensor:
+    """The whole-array container from shard containers (device tensors) of
+    the block ranges `ranges`, in order."""
+    k = len(containers)
+    arr = (Shard * k)(*[Shard(c.data_ptr(), c.numel(), b0, b1)
+                        for c, (b0, b1) in zip(containers, ranges)])
+    cap = encoded_size(dtype_code, n, p)
+    dev = containers[0].device
+    out = torch.empty(cap, dtype=torch.uint8, device=dev)
+    res = new_result(dev)
+    _check(lib().apax_merge_shards(arr, k, dtype_code, n, ctypes.byref(p), out.data_ptr(), cap,
+                                   res.data_ptr(), _stream(stream)), "merge_shards")
+    r = read_result(res)
+    _check(r.status, "merge_shards (device)")
+    return out[:r.bytes]

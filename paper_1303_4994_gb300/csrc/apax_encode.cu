@@ -41,7 +41,7 @@ __device__ void write_container_header(const EncArgs &a, int code)
     put_le(h + 12, a.mode == 1 ? (uint64_t)code : 0, 2);
     put_le(h + 14, 0, 2);
     put_le(h + 16, a.mode == 0 ? a.B : 0, 4);
-    put_le(h + 20, a.n, 8);
+    put_le(h + 20, a.n_hdr, 8);
     put_le(h + 36, 0, 4);
 }
 
@@ -315,7 +315,9 @@ __device__ __forceinline__ void encode_tile(const EncArgs &a, uint64_t tile, uin
     const int nteams = blockDim.x / TS;
     const int gp = a.gp;
 
-    const uint64_t j = tile * (uint64_t)nteams + (uint64_t)team;
+    // block j of the array; jl = j - jb0 its place in this container
+    const uint64_t j = a.jb0 + tile * (uint64_t)nteams + (uint64_t)team;
+    const uint64_t jl = j - a.jb0, nbl = a.nb - a.jb0;
     int code = (int)a.code;
     if (a.code_dev) code = (int)*a.code_dev;
     uint32_t *pkt = smem + (size_t)team * (a.pkt_words + a.ebuf_words);
@@ -328,7 +330,7 @@ __device__ __forceinline__ void encode_tile(const EncArgs &a, uint64_t tile, uin
     uint64_t base = 0;
     if (a.stage_off) {
         raw *xs = reinterpret_cast<raw *>(reinterpret_cast<uint8_t *>(smem) + a.stage_off);
-        const uint64_t jb0 = tile * (uint64_t)nteams;
+        const uint64_t jb0 = a.jb0 + tile * (uint64_t)nteams;
         base = jb0 ? jb0 - 1 : 0;
         const uint64_t bend = min(jb0 + (uint64_t)nteams, a.nb);
         if (stage_blocks<DT>(xs, x, a.n, a.N, base, bend > base ? bend : base, a.status, a.spin_limit))
@@ -491,7 +493,7 @@ __device__ __forceinline__ void encode_tile(const EncArgs &a, uint64_t tile, uin
         __syncthreads();
         off_words = s_base + s_words[team];
     } else {
-        off_words = j * (uint64_t)(a.B >> 2);
+        off_words = jl * (uint64_t)(a.B >> 2);
     }
 
     if (b.active) {
@@ -500,8 +502,8 @@ __device__ __forceinline__ void encode_tile(const EncArgs &a, uint64_t tile, uin
             if (off_words > 0xffffffffull) {
                 set_status(a.status, -6);
             } else {
-                reinterpret_cast<uint32_t *>(a.out + 40)[j] = (uint32_t)off_words;
-                if (j == a.nb - 1 && (a.nb & 1)) reinterpret_cast<uint32_t *>(a.out + 40)[j + 1] = 0;
+                reinterpret_cast<uint32_t *>(a.out + 40)[jl] = (uint32_t)off_words;
+                if (jl == nbl - 1 && (nbl & 1)) reinterpret_cast<uint32_t *>(a.out + 40)[jl + 1] = 0;
             }
         }
         if (start + 4ull * words > a.cap) {
@@ -621,7 +623,7 @@ __device__ __forceinline__ void encode_tile_t1(const EncArgs &a, uint64_t tile, 
     using lt = typename LaneT<DT>::t;
     constexpr int H = T::H;
     const int tid = threadIdx.x, nt = blockDim.x;
-    const uint64_t j = tile * (uint64_t)nt + (uint64_t)tid;
+    const uint64_t j = a.jb0 + tile * (uint64_t)nt + (uint64_t)tid;  // block of the array
     uint8_t *eb = smem + tid;  // exponent of group g at eb[g * nt]
     if (tile == 0 && tid == 0) write_container_header(a, 0);
     const raw *x = reinterpret_cast<const raw *>(a.x);
@@ -682,7 +684,7 @@ __device__ __forceinline__ void encode_tile_t1(const EncArgs &a, uint64_t tile, 
     });
     const uint32_t words = b.active ? plen >> 2 : 0;
     if (b.active) {
-        const uint64_t start = a.poff + (uint64_t)j * a.B;
+        const uint64_t start = a.poff + (j - a.jb0) * a.B;
         if (start + 4ull * words > a.cap) {
             set_status(a.status, -5);
         } else {
@@ -883,6 +885,48 @@ cudaError_t launch_encode(const EncArgs &a, int ts, int threads, size_t smem, cu
     case 4: return launch_dt<4>(a, ts, threads, smem, s);
     default: return launch_dt<5>(a, ts, threads, smem, s);
     }
+}
+
+
+// ---------------------------------------------------------------- shards
+// One container from the containers of contiguous block ranges (shards):
+// each shard's offset table slice moves to its place with its payload's word
+// offset added; the header names the whole array.
+namespace {
+__global__ void k_table_rebase(const uint32_t *src, uint32_t *dst, uint64_t count, uint64_t add)
+{
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        dst[i] = (uint32_t)((uint64_t)src[i] + add);  // the host checked the 2^32-word limit
+}
+
+__global__ void k_merged_header(EncArgs a, uint64_t payload)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        write_container_header(a, (int)a.code);
+        put_le(a.out + 28, payload, 8);
+        if (a.res) {
+            a.res->bytes = a.poff + payload;
+            a.res->status = 0;
+        }
+    }
+}
+}  // namespace
+
+cudaError_t launch_table_rebase(const uint32_t *src, uint32_t *dst, uint64_t count, uint64_t add,
+                                cudaStream_t s)
+{
+    if (count) {
+        const uint64_t g = (count + 255) / 256;
+        k_table_rebase<<<(unsigned)(g < 4096 ? g : 4096), 256, 0, s>>>(src, dst, count, add);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_merged_header(const EncArgs &a, uint64_t payload, cudaStream_t s)
+{
+    k_merged_header<<<1, 32, 0, s>>>(a, payload);
+    return cudaGetLastError();
 }
 
 }  // namespace apax

@@ -48,6 +48,7 @@ int fill_enc_args(const void *x, int dtype, uint64_t n, const apax_params *p,
     a.out = (uint8_t *)out;
     a.cap = cap;
     a.res = res;
+    a.n_hdr = n;
     a.spin_limit = 1ll << 31;
     a.test_stall_tile = -1;
     if (p->mode == APAX_FIXED_RATE) {
@@ -112,9 +113,13 @@ int fill_prof_args(const void *x, int dtype, uint64_t n, uint32_t block_size,
 
 namespace {
 
+// A whole array, or (shard) the blocks [b0, b1) of an array of n_all
+// elements, x pointing at block b0 - 1 (b0 > 0: the lag decision's halo) or
+// at block 0; the container then describes the sub-array of those blocks.
 int encode_impl(const void *x, int dtype, uint64_t n, const apax_params *p,
                 const uint32_t *code_dev, void *out, uint64_t cap, void *ws, uint64_t wsb,
-                apax_result *res, int64_t stall, int64_t spin, void *stream)
+                apax_result *res, int64_t stall, int64_t spin, void *stream,
+                bool shard = false, uint64_t n_all = 0, uint64_t b0 = 0, uint64_t b1 = 0)
 {
     EncArgs a;
     uint32_t pw, ew;
@@ -156,6 +161,16 @@ int encode_impl(const void *x, int dtype, uint64_t n, const apax_params *p,
     a.done = (unsigned *)(w + 4);
     a.status = (int *)(w + 8);
     a.tiles = (unsigned long long *)(w + kWsHead);
+    if (shard) {
+        // blocks keep their global numbers: the halo block j - 1 of the first
+        // one is read, and x is placed so that block j sits at x + j N
+        const uint64_t xb0 = b0 ? b0 - 1 : 0;
+        a.x = (const void *)((uintptr_t)x - (uintptr_t)(xb0 * (uint64_t)a.N * f.size));
+        a.n = n_all;
+        a.jb0 = b0;
+        a.nb = b1;
+        a.n_hdr = n;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     st = cuda_fail(cudaMemsetAsync(ws, 0, need_ws, s));
     if (st) return st;
@@ -336,6 +351,101 @@ int apax_encode_test_stall(const void *x, int dtype, uint64_t n, const apax_para
     if (!p || p->mode != APAX_FIXED_QUALITY || spin_cycles <= 0) return APAX_ERR_INVALID_ARG;
     return encode_impl(x, dtype, n, p, nullptr, out, out_capacity, workspace, workspace_bytes,
                        res, stall_tile, spin_cycles, stream);
+}
+
+int apax_shard_elements(uint64_t n, uint32_t block_size, uint64_t block_begin, uint64_t block_end,
+                        uint64_t *elements)
+{
+    if (!block_size_ok(block_size)) return APAX_ERR_BLOCK_SIZE;
+    const uint64_t nb = (n + block_size - 1) / block_size;
+    if (!elements || block_begin >= block_end || block_end > nb) return APAX_ERR_INVALID_ARG;
+    const uint64_t e1 = block_end * (uint64_t)block_size < n ? block_end * (uint64_t)block_size : n;
+    *elements = e1 - block_begin * (uint64_t)block_size;
+    return APAX_OK;
+}
+
+int apax_encode_shard(const void *x, int dtype, uint64_t n, const apax_params *p,
+                      uint64_t block_begin, uint64_t block_end, void *out, uint64_t out_capacity,
+                      void *workspace, uint64_t workspace_bytes, apax_result *res, void *stream)
+{
+    if (!p) return APAX_ERR_INVALID_ARG;
+    uint64_t n_sub;
+    int st = apax_shard_elements(n, p->block_size, block_begin, block_end, &n_sub);
+    if (st) return st;
+    return encode_impl(x, dtype, n_sub, p, nullptr, out, out_capacity, workspace, workspace_bytes,
+                       res, -1, 1ll << 31, stream, true, n, block_begin, block_end);
+}
+
+int apax_shard_rebase(void *container, uint64_t block_count, uint64_t add_words, void *stream)
+{
+    if (!container || ((uintptr_t)container & 3)) return APAX_ERR_INVALID_ARG;
+    uint32_t *t = (uint32_t *)((uint8_t *)container + 40);
+    return cuda_fail(launch_table_rebase(t, t, block_count, add_words, (cudaStream_t)stream));
+}
+
+int apax_merge_shards(const apax_shard *shards, int count, int dtype, uint64_t n,
+                      const apax_params *p, void *out, uint64_t out_capacity, apax_result *res,
+                      void *stream)
+{
+    Fmt f;
+    int st = check(dtype, p, f);
+    if (st) return st;
+    if (!shards || count < 1 || !out || ((uintptr_t)out & 3)) return APAX_ERR_INVALID_ARG;
+    const uint32_t N = p->block_size;
+    const uint64_t nb = (n + N - 1) / N;
+    const bool fq = p->mode == APAX_FIXED_QUALITY;
+    // the shards tile [0, nb) in order; their payload sizes from their byte counts
+    uint64_t next = 0, payload = 0;
+    for (int i = 0; i < count; ++i) {
+        const apax_shard &sh = shards[i];
+        if (!sh.container || ((uintptr_t)sh.container & 3) || sh.block_begin != next ||
+            sh.block_end <= sh.block_begin || sh.block_end > nb)
+            return APAX_ERR_INVALID_ARG;
+        const uint64_t head = 40 + (fq ? table_bytes(sh.block_end - sh.block_begin) : 0);
+        if (sh.bytes < head || ((sh.bytes - head) & 3)) return APAX_ERR_INVALID_ARG;
+        payload += sh.bytes - head;
+        next = sh.block_end;
+    }
+    if (next != nb) return APAX_ERR_INVALID_ARG;
+    if (fq && payload / 4 > 0xffffffffull) return APAX_ERR_TOO_LARGE;
+    const uint64_t poff = 40 + (fq ? table_bytes(nb) : 0);
+    if (out_capacity < poff + payload) return APAX_ERR_CAPACITY;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint8_t *o = (uint8_t *)out;
+    uint64_t at = 0;
+    for (int i = 0; i < count; ++i) {
+        const apax_shard &sh = shards[i];
+        const uint64_t nbs = sh.block_end - sh.block_begin;
+        const uint64_t head = 40 + (fq ? table_bytes(nbs) : 0);
+        const uint8_t *src = (const uint8_t *)sh.container;
+        if (fq) {
+            st = cuda_fail(launch_table_rebase((const uint32_t *)(src + 40),
+                                               (uint32_t *)(o + 40) + sh.block_begin, nbs, at / 4, s));
+            if (st) return st;
+        }
+        if (sh.bytes > head) {
+            st = cuda_fail(cudaMemcpyAsync(o + poff + at, src + head, sh.bytes - head,
+                                           cudaMemcpyDeviceToDevice, s));
+            if (st) return st;
+        }
+        at += sh.bytes - head;
+    }
+    if (fq && (nb & 1)) {  // the table's padding word
+        st = cuda_fail(cudaMemsetAsync(o + 40 + 4 * nb, 0, 4, s));
+        if (st) return st;
+    }
+    EncArgs a;
+    memset(&a, 0, sizeof a);
+    a.out = o;
+    a.dtype = dtype;
+    a.mode = p->mode;
+    a.N = N;
+    a.code = p->atten_code;
+    a.B = p->mode == APAX_FIXED_RATE ? (uint32_t)budget(f, N, p->rate_num, p->rate_den) : 0;
+    a.n_hdr = n;
+    a.poff = poff;
+    a.res = res;
+    return cuda_fail(launch_merged_header(a, payload, s));
 }
 
 uint64_t apax_decode_workspace_size(void) { return kWsHead; }

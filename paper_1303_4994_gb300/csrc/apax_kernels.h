@@ -67,10 +67,13 @@ inline int sm_count()
 }
 
 struct EncArgs {
-    const void *x;
+    const void *x;      // element 0 of the array (a shard's x is offset so that
+                        // its blocks sit at their global places)
     uint64_t n;
     uint32_t N;
-    uint64_t nb;        // blocks
+    uint64_t nb;        // blocks (the end of the encoded range)
+    uint64_t jb0;       // first block encoded (0, or a shard's first block)
+    uint64_t n_hdr;     // elements named in the container header
     int dtype;
     int mode;           // 0 fixed rate, 1 fixed quality
     uint32_t code;      // fixed-quality code
@@ -172,6 +175,11 @@ bool profile_t1_eligible(const ProfArgs &a);
 cudaError_t launch_profile_t1(const ProfArgs &a, cudaStream_t s);
 
 cudaError_t launch_encode(const EncArgs &a, int ts, int threads, size_t smem, cudaStream_t s);
+// Shard merging: dst[i] = src[i] + add for i < count; the merged header
+// (a.out, a.n_hdr, a.mode, a.code, a.B, a.poff) and a.res.
+cudaError_t launch_table_rebase(const uint32_t *src, uint32_t *dst, uint64_t count, uint64_t add,
+                                cudaStream_t s);
+cudaError_t launch_merged_header(const EncArgs &a, uint64_t payload, cudaStream_t s);
 cudaError_t launch_encode_batch(const EncBatchArgs &b, int ts, int threads, size_t smem,
                                unsigned ctas, cudaStream_t s);
 int encode_batch_occupancy(int ts, int threads, size_t smem);  // CTAs per SM
