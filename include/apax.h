@@ -279,6 +279,43 @@ int apax_merge_shards(const apax_shard *shards, int count, int dtype, uint64_t n
                       const apax_params *p, void *out, uint64_t out_capacity, apax_result *res,
                       void *stream);
 
+/* ---------------------------------------------------------------- quality
+ * The profiler's windows 3 and 4 (Sec. 4) for an array x and its decoded y
+ * (e.g. at the recommended code): the 2-sigma S2R margin -- the level that
+ * 95.5% of the samples' signal-to-residual ratios 20 log10(|x|/|x - y|)
+ * reach -- and the spectral levels: peaks and floors of x, y and d = x - y,
+ * the residual spectrum's mean level, the dynamic range DR = peak - floor of
+ * x, the SRR = peak of x - residual mean, and the FFT S2R margin = floor of
+ * x - residual mean.  Readings (the paper gives no estimator): d is x - y
+ * rounded once to binary64; the margin's ratio is the floor(45 n / 1000)-th
+ * smallest per-sample |x| / |d| (0-based; +inf where d = 0, 0 where x = 0
+ * and d != 0); spectra average full segments of 4096 samples (the largest
+ * power of two <= n below that), each mean-removed and multiplied by the
+ * periodic Hann window, as |FFT|^2 / sum(w^2) over bins 1..L/2; peak = max,
+ * floor = lower median, residual mean = mean of 10 log10 over the bins. */
+typedef struct {
+    double s2r_ratio;        /* the 2-sigma S2R margin as an amplitude ratio */
+    uint64_t n;
+    uint32_t L, segments;    /* spectral segment length and count (0: no spectrum) */
+    double peak_x, floor_x, peak_y, floor_y, peak_d, floor_d; /* bin powers */
+    double mean_d_db;        /* mean of 10 log10 of the residual's bins */
+} apax_quality;
+
+/* Workspace bytes of apax_quality_metrics for n elements (host call). */
+int apax_quality_workspace_size(int dtype, uint64_t n, uint64_t *bytes /* host */);
+
+/* Compute the metrics of x against y (device, n elements of dtype each,
+ * finite) into q (device), asynchronously on the stream: kernels and one
+ * cudaMemsetAsync of the workspace.  The margin's ratio is exact (the same
+ * bits as sorting the ratios); the spectral levels are binary64 FFT sums
+ * added in an order that does not depend on the device. */
+int apax_quality_metrics(const void *x, const void *y, int dtype, uint64_t n, void *workspace,
+                         uint64_t workspace_bytes, apax_quality *q, void *stream);
+
+/* The metrics in dB (host call): out = [2-sigma S2R margin, peak_x, floor_x,
+ * peak_y, floor_y, peak_d, floor_d, residual mean, DR, SRR, FFT S2R margin]. */
+void apax_quality_db(const apax_quality *q, double *out /* host, 11 */);
+
 /* Encode without any allocation (no counterpart in the paper: this entry
  * exists for callers that cannot allocate device memory at all -- code
  * running inside another runtime's allocator or memory-pool hook, paths that

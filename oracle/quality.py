@@ -22,7 +22,7 @@ Readings (the paper gives no estimator, FFT length or window):
     property.  In dB: 20 log10(ratio).
   * Spectra: Welch-Bartlett averaging over the array flattened in C order:
     segments of L = 4096 samples (the largest power of two <= n when
-    n < 4096), hop L, full segments only; each segment has its mean removed
+    n < 4096; no spectrum below 4 samples), hop L, full segments only; each segment has its mean removed
     and is multiplied by the periodic Hann window w[m] = (1 - cos(2 pi m / L))/2;
     P[k] = mean over segments of |FFT[k]|^2 / sum(w^2), for bins k = 1..L/2
     (DC left out).  Peak = max P, floor = the lower median (the
@@ -115,8 +115,8 @@ def spectral_metrics(x: np.ndarray, y: np.ndarray) -> dict:
     the FFT S2R margin (dB), with the raw powers beside them."""
     n = np.asarray(x).size
     L = segment_length(n)
-    if L < 4:
-        return {"L": L, "segments": 0}
+    if L < 4:  # no spectrum below 4 samples (a segment of 2 has one bin)
+        return {"L": 0, "segments": 0}
     xd = np.asarray(x, dtype=np.float64).reshape(-1)
     yd = np.asarray(y, dtype=np.float64).reshape(-1)
     out = {"L": L, "segments": n // L}

@@ -99,6 +99,18 @@ class ServerStats(ctypes.Structure):
                                                 "undelivered")]
 
 
+class Quality(ctypes.Structure):
+    _fields_ = [("s2r_ratio", ctypes.c_double), ("n", ctypes.c_uint64), ("L", ctypes.c_uint32),
+                ("segments", ctypes.c_uint32), ("peak_x", ctypes.c_double),
+                ("floor_x", ctypes.c_double), ("peak_y", ctypes.c_double),
+                ("floor_y", ctypes.c_double), ("peak_d", ctypes.c_double),
+                ("floor_d", ctypes.c_double), ("mean_d_db", ctypes.c_double)]
+
+
+QUALITY_DB = ("s2r_2sigma", "peak_x", "floor_x", "peak_y", "floor_y", "peak_d", "floor_d",
+              "mean_d", "dr", "srr", "fft_s2r_margin")
+
+
 class Shard(ctypes.Structure):
     _fields_ = [("container", ctypes.c_void_p), ("bytes", ctypes.c_uint64),
                 ("block_begin", ctypes.c_uint64), ("block_end", ctypes.c_uint64)]
@@ -125,7 +137,8 @@ EXPORTS = ("apax_encoded_size", "apax_workspace_size", "apax_encode", "apax_enco
            "apax_batch_decode_create", "apax_batch_profile_workspace_size",
            "apax_batch_profile_create", "apax_server_create", "apax_server_submit",
            "apax_server_poll", "apax_server_release", "apax_server_stats", "apax_server_destroy",
-           "apax_shard_elements", "apax_encode_shard", "apax_shard_rebase", "apax_merge_shards")
+           "apax_shard_elements", "apax_encode_shard", "apax_shard_rebase", "apax_merge_shards",
+           "apax_quality_workspace_size", "apax_quality_metrics", "apax_quality_db")
 OP_ENCODE, OP_DECODE = 0, 1
 NOALLOC_SCRATCH_BYTES = 256 << 10
 
@@ -185,6 +198,10 @@ def lib():
         L.apax_encode_shard.argtypes = [vp, i32, u64, pP, u64, u64, vp, u64, vp, u64, vp, vp]
         L.apax_shard_rebase.argtypes = [vp, u64, u64, vp]
         L.apax_merge_shards.argtypes = [ctypes.POINTER(Shard), i32, i32, u64, pP, vp, u64, vp, vp]
+        L.apax_quality_workspace_size.argtypes = [i32, u64, p64]
+        L.apax_quality_metrics.argtypes = [vp, vp, i32, u64, vp, u64, vp, vp]
+        L.apax_quality_db.argtypes = [ctypes.POINTER(Quality), vp]
+        L.apax_quality_db.restype = None
         L.apax_status_string.argtypes = [i32]
         L.apax_status_string.restype = ctypes.c_char_p
         L.apax_build_info.argtypes = []
@@ -720,3 +737,44 @@ def merge_shards(containers, ranges, dtype_code: int, n: int, p: Params, stream=
     r = read_result(res)
     _check(r.status, "merge_shards (device)")
     return out[:r.bytes]
+
+
+# ---------------------------------------------------------------- quality
+def quality_workspace_size(dtype_code: int, n: int) -> int:
+    out = ctypes.c_uint64()
+    _check(lib().apax_quality_workspace_size(dtype_code, n, ctypes.byref(out)),
+           "quality_workspace_size")
+    return out.value
+
+
+def quality_into(x: torch.Tensor, y: torch.Tensor, workspace: torch.Tensor, q: torch.Tensor,
+                 stream=None):
+    """Enqueue apax_quality_metrics (x, y device tensors of one dtype; q a
+    device uint8 tensor of sizeof(Quality) bytes, 8-byte aligned)."""
+    xf, yf = x.reshape(-1), y.reshape(-1)
+    assert xf.dtype == yf.dtype and xf.numel() == yf.numel()
+    _check(lib().apax_quality_metrics(xf.data_ptr(), yf.data_ptr(), _dtype_code(xf), xf.numel(),
+                                      workspace.data_ptr(), workspace.numel(), q.data_ptr(),
+                                      _stream(stream)), "quality")
+
+
+def read_quality(q: torch.Tensor) -> Quality:
+    b = q.cpu().numpy().tobytes()
+    return Quality.from_buffer_copy(b[:ctypes.sizeof(Quality)])
+
+
+def quality_db(qr: Quality) -> dict:
+    import numpy as _np
+    out = _np.zeros(len(QUALITY_DB), dtype=_np.float64)
+    lib().apax_quality_db(ctypes.byref(qr), out.ctypes.data)
+    return dict(zip(QUALITY_DB, out.tolist()))
+
+
+def quality(x: torch.Tensor, y: torch.Tensor, stream=None):
+    """(Quality record, its levels in dB) for x against y."""
+    ws = aligned_workspace(quality_workspace_size(_dtype_code(x.reshape(-1)), x.numel()),
+                           x.device)
+    q = torch.zeros(ctypes.sizeof(Quality), dtype=torch.uint8, device=x.device)
+    quality_into(x, y, ws, q, stream)
+    qr = read_quality(q)
+    return qr, quality_db(qr)

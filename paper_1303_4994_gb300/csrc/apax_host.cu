@@ -448,6 +448,116 @@ int apax_merge_shards(const apax_shard *shards, int count, int dtype, uint64_t n
     return cuda_fail(launch_merged_header(a, payload, s));
 }
 
+namespace {
+// Spectral segment length for n elements (0 below 4 samples).
+int quality_L(uint64_t n, int &logL)
+{
+    if (n < 4) {
+        logL = 0;
+        return 0;
+    }
+    int L = 4096;
+    while ((uint64_t)L > n) L >>= 1;
+    logL = 0;
+    while ((1 << logL) < L) ++logL;
+    return L;
+}
+
+struct QLayout {
+    uint64_t state, hist, keys, tw, part, P, total;
+};
+
+QLayout quality_layout(uint64_t n)
+{
+    int logL;
+    const int L = quality_L(n, logL);
+    const uint64_t H = (uint64_t)L / 2, segs = L ? n / (uint64_t)L : 0;
+    auto up = [](uint64_t v) { return (v + 255) / 256 * 256; };
+    QLayout q;
+    q.state = 0;
+    q.hist = 256;
+    q.keys = q.hist + up(256 * 8);
+    q.tw = q.keys + up(8 * n);
+    q.part = q.tw + up(16 * H);
+    q.P = q.part + up(8 * 3 * H * quality_spectral_ctas(segs));
+    q.total = q.P + up(8 * 3 * H);
+    return q;
+}
+}  // namespace
+
+int apax_quality_workspace_size(int dtype, uint64_t n, uint64_t *bytes)
+{
+    Fmt f;
+    int st = fmt_of(dtype, f);
+    if (st) return st;
+    if (!bytes) return APAX_ERR_INVALID_ARG;
+    *bytes = quality_layout(n).total;
+    return APAX_OK;
+}
+
+int apax_quality_metrics(const void *x, const void *y, int dtype, uint64_t n, void *workspace,
+                         uint64_t workspace_bytes, apax_quality *q, void *stream)
+{
+    Fmt f;
+    int st = fmt_of(dtype, f);
+    if (st) return st;
+    if ((n && (!x || !y)) || !q || !workspace || ((uintptr_t)workspace & 255) ||
+        ((uintptr_t)x % f.size) || ((uintptr_t)y % f.size) || ((uintptr_t)q & 7))
+        return APAX_ERR_INVALID_ARG;
+    const QLayout lay = quality_layout(n);
+    if (workspace_bytes < lay.total) return APAX_ERR_CAPACITY;
+    uint8_t *w = (uint8_t *)workspace;
+    QualityArgs a;
+    memset(&a, 0, sizeof a);
+    a.x = x;
+    a.y = y;
+    a.dtype = dtype;
+    a.n = n;
+    a.state = (SelState *)(w + lay.state);
+    a.hist = (unsigned long long *)(w + lay.hist);
+    a.keys = (unsigned long long *)(w + lay.keys);
+    a.L = quality_L(n, a.logL);
+    a.segs = a.L ? n / (uint64_t)a.L : 0;
+    a.tw = (double2 *)(w + lay.tw);
+    a.part = (double *)(w + lay.part);
+    a.P = (double *)(w + lay.P);
+    a.q = q;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = cuda_fail(cudaMemsetAsync(w, 0, lay.keys, s));  // state and counters
+    if (st) return st;
+    apax_quality head;
+    memset(&head, 0, sizeof head);
+    head.s2r_ratio = __builtin_nan("");
+    head.n = n;
+    head.L = (uint32_t)a.L;
+    head.segments = (uint32_t)a.segs;
+    // the header fields known on the host go in with a small kernel-free copy
+    // of the whole record's defaults through the memset-cleared workspace:
+    // the kernels overwrite the computed fields
+    st = cuda_fail(launch_quality_header(q, head, s));
+    if (st) return st;
+    return cuda_fail(launch_quality(a, s));
+}
+
+void apax_quality_db(const apax_quality *q, double *out)
+{
+    auto db = [](double p) { return p > 0.0 ? 10.0 * log10(p) : (p == 0.0 ? -INFINITY : NAN); };
+    const double r = q->s2r_ratio;
+    out[0] = r != r ? r : (r == 0.0 ? -INFINITY : (isinf(r) ? INFINITY : 20.0 * log10(r)));
+    out[1] = db(q->peak_x);
+    out[2] = db(q->floor_x);
+    out[3] = db(q->peak_y);
+    out[4] = db(q->floor_y);
+    out[5] = db(q->peak_d);
+    out[6] = db(q->floor_d);
+    out[7] = q->mean_d_db;
+    out[8] = out[1] - out[2];
+    out[9] = out[1] - out[7];
+    out[10] = out[2] - out[7];
+    if (!q->segments)
+        for (int i = 1; i < 11; ++i) out[i] = NAN;
+}
+
 uint64_t apax_decode_workspace_size(void) { return kWsHead; }
 
 int apax_decode(const void *in, uint64_t in_bytes, void *y, int dtype, uint64_t n,

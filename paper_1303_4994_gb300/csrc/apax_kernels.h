@@ -167,6 +167,31 @@ struct ProfArgs {
                          // sweep (NULL: that sweep is not used)
 };
 
+// Signal-quality metrics (apax_quality.cu).
+struct SelState {
+    unsigned long long prefix;  // key bits chosen so far
+    unsigned long long k;       // rank still to find among the keys matching prefix
+    int shift;                  // bit position of the byte being counted
+    int pad;
+};
+struct QualityArgs {
+    const void *x, *y;
+    int dtype;
+    uint64_t n;
+    SelState *state;
+    unsigned long long *hist;  // 256 counters
+    unsigned long long *keys;  // n
+    int L, logL;               // spectral segment length (0: no spectrum)
+    uint64_t segs;
+    double2 *tw;               // L/2 twiddles
+    double *part;              // per-CTA periodogram sums
+    double *P;                 // 3 * L/2 averaged bins
+    apax_quality *q;
+};
+uint64_t quality_spectral_ctas(uint64_t segs);
+cudaError_t launch_quality(const QualityArgs &a, cudaStream_t s);
+cudaError_t launch_quality_header(apax_quality *q, const apax_quality &h, cudaStream_t s);
+
 // The one-block-per-thread float32 sweep (apax_profile_t1.cu): arrays of at
 // least this many blocks of at most 256 samples, candidates 0 then
 // power-of-two attenuations.
