@@ -38,6 +38,7 @@ Other workloads (one GPU):
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import subprocess
@@ -298,6 +299,15 @@ def run_ours(args, rank, world, local_rank):
     ms = _median(t_step)
     ms_prof, ms_enc, ms_dec = (_median(t) for t in (t_prof, t_enc, t_dec))
 
+    # the profiler's windows 3 and 4 at the recommended point (x against the
+    # decoded y): 2-sigma S2R margin and spectral levels, timed on their own
+    qws = A.aligned_workspace(A.quality_workspace_size(A.F32, n), dev)
+    qbuf = torch.zeros(ctypes.sizeof(A.Quality), dtype=torch.uint8, device=dev)
+    A.quality_into(x, y, qws, qbuf)
+    torch.cuda.synchronize()
+    t_q = _events(lambda: A.quality_into(x, y, qws, qbuf), 5, stream, flush)
+    qdb = A.quality_db(A.read_quality(qbuf))
+
     # end to end through the C ABI with host buffers: the host-input sweep
     # (H2D of x in pieces on a copy stream, hidden behind the sweep), encode,
     # decode, D2H of the container and the profile points
@@ -374,6 +384,8 @@ def run_ours(args, rank, world, local_rank):
         "encode_gbs": round(kern["encode"]["uncompressed_gbs"] * world, 2),
         "decode_gbs": round(kern["decode"]["uncompressed_gbs"] * world, 2),
         "kernels": kern,
+        "quality_db": {k: (round(v, 4) if abs(v) != float("inf") else str(v)) for k, v in qdb.items()},
+        "quality_ms": round(_median(t_q), 4),
         "roofline": roof,
         "e2e": {"value": round(world * xb / e2e / 1e6, 3), "unit": "GB/s",
                 "h2d_bytes_per_step": xb,
