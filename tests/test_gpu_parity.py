@@ -372,3 +372,48 @@ def test_profile_from_host_matches_device(dt):
     A.profile_from_host_into(e.pin_memory(), e.cuda(), N, None, 0.9999, ws3, pts3, summ3)
     torch.cuda.synchronize()
     assert A.read_summary(summ3).status == 0 and A.read_summary(summ3).n == 0
+
+
+@pytest.mark.parametrize("dt", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("N", [128, 200, 512])
+def test_large_arrays_block_sizes_decode(dt, N):
+    # 32,768+ blocks of 128..512 samples (the block-per-thread decoder):
+    # whole arrays (ragged tails, all three streams, both modes) against the
+    # oracle, a block range, and corrupt packets
+    rng = np.random.default_rng(300 + 7 * dt + N)
+    nb = 32768 + 17
+    n = nb * N - 3
+    x = _data(dt, n, rng, 1)
+    if dt >= 4:
+        x[: n // 3] = _data(dt, n // 3, rng, 0)  # noise: stream 0 blocks too
+    xt = torch.from_numpy(x).cuda()
+    ydt = TT[dt]
+    for mode, rate, code in ((1, (1, 1), 700), (0, (4, 1), 0)):
+        try:
+            O.encoded_size(x.dtype, n, N, mode, rate[0], rate[1])
+        except O.OracleError:
+            continue
+        c = A.encode(xt, N, mode, rate, code)
+        cb = c.cpu().numpy().tobytes()
+        assert cb == O.encode(x, N, mode, rate[0], rate[1], code, threads=0)
+        y = A.decode(c, ydt, n)
+        yo = O.decode(cb, x.dtype, n, threads=0)
+        np.testing.assert_array_equal(_bits(y.cpu().numpy()), _bits(yo))
+        part = A.decode_blocks(c, ydt, n, 100, 32700, N)
+        assert torch.equal(part.view(torch.uint8), y[100 * N:32700 * N].view(torch.uint8))
+        bad = bytearray(cb)
+        poff = 40 + (((4 * nb + 7) // 8) * 8 if mode == 1 else 0)
+        B_ = 0 if mode == 1 else int(np.frombuffer(cb, np.uint32, 1, 16)[0])
+        start = poff + (4 * int(np.frombuffer(cb, np.uint32, 1, 40 + 4 * 20000)[0])
+                        if mode == 1 else B_ * 20000)
+        bad[start] |= 3  # reserved stream selector
+        _, r = A.decode(torch.frombuffer(bad, dtype=torch.uint8).cuda(), ydt, n, check=False)
+        assert r.status == -9
+        bad = bytearray(cb)
+        bad[start + 6] ^= 0xFF  # scrambled tokens: a status or the oracle's values
+        st = O.decode_status(bytes(bad), x.dtype, n)
+        yb, r = A.decode(torch.frombuffer(bad, dtype=torch.uint8).cuda(), ydt, n, check=False)
+        if st == 0:
+            assert r.status == 0
+        else:
+            assert r.status == -9
