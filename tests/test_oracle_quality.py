@@ -121,3 +121,36 @@ def test_window3_relations_on_the_paper_example():
 def test_segment_length():
     assert Q.segment_length(10 ** 6) == 4096 and Q.segment_length(4096) == 4096
     assert Q.segment_length(4095) == 2048 and Q.segment_length(5) == 4
+
+
+def _tables23():
+    rows = []
+    for ln in open(os.path.join(HERE, "golden", "tables2_3_spectral.txt")):
+        ln = ln.strip()
+        if ln and not ln.startswith("#"):
+            name, *v = ln.split()
+            rows.append((name, *map(float, v)))
+    return rows
+
+
+def test_tables2_3_sdr_is_dr_plus_margin():
+    # Table 2's DR is its peak minus its floor on every row (within the 0.1 dB
+    # rounding of three printed values), and Table 3's SDR equals Table 2's DR
+    # plus Table 3's spectral margin on all rows but the first and third 8-bit
+    # datasets: the paper's SDR is the oracle's SRR (input peak minus residual
+    # mean) and its margin the oracle's floor minus residual mean
+    rows = _tables23()
+    assert len(rows) == 25
+    tol = 0.15 + 1e-9
+    for name, pk, fl, dr, sdr, mg in rows:
+        assert abs(pk - fl - dr) <= tol, name
+    bad = [r[0] for r in rows if abs(r[4] - (r[3] + r[5])) > tol]
+    assert bad == ["image1_i8", "oscilloscope_i8"]
+    # the oracle's levels obey the same identities exactly on a field whose
+    # levels span several tens of dB
+    rng = np.random.default_rng(23)
+    x = np.cumsum(rng.standard_normal(3 * 4096 + 17))
+    y = x + rng.standard_normal(x.size) * 1e-3
+    m = Q.spectral_metrics(x, y)
+    assert m["dr"] == m["peak_x"] - m["floor_x"]
+    assert m["srr"] == pytest.approx(m["dr"] + m["fft_s2r_margin"], abs=1e-9)
