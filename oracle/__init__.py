@@ -60,15 +60,16 @@ def lib():
         _lib = ctypes.CDLL(build())
         u64, i32, vp = ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p
         u32, p64 = ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64)
-        _lib.oracle_encoded_size.argtypes = [i32, u64, u32, i32, u32, u32, i32, p64]
+        _lib.oracle_encoded_size.argtypes = [i32, u64, u32, i32, i32, u32, u32, i32, p64]
         _lib.oracle_encode.argtypes = [vp, i32, u64, u32, i32, u32, u32, i32, vp, u64, p64]
-        _lib.oracle_encode_s.argtypes = [vp, i32, u64, u32, i32, u32, u32, i32, i32, vp, u64, p64]
+        _lib.oracle_encode_s.argtypes = [vp, i32, u64, u32, i32, i32, u32, u32, i32, i32, vp, u64,
+                                         p64]
         _lib.oracle_decode.argtypes = [vp, u64, vp, i32, u64]
         _lib.oracle_metrics.argtypes = [vp, vp, i32, u64, u32, vp]
         _lib.oracle_block_sums.argtypes = [vp, vp, i32, u64, u32, u64, u64, vp]
         _lib.oracle_corr.argtypes = [ctypes.c_double] * 3
         _lib.oracle_corr.restype = ctypes.c_double
-        _lib.oracle_profile.argtypes = [vp, i32, u64, u32, vp, i32, ctypes.c_double, vp,
+        _lib.oracle_profile.argtypes = [vp, i32, u64, u32, i32, vp, i32, ctypes.c_double, vp,
                                         ctypes.POINTER(ctypes.c_int)]
         _lib.oracle_bits.argtypes = [ctypes.c_int32]
         _lib.oracle_recip.argtypes = [i32]
@@ -81,21 +82,21 @@ def lib():
         _lib.oracle_quantise.restype = ctypes.c_int32
         _lib.oracle_dequantise.argtypes = [ctypes.c_int32, i32, i32, i32, vp]
         _lib.oracle_block_exponent.argtypes = [vp, i32, u64, i32, ctypes.POINTER(ctypes.c_int)]
-        _lib.oracle_packet_bits.argtypes = [vp, i32, u64, u32, u64, i32, i32, p64]
-        _lib.oracle_streams.argtypes = [vp, i32, u64, u32, u64, u64, vp]
-        _lib.oracle_fr_code.argtypes = [vp, i32, u64, u32, u64, i32, u64, i32,
+        _lib.oracle_packet_bits.argtypes = [vp, i32, u64, u32, i32, u64, i32, i32, p64]
+        _lib.oracle_streams.argtypes = [vp, i32, u64, u32, i32, u64, u64, vp]
+        _lib.oracle_fr_code.argtypes = [vp, i32, u64, u32, i32, u64, i32, u64, i32,
                                         ctypes.POINTER(ctypes.c_int)]
-        _lib.oracle_encode_blocks.argtypes = [vp, i32, u64, u32, i32, u32, u32, i32, i32, u64,
-                                              u64, vp, u64, vp]
-        _lib.oracle_fr_budget.argtypes = [i32, u32, i32, u32, u32, p64]
-        _lib.oracle_min_packet.argtypes = [i32, u32, i32, p64]
+        _lib.oracle_encode_blocks.argtypes = [vp, i32, u64, u32, i32, i32, u32, u32, i32, i32,
+                                              u64, u64, vp, u64, vp]
+        _lib.oracle_fr_budget.argtypes = [i32, u32, i32, i32, u32, u32, p64]
+        _lib.oracle_min_packet.argtypes = [i32, u32, i32, i32, p64]
         _lib.oracle_derived.argtypes = [vp, u64, vp]
         _lib.oracle_threads.argtypes = [i32]
-        _lib.oracle_encode_mt.argtypes = [vp, i32, u64, u32, i32, u32, u32, i32, i32, vp, u64,
-                                          p64, i32]
+        _lib.oracle_encode_mt.argtypes = [vp, i32, u64, u32, i32, i32, u32, u32, i32, i32, vp,
+                                          u64, p64, i32]
         _lib.oracle_decode_mt.argtypes = [vp, u64, vp, i32, u64, i32]
         _lib.oracle_metrics_mt.argtypes = [vp, vp, i32, u64, u32, vp, i32]
-        _lib.oracle_profile_mt.argtypes = [vp, i32, u64, u32, vp, i32, ctypes.c_double, vp,
+        _lib.oracle_profile_mt.argtypes = [vp, i32, u64, u32, i32, vp, i32, ctypes.c_double, vp,
                                            ctypes.POINTER(ctypes.c_int), i32]
     return _lib
 
@@ -114,10 +115,14 @@ def _ptr(a: np.ndarray) -> int:
     return a.ctypes.data
 
 
+# format options (container version 2): BFPE groups of 8, the sum stream
+FMT_GROUP8, FMT_SUM_STREAM = 1, 2
+
+
 def encoded_size(dtype, n: int, N: int = 256, mode: int = MODE_FQ, num: int = 1,
-                 den: int = 1, code: int = 0) -> int:
+                 den: int = 1, code: int = 0, fmt: int = 0) -> int:
     out = ctypes.c_uint64()
-    st = lib().oracle_encoded_size(DTYPE_CODE[np.dtype(dtype)], n, N, mode, num, den, code,
+    st = lib().oracle_encoded_size(DTYPE_CODE[np.dtype(dtype)], n, N, fmt, mode, num, den, code,
                                    ctypes.byref(out))
     if st:
         raise OracleError(st, "encoded_size")
@@ -133,21 +138,23 @@ SEARCH_BISECT, SEARCH_PREDICT = 0, 1
 
 
 def encode(x: np.ndarray, N: int = 256, mode: int = MODE_FQ, num: int = 1, den: int = 1,
-           code: int = 0, threads: int | None = None, search: int = SEARCH_BISECT) -> bytes:
+           code: int = 0, threads: int | None = None, search: int = SEARCH_BISECT,
+           fmt: int = 0) -> bytes:
     """Encode a C-contiguous array; returns the container bytes.  threads:
     None runs the plain sequential encoder; an int runs the same per-block
     code on that many threads over block ranges (0 = all cores).  search:
-    the fixed-rate search policy (BISECT or PREDICT)."""
+    the fixed-rate search policy (BISECT or PREDICT).  fmt: format options
+    (FMT_GROUP8 | FMT_SUM_STREAM; 0 writes a version-1 container)."""
     x = np.ascontiguousarray(x).reshape(-1)
-    cap = encoded_size(x.dtype, x.size, N, mode, num, den, code)
+    cap = encoded_size(x.dtype, x.size, N, mode, num, den, code, fmt)
     buf = np.zeros(cap, dtype=np.uint8)
     out = ctypes.c_uint64()
     if threads is None:
-        st = lib().oracle_encode_s(_ptr(x), _code(x), x.size, N, mode, num, den, code, search,
-                                   _ptr(buf), cap, ctypes.byref(out))
+        st = lib().oracle_encode_s(_ptr(x), _code(x), x.size, N, fmt, mode, num, den, code,
+                                   search, _ptr(buf), cap, ctypes.byref(out))
     else:
-        st = lib().oracle_encode_mt(_ptr(x), _code(x), x.size, N, mode, num, den, code, search,
-                                    _ptr(buf), cap, ctypes.byref(out), threads)
+        st = lib().oracle_encode_mt(_ptr(x), _code(x), x.size, N, fmt, mode, num, den, code,
+                                    search, _ptr(buf), cap, ctypes.byref(out), threads)
     if st:
         raise OracleError(st, "encode")
     return buf[:out.value].tobytes()
@@ -216,19 +223,19 @@ DEFAULT_CANDIDATES = tuple(256 * i for i in range(16))
 
 
 def profile(x: np.ndarray, N: int = 256, candidates=DEFAULT_CANDIDATES, target: float = 0.99999,
-            threads: int | None = None):
-    """Returns (points, recommended_index, target_missed); threads as for
-    encode."""
+            threads: int | None = None, fmt: int = 0):
+    """Returns (points, recommended_index, target_missed); threads and fmt
+    as for encode."""
     x = np.ascontiguousarray(x).reshape(-1)
     c = np.asarray(candidates, dtype=np.uint16)
     pts = (Point * len(c))()
     rec = ctypes.c_int()
     if threads is None:
-        st = lib().oracle_profile(_ptr(x), _code(x), x.size, N, _ptr(c), len(c), target, pts,
-                                  ctypes.byref(rec))
+        st = lib().oracle_profile(_ptr(x), _code(x), x.size, N, fmt, _ptr(c), len(c), target,
+                                  pts, ctypes.byref(rec))
     else:
-        st = lib().oracle_profile_mt(_ptr(x), _code(x), x.size, N, _ptr(c), len(c), target, pts,
-                                     ctypes.byref(rec), threads)
+        st = lib().oracle_profile_mt(_ptr(x), _code(x), x.size, N, fmt, _ptr(c), len(c), target,
+                                     pts, ctypes.byref(rec), threads)
     if st < 0:
         raise OracleError(st, "profile")
     return list(pts), rec.value, st == 1
@@ -285,60 +292,63 @@ def block_exponent(x: np.ndarray, off: int, L: int) -> int:
     return e.value
 
 
-def packet_bits(x: np.ndarray, N: int, j: int, code: int, s: int) -> int:
+def packet_bits(x: np.ndarray, N: int, j: int, code: int, s: int, fmt: int = 0) -> int:
     x = np.ascontiguousarray(x).reshape(-1)
     out = ctypes.c_uint64()
-    st = lib().oracle_packet_bits(_ptr(x), _code(x), x.size, N, j, code, s, ctypes.byref(out))
+    st = lib().oracle_packet_bits(_ptr(x), _code(x), x.size, N, fmt, j, code, s,
+                                  ctypes.byref(out))
     if st:
         raise OracleError(st, "packet_bits")
     return out.value
 
 
-def streams(x: np.ndarray, N: int, b0: int, b1: int) -> list:
+def streams(x: np.ndarray, N: int, b0: int, b1: int, fmt: int = 0) -> list:
     x = np.ascontiguousarray(x).reshape(-1)
     out = np.zeros(b1 - b0, dtype=np.int32)
-    st = lib().oracle_streams(_ptr(x), _code(x), x.size, N, b0, b1, _ptr(out))
+    st = lib().oracle_streams(_ptr(x), _code(x), x.size, N, fmt, b0, b1, _ptr(out))
     if st:
         raise OracleError(st, "streams")
     return out.tolist()
 
 
-def fr_code(x: np.ndarray, N: int, j: int, s: int, budget: int, search: int = SEARCH_BISECT) -> int:
+def fr_code(x: np.ndarray, N: int, j: int, s: int, budget: int, search: int = SEARCH_BISECT,
+            fmt: int = 0) -> int:
     x = np.ascontiguousarray(x).reshape(-1)
     out = ctypes.c_int()
-    st = lib().oracle_fr_code(_ptr(x), _code(x), x.size, N, j, s, budget, search,
+    st = lib().oracle_fr_code(_ptr(x), _code(x), x.size, N, fmt, j, s, budget, search,
                               ctypes.byref(out))
     if st:
         raise OracleError(st, "fr_code")
     return out.value
 
 
-def fr_budget(dtype, N: int, L: int, num: int, den: int) -> int:
+def fr_budget(dtype, N: int, L: int, num: int, den: int, fmt: int = 0) -> int:
     out = ctypes.c_uint64()
-    st = lib().oracle_fr_budget(DTYPE_CODE[np.dtype(dtype)], N, L, num, den, ctypes.byref(out))
+    st = lib().oracle_fr_budget(DTYPE_CODE[np.dtype(dtype)], N, fmt, L, num, den,
+                                ctypes.byref(out))
     if st:
         raise OracleError(st, "fr_budget")
     return out.value
 
 
-def min_packet(dtype, N: int, L: int) -> int:
+def min_packet(dtype, N: int, L: int, fmt: int = 0) -> int:
     out = ctypes.c_uint64()
-    st = lib().oracle_min_packet(DTYPE_CODE[np.dtype(dtype)], N, L, ctypes.byref(out))
+    st = lib().oracle_min_packet(DTYPE_CODE[np.dtype(dtype)], N, fmt, L, ctypes.byref(out))
     if st:
         raise OracleError(st, "min_packet")
     return out.value
 
 
 def encode_blocks(x: np.ndarray, N: int, mode: int, num: int, den: int, code: int, b0: int,
-                  b1: int, search: int = SEARCH_BISECT):
+                  b1: int, search: int = SEARCH_BISECT, fmt: int = 0):
     """Packets of blocks [b0, b1) as a list of bytes objects."""
     x = np.ascontiguousarray(x).reshape(-1)
     maxp = 4 * ((48 + 8 * (N // 4) + 32 * N + 31) // 32)
     cap = maxp * (b1 - b0)
     buf = np.zeros(cap, dtype=np.uint8)
     lens = np.zeros(b1 - b0, dtype=np.uint64)
-    st = lib().oracle_encode_blocks(_ptr(x), _code(x), x.size, N, mode, num, den, code, search,
-                                    b0, b1, _ptr(buf), cap, _ptr(lens))
+    st = lib().oracle_encode_blocks(_ptr(x), _code(x), x.size, N, fmt, mode, num, den, code,
+                                    search, b0, b1, _ptr(buf), cap, _ptr(lens))
     if st:
         raise OracleError(st, "encode_blocks")
     out, pos = [], 0

@@ -16,10 +16,13 @@
  *       the best-stream decision of block j carried in block j+1's header;
  *       a 4-byte (integer) or 6-byte (float) block header.
  *   Sec. 6, bit-packer paragraph: block floating point with one exponent per
- *       group of N=4 samples, joint exponent encoding (nine 4-bit joint
- *       tokens, five 4-bit single tokens, 8-bit absolute tokens, the first
- *       exponent of a block absolute).
- *   Sec. 5: derivatives remove sample-to-sample redundancy (Fig. 3b).
+ *       group of 4 samples (or, in the second container version, of 8),
+ *       joint exponent encoding (nine 4-bit joint tokens, five 4-bit single
+ *       tokens, 8-bit absolute tokens, the first exponent of a block
+ *       absolute).
+ *   Sec. 5: derivatives remove sample-to-sample redundancy (Fig. 3b); the
+ *       signal monitor's correlated-neighbour choice adds, in the second
+ *       container version, the sum of neighbours for near-Nyquist data.
  *   Sec. 4: profiler -- rate/correlation sweep, r = sum(xy)/sqrt(sum x^2 sum y^2),
  *       recommended operating point at a correlation target.
  * Where the paper is silent the reading is stated beside the code; the
@@ -50,6 +53,11 @@
 
 enum { DT_I8 = 1, DT_I16 = 2, DT_I32 = 3, DT_F32 = 4, DT_F64 = 5 };
 enum { MODE_FR = 0, MODE_FQ = 1 };
+/* Format options (container version 2): BFPE groups of 8 samples (Sec. 6
+ * bit packer, "groups of 4 or 8"); the sum stream u_i = q_i + q_{i-1} as a
+ * fourth choice of the redundancy remover (Sec. 6 signal monitor, Sec. 5
+ * Fig. 3b: data near the Nyquist frequency alternate in sign). */
+enum { FMT_GROUP8 = 1, FMT_SUM_STREAM = 2, FMT_ALL = 3 };
 
 typedef __int128 i128;
 typedef unsigned __int128 u128;
@@ -65,13 +73,20 @@ typedef struct {
     int Q;         /* float quantiser precision: 23 (f32), 29 (f64) */
     int hbits;     /* block header bits: 32 (ints), 48 (floats) -- Sec. 6 */
     uint32_t N;    /* block size */
+    int fmt;       /* format options (FMT_*) */
+    int gs;        /* BFPE group size: 4, or 8 with FMT_GROUP8 */
+    int nstreams;  /* streams the redundancy remover compares: 3, or 4 with FMT_SUM_STREAM */
 } fmt_t;
 
-static int fmt_init(fmt_t *f, int dtype, uint32_t N)
+static int fmt_init(fmt_t *f, int dtype, uint32_t N, int fmt)
 {
     memset(f, 0, sizeof *f);
     f->dtype = dtype;
     f->N = N;
+    if (fmt & ~FMT_ALL) return ST_INVALID_ARG;
+    f->fmt = fmt;
+    f->gs = (fmt & FMT_GROUP8) ? 8 : 4;
+    f->nstreams = (fmt & FMT_SUM_STREAM) ? 4 : 3;
     switch (dtype) {
     case DT_I8:  f->size = 1; f->width = 8;  break;
     case DT_I16: f->size = 2; f->width = 16; break;
@@ -81,8 +96,9 @@ static int fmt_init(fmt_t *f, int dtype, uint32_t N)
     default: return ST_DTYPE;
     }
     f->hbits = f->isfloat ? 48 : 32;
-    /* Sec. 6: "block size between 64 and 16,384 (any multiple of 4)". */
-    if (N < 64 || N > 16384 || (N % 4) != 0) return ST_BLOCK_SIZE;
+    /* Sec. 6: "block size between 64 and 16,384 (any multiple of 4)"; with
+     * groups of 8 the block holds whole groups (a multiple of 8). */
+    if (N < 64 || N > 16384 || (N % (uint32_t)f->gs) != 0) return ST_BLOCK_SIZE;
     return ST_OK;
 }
 
@@ -279,26 +295,29 @@ static void dequantise_value(const fmt_t *F, int32_t q, int c, int Eb, void *y, 
 
 /* Streams (Sec. 5/6: the data and selected derivatives), within the block,
  * modulo 2^W:  S0 u_i = q_i;  S1 u_0 = q_0, u_i = q_i - q_{i-1};
- * S2 u_0 = q_0, u_1 = q_1 - q_0, u_i = q_i - 2 q_{i-1} + q_{i-2}. */
+ * S2 u_0 = q_0, u_1 = q_1 - q_0, u_i = q_i - 2 q_{i-1} + q_{i-2};
+ * S3 (sum stream) u_0 = q_0, u_i = q_i + q_{i-1}. */
 static void derive_stream(const int32_t *q, int len, int s, int W, int32_t *u)
 {
     for (int i = 0; i < len; ++i) {
         int64_t v;
         if (s == 0 || i == 0) v = q[i];
+        else if (s == 3) v = (int64_t)q[i] + q[i - 1];
         else if (s == 1 || i == 1) v = (int64_t)q[i] - q[i - 1];
         else v = (int64_t)q[i] - 2 * (int64_t)q[i - 1] + q[i - 2];
         u[i] = wrap_w(v, W);
     }
 }
 
-/* Group exponent (BFPE, N = 4): largest bits() of the group; a width of 31
- * is promoted to 32 so that every exponent fits the 5-bit absolute field. */
-static void group_exponents(const int32_t *u, int G, int *e)
+/* Group exponent (BFPE, groups of gs = 4 or 8): largest bits() of the
+ * group; a width of 31 is promoted to 32 so that every exponent fits the
+ * 5-bit absolute field. */
+static void group_exponents(const int32_t *u, int G, int gs, int *e)
 {
     for (int g = 0; g < G; ++g) {
         int b = 0;
-        for (int j = 0; j < 4; ++j) {
-            int t = bits_of(u[4 * g + j]);
+        for (int j = 0; j < gs; ++j) {
+            int t = bits_of(u[gs * g + j]);
             if (t > b) b = t;
         }
         e[g] = (b == 31) ? 32 : b;
@@ -413,46 +432,49 @@ typedef struct {
     int nnib;
 } blk_t;
 
-/* Quantise block j at code c: q[0..4G), the tail replicating q[L-1]. */
+/* Quantise block j at code c: q[0..gs G), the tail replicating q[L-1]. */
 static int quantise_block(const fmt_t *F, const void *x, uint64_t n, uint64_t j, int c, blk_t *b)
 {
     uint64_t off = j * F->N;
     uint64_t rem = n - off;
     b->L = (int)(rem < F->N ? rem : F->N);
-    b->G = (b->L + 3) / 4;
+    b->G = (b->L + F->gs - 1) / F->gs;
     b->Eb = 0;
     if (F->isfloat) {
         int st = block_exponent(F, x, off, b->L, &b->Eb);
         if (st) return st;
     }
     for (int i = 0; i < b->L; ++i) b->q[i] = quantise_value(F, x, off + i, c, b->Eb);
-    for (int i = b->L; i < 4 * b->G; ++i) b->q[i] = b->q[b->L - 1];
+    for (int i = b->L; i < F->gs * b->G; ++i) b->q[i] = b->q[b->L - 1];
     return ST_OK;
 }
 
 /* Unpadded packet bits of the quantised block b with stream s. */
 static uint64_t packet_bits(const fmt_t *F, blk_t *b, int s)
 {
-    derive_stream(b->q, 4 * b->G, s, F->width, b->u);
-    group_exponents(b->u, b->G, b->e);
+    derive_stream(b->q, F->gs * b->G, s, F->width, b->u);
+    group_exponents(b->u, b->G, F->gs, b->e);
     b->nnib = jee_encode(b->e, b->G, b->nib);
     uint64_t bits = (uint64_t)F->hbits + 4u * (uint64_t)b->nnib;
-    for (int g = 0; g < b->G; ++g) bits += 4u * (uint64_t)b->e[g];
+    for (int g = 0; g < b->G; ++g) bits += (uint64_t)F->gs * (uint64_t)b->e[g];
     return bits;
 }
 
 static uint64_t pad32_bytes(uint64_t bits) { return 4 * ((bits + 31) / 32); }
 
 /* best(j): the stream with the fewest packet bits at code 0 (ties to the
- * lower index).  Sec. 6: the redundancy remover "determines which of the
- * numeric streams ... encodes using the fewest bits". */
+ * lower index) among S0..S2, and S3 with the sum-stream option.  Sec. 6: the
+ * redundancy remover keeps whichever candidate stream packs into the fewest
+ * bits; the signal monitor's say over which neighbours are correlated is
+ * read as offering the sum stream, which the same fewest-bits rule takes
+ * exactly when it is the smallest. */
 static int best_stream(const fmt_t *F, const void *x, uint64_t n, uint64_t j, blk_t *b, int *st)
 {
     *st = quantise_block(F, x, n, j, 0, b);
     if (*st) return 0;
     int best = 0;
     uint64_t bb = packet_bits(F, b, 0);
-    for (int s = 1; s < 3; ++s) {
+    for (int s = 1; s < F->nstreams; ++s) {
         uint64_t t = packet_bits(F, b, s);
         if (t < bb) { bb = t; best = s; }
     }
@@ -472,9 +494,9 @@ static void write_packet(const fmt_t *F, blk_t *b, int s, int c, uint8_t *out, u
     if (F->isfloat) put_bits(&w, (uint64_t)(uint16_t)(int16_t)b->Eb, 16);
     for (int t = 0; t < b->nnib; ++t) put_bits(&w, b->nib[t], 4);
     for (int g = 0; g < b->G; ++g)
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < F->gs; ++i) {
             int e = b->e[g];
-            uint64_t v = (uint64_t)(uint32_t)b->u[4 * g + i];
+            uint64_t v = (uint64_t)(uint32_t)b->u[F->gs * g + i];
             if (e < 64) v &= (e == 0) ? 0 : (((uint64_t)1 << e) - 1);
             put_bits(&w, v, e);
         }
@@ -485,7 +507,7 @@ static void write_packet(const fmt_t *F, blk_t *b, int s, int c, uint8_t *out, u
 /* ------------------------------------------------------------------------ */
 static uint64_t min_packet(const fmt_t *F, int L)
 {
-    int G = (L + 3) / 4;
+    int G = (L + F->gs - 1) / F->gs;
     uint64_t bits = (uint64_t)F->hbits + 8 + 4 * (uint64_t)((G - 1 + 1) / 2);
     return pad32_bytes(bits);
 }
@@ -536,11 +558,11 @@ static int check_params(const fmt_t *F, int mode, uint32_t num, uint32_t den, in
 /* ------------------------------------------------------------------------ */
 
 /* Fixed rate: the exact size; fixed quality: the worst-case bound. */
-int oracle_encoded_size(int dtype, uint64_t n, uint32_t N, int mode, uint32_t num,
+int oracle_encoded_size(int dtype, uint64_t n, uint32_t N, int fmt, int mode, uint32_t num,
                         uint32_t den, int c, uint64_t *bytes)
 {
     fmt_t F;
-    int st = fmt_init(&F, dtype, N);
+    int st = fmt_init(&F, dtype, N, fmt);
     if (st) return st;
     st = check_params(&F, mode, num, den, c);
     if (st) return st;
@@ -552,28 +574,29 @@ int oracle_encoded_size(int dtype, uint64_t n, uint32_t N, int mode, uint32_t nu
         *bytes = 40 + (nb - 1) * B + fr_budget(&F, (int)Lend, num, den);
     } else {
         uint64_t wmax = (uint64_t)F.width;
-        uint64_t full = pad32_bytes((uint64_t)F.hbits + 8ull * (N / 4) + wmax * N);
-        int Gl = (int)((Lend + 3) / 4);
-        uint64_t last = pad32_bytes((uint64_t)F.hbits + 8ull * Gl + wmax * 4ull * Gl);
+        uint64_t full = pad32_bytes((uint64_t)F.hbits + 8ull * (N / F.gs) + wmax * N);
+        int Gl = (int)((Lend + F.gs - 1) / F.gs);
+        uint64_t last = pad32_bytes((uint64_t)F.hbits + 8ull * Gl + wmax * (uint64_t)F.gs * Gl);
         *bytes = 40 + table_bytes(nb) + (nb - 1) * full + last;
     }
     return ST_OK;
 }
 
 /* Fixed-rate budget B of a full block and minimum packet (for tests). */
-int oracle_fr_budget(int dtype, uint32_t N, int L, uint32_t num, uint32_t den, uint64_t *B)
+int oracle_fr_budget(int dtype, uint32_t N, int fmt, int L, uint32_t num, uint32_t den,
+                     uint64_t *B)
 {
     fmt_t F;
-    int st = fmt_init(&F, dtype, N);
+    int st = fmt_init(&F, dtype, N, fmt);
     if (st) return st;
     *B = fr_budget(&F, L, num, den);
     return ST_OK;
 }
 
-int oracle_min_packet(int dtype, uint32_t N, int L, uint64_t *bytes)
+int oracle_min_packet(int dtype, uint32_t N, int fmt, int L, uint64_t *bytes)
 {
     fmt_t F;
-    int st = fmt_init(&F, dtype, N);
+    int st = fmt_init(&F, dtype, N, fmt);
     if (st) return st;
     *bytes = min_packet(&F, L);
     return ST_OK;
@@ -583,19 +606,21 @@ int oracle_min_packet(int dtype, uint32_t N, int L, uint64_t *bytes)
 /* Exported: encoder                                                         */
 /* ------------------------------------------------------------------------ */
 
-/* The 40-byte container header (reading 11): magic "APX1", version 1,
- * dtype, mode, flags (bit 0: offset table), N, the fixed-quality code, the
+/* The 40-byte container header (reading 11): magic "APX1", version (1; 2
+ * when a format option is on), dtype, mode, flags (bit 0: offset table;
+ * bit 1: groups of 8; bit 2: sum stream), N, the fixed-quality code, the
  * fixed-rate budget B, n; the payload size at bytes 28..35 is written once
  * the packets are placed. */
-static void write_container_header(uint8_t *out, int dtype, uint32_t N, int mode, int cfq,
+static void write_container_header(uint8_t *out, const fmt_t *F, int mode, int cfq,
                                    uint64_t B, uint64_t n)
 {
     memset(out, 0, 40);
     out[0] = 'A'; out[1] = 'P'; out[2] = 'X'; out[3] = '1';
-    out[4] = 1;
-    out[5] = (uint8_t)dtype;
+    out[4] = F->fmt ? 2 : 1;
+    out[5] = (uint8_t)F->dtype;
     out[6] = (uint8_t)mode;
-    out[7] = (mode == MODE_FQ) ? 1 : 0;
+    out[7] = (uint8_t)(((mode == MODE_FQ) ? 1 : 0) | (F->fmt << 1));
+    const uint32_t N = F->N;
     put_le(out + 8, N, 4);
     put_le(out + 12, mode == MODE_FQ ? (uint64_t)cfq : 0, 2);
     put_le(out + 16, B, 4);
@@ -625,7 +650,8 @@ static int fr_bisect(const fmt_t *F, const void *x, uint64_t n, uint64_t j, int 
 /* Fixed-rate search, policy PREDICT (the adaptive loop of Sec. 6 read as a
  * prediction from the code-0 packet, then a short walk up a ladder of codes).
  * Attenuating by 2^-k narrows every group of exponent e by min(e, k) bits,
- * so red(k) = 4 sum_g min(e_g, k) bits are predicted to go; with the excess
+ * so red(k) = gs sum_g min(e_g, k) bits are predicted to go (gs samples per
+ * group); with the excess
  * D = packet_bits(0) - 8 B_j, k1 is the least k in 1..31 with red(k) >= D
  * (31 if none), and the fraction f = ceil(16 (D - red(k1-1)) /
  * (red(k1) - red(k1-1))) clamped to 1..16 (16 if the denominator is 0)
@@ -658,7 +684,7 @@ static int fr_predict(const fmt_t *F, const void *x, uint64_t n, uint64_t j, int
     red[0] = 0;
     for (int k = 1; k < 32; ++k) {
         int64_t r = 0;
-        for (int g = 0; g < b->G; ++g) r += 4 * (int64_t)(b->e[g] < k ? b->e[g] : k);
+        for (int g = 0; g < b->G; ++g) r += F->gs * (int64_t)(b->e[g] < k ? b->e[g] : k);
         red[k] = r;
     }
     int k1 = 31;
@@ -692,18 +718,19 @@ static int fr_search(const fmt_t *F, const void *x, uint64_t n, uint64_t j, int 
                                     : fr_bisect(F, x, n, j, s, budget, b, st);
 }
 
-int oracle_encode_s(const void *x, int dtype, uint64_t n, uint32_t N, int mode, uint32_t num,
-                    uint32_t den, int cfq, int search, uint8_t *out, uint64_t cap, uint64_t *bytes)
+int oracle_encode_s(const void *x, int dtype, uint64_t n, uint32_t N, int fmt, int mode,
+                    uint32_t num, uint32_t den, int cfq, int search, uint8_t *out, uint64_t cap,
+                    uint64_t *bytes)
 {
     fmt_t F;
-    int st = fmt_init(&F, dtype, N);
+    int st = fmt_init(&F, dtype, N, fmt);
     if (st) return st;
     st = check_params(&F, mode, num, den, cfq);
     if (st) return st;
     uint64_t nb = nblocks_of(n, N);
     if (cap < 40) return ST_CAPACITY;
     uint64_t B = (mode == MODE_FR) ? fr_budget(&F, (int)N, num, den) : 0;
-    write_container_header(out, dtype, N, mode, cfq, B, n);
+    write_container_header(out, &F, mode, cfq, B, n);
 
     blk_t *b = (blk_t *)malloc(sizeof(blk_t));
     if (!b) return ST_INVALID_ARG;
@@ -750,7 +777,7 @@ int oracle_encode_s(const void *x, int dtype, uint64_t n, uint32_t N, int mode, 
 int oracle_encode(const void *x, int dtype, uint64_t n, uint32_t N, int mode, uint32_t num,
                   uint32_t den, int cfq, uint8_t *out, uint64_t cap, uint64_t *bytes)
 {
-    return oracle_encode_s(x, dtype, n, N, mode, num, den, cfq, SEARCH_BISECT, out, cap, bytes);
+    return oracle_encode_s(x, dtype, n, N, 0, mode, num, den, cfq, SEARCH_BISECT, out, cap, bytes);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -765,7 +792,7 @@ static int decode_packet(const fmt_t *F, const uint8_t *p, uint64_t avail, int L
     uint64_t v;
     if (get_bits(&r, 2, &v)) return ST_CORRUPT;
     int s = (int)v;
-    if (s == 3) return ST_CORRUPT;
+    if (s >= F->nstreams) return ST_CORRUPT; /* S3 only with the sum-stream option */
     if (get_bits(&r, 12, &v)) return ST_CORRUPT;
     int c = (int)v;
     if (get_bits(&r, 18, &v)) return ST_CORRUPT;
@@ -777,7 +804,8 @@ static int decode_packet(const fmt_t *F, const uint8_t *p, uint64_t avail, int L
         if (get_bits(&r, 16, &v)) return ST_CORRUPT;
         Eb = (int16_t)(uint16_t)v;
     }
-    int G = (L + 3) / 4;
+    const int gs = F->gs;
+    int G = (L + gs - 1) / gs;
     /* token section: read nibbles lazily through a small buffer */
     int maxnib = (int)((r.end - r.bit) / 4);
     if (maxnib > 2 * G) maxnib = 2 * G;
@@ -792,7 +820,7 @@ static int decode_packet(const fmt_t *F, const uint8_t *p, uint64_t avail, int L
     if (nn < 0) return ST_CORRUPT;
     r.bit += 4ull * nn;
     for (int g = 0; g < G; ++g)
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < gs; ++i) {
             int e = b->e[g];
             uint64_t m = 0;
             if (e > 0 && get_bits(&r, e, &m)) return ST_CORRUPT;
@@ -801,13 +829,14 @@ static int decode_packet(const fmt_t *F, const uint8_t *p, uint64_t avail, int L
                 sv = (int64_t)m;
                 if ((m >> (e - 1)) & 1) sv -= (int64_t)1 << e;
             }
-            b->u[4 * g + i] = wrap_w(sv, F->width);
+            b->u[gs * g + i] = wrap_w(sv, F->width);
         }
     /* inverse streams, modulo 2^W */
-    int n4 = 4 * G;
-    for (int i = 0; i < n4; ++i) {
+    int ng = gs * G;
+    for (int i = 0; i < ng; ++i) {
         int64_t qv;
         if (s == 0 || i == 0) qv = b->u[i];
+        else if (s == 3) qv = (int64_t)b->u[i] - b->q[i - 1];
         else if (s == 1 || i == 1) qv = (int64_t)b->u[i] + b->q[i - 1];
         else qv = (int64_t)b->u[i] + 2 * (int64_t)b->q[i - 1] - b->q[i - 2];
         b->q[i] = wrap_w(qv, F->width);
@@ -827,14 +856,17 @@ typedef struct {
 static int parse_container(const uint8_t *in, uint64_t in_bytes, int dtype, uint64_t n, cont_t *c)
 {
     if (in_bytes < 40) return ST_CORRUPT;
-    if (in[0] != 'A' || in[1] != 'P' || in[2] != 'X' || in[3] != '1' || in[4] != 1)
+    if (in[0] != 'A' || in[1] != 'P' || in[2] != 'X' || in[3] != '1') return ST_CORRUPT;
+    /* version 1: no format option; version 2: at least one (flags bits 1-2) */
+    const int fmt = (in[7] >> 1) & 0x7f;
+    if (!((in[4] == 1 && fmt == 0) || (in[4] == 2 && fmt != 0 && fmt <= FMT_ALL)))
         return ST_CORRUPT;
     if (in[5] != dtype) return ST_INVALID_ARG;
     c->mode = in[6];
     uint32_t N = (uint32_t)get_le(in + 8, 4);
     uint64_t hn = get_le(in + 20, 8);
     if (hn != n) return ST_INVALID_ARG;
-    if (fmt_init(&c->F, dtype, N)) return ST_CORRUPT;
+    if (fmt_init(&c->F, dtype, N, fmt)) return ST_CORRUPT;
     if (c->mode != MODE_FR && c->mode != MODE_FQ) return ST_CORRUPT;
     c->B = get_le(in + 16, 4);
     c->payload = get_le(in + 28, 8);
@@ -1014,7 +1046,7 @@ int oracle_block_sums(const void *x, const void *y, int dtype, uint64_t n, uint3
                       uint64_t b0, uint64_t b1, double *out)
 {
     fmt_t F;
-    int st = fmt_init(&F, dtype, N);
+    int st = fmt_init(&F, dtype, N, 0); /* the sums do not depend on the packet format */
     if (st) return st;
     for (uint64_t j = b0; j < b1; ++j) {
         uint64_t off = j * N;
@@ -1028,7 +1060,7 @@ int oracle_block_sums(const void *x, const void *y, int dtype, uint64_t n, uint3
 int oracle_metrics(const void *x, const void *y, int dtype, uint64_t n, uint32_t N, double *out)
 {
     fmt_t F;
-    int st = fmt_init(&F, dtype, N);
+    int st = fmt_init(&F, dtype, N, 0);
     if (st) return st;
     uint64_t nb = nblocks_of(n, N);
     double *bs = (double *)malloc(sizeof(double) * 6 * (nb ? nb : 1));
@@ -1078,11 +1110,12 @@ typedef struct {
  * recommended
  * point is the largest i with r_j >= target for all j <= i (candidates in
  * increasing attenuation); 0 if even r_0 misses the target. */
-int oracle_profile(const void *x, int dtype, uint64_t n, uint32_t N, const uint16_t *cand,
-                   int ncand, double target, oracle_point *pts, int *recommended)
+int oracle_profile(const void *x, int dtype, uint64_t n, uint32_t N, int fmt,
+                   const uint16_t *cand, int ncand, double target, oracle_point *pts,
+                   int *recommended)
 {
     fmt_t F;
-    int st = fmt_init(&F, dtype, N);
+    int st = fmt_init(&F, dtype, N, fmt);
     if (st) return st;
     if (ncand < 1) return ST_INVALID_ARG;
     for (int i = 0; i < ncand; ++i) {
@@ -1090,14 +1123,15 @@ int oracle_profile(const void *x, int dtype, uint64_t n, uint32_t N, const uint1
         if (i > 0 && cand[i] <= cand[i - 1]) return ST_INVALID_ARG;
     }
     uint64_t cap;
-    st = oracle_encoded_size(dtype, n, N, MODE_FQ, 1, 1, 0, &cap);
+    st = oracle_encoded_size(dtype, n, N, fmt, MODE_FQ, 1, 1, 0, &cap);
     if (st) return st;
     uint8_t *buf = (uint8_t *)malloc(cap);
     void *y = malloc((size_t)(n ? n : 1) * F.size);
     int rec = -1, ok_prefix = 1;
     for (int i = 0; i < ncand; ++i) {
         uint64_t bytes;
-        st = oracle_encode(x, dtype, n, N, MODE_FQ, 1, 1, cand[i], buf, cap, &bytes);
+        st = oracle_encode_s(x, dtype, n, N, fmt, MODE_FQ, 1, 1, cand[i], SEARCH_BISECT, buf,
+                             cap, &bytes);
         if (st) break;
         st = oracle_decode(buf, bytes, y, dtype, n);
         if (st) break;
@@ -1139,7 +1173,7 @@ int oracle_jee_decode(const uint8_t *nib, int maxnib, int G, int *e)
 int32_t oracle_quantise(const void *x, int dtype, uint64_t i, int c, int Eb)
 {
     fmt_t F;
-    if (fmt_init(&F, dtype, 64)) return 0;
+    if (fmt_init(&F, dtype, 64, 0)) return 0;
     return quantise_value(&F, x, i, c, Eb);
 }
 
@@ -1147,7 +1181,7 @@ int32_t oracle_quantise(const void *x, int dtype, uint64_t i, int c, int Eb)
 int oracle_dequantise(int32_t q, int dtype, int c, int Eb, void *y)
 {
     fmt_t F;
-    int st = fmt_init(&F, dtype, 64);
+    int st = fmt_init(&F, dtype, 64, 0);
     if (st) return st;
     dequantise_value(&F, q, c, Eb, y, 0);
     return ST_OK;
@@ -1156,17 +1190,17 @@ int oracle_dequantise(int32_t q, int dtype, int c, int Eb, void *y)
 int oracle_block_exponent(const void *x, int dtype, uint64_t off, int L, int *Eb)
 {
     fmt_t F;
-    int st = fmt_init(&F, dtype, 64);
+    int st = fmt_init(&F, dtype, 64, 0);
     if (st) return st;
     return block_exponent(&F, x, off, L, Eb);
 }
 
 /* Unpadded packet bits of block j at code c with stream s (tests). */
-int oracle_packet_bits(const void *x, int dtype, uint64_t n, uint32_t N, uint64_t j, int c,
-                       int s, uint64_t *bits)
+int oracle_packet_bits(const void *x, int dtype, uint64_t n, uint32_t N, int fmt, uint64_t j,
+                       int c, int s, uint64_t *bits)
 {
     fmt_t F;
-    int st = fmt_init(&F, dtype, N);
+    int st = fmt_init(&F, dtype, N, fmt);
     if (st) return st;
     blk_t *b = (blk_t *)malloc(sizeof(blk_t));
     st = quantise_block(&F, x, n, j, c, b);
@@ -1176,11 +1210,11 @@ int oracle_packet_bits(const void *x, int dtype, uint64_t n, uint32_t N, uint64_
 }
 
 /* Streams chosen for blocks [b0, b1) (the one-block lag of Sec. 6). */
-int oracle_streams(const void *x, int dtype, uint64_t n, uint32_t N, uint64_t b0, uint64_t b1,
-                   int *streams)
+int oracle_streams(const void *x, int dtype, uint64_t n, uint32_t N, int fmt, uint64_t b0,
+                   uint64_t b1, int *streams)
 {
     fmt_t F;
-    int st = fmt_init(&F, dtype, N);
+    int st = fmt_init(&F, dtype, N, fmt);
     if (st) return st;
     blk_t *b = (blk_t *)malloc(sizeof(blk_t));
     for (uint64_t j = b0; j < b1; ++j) {
@@ -1193,11 +1227,11 @@ int oracle_streams(const void *x, int dtype, uint64_t n, uint32_t N, uint64_t b0
 }
 
 /* Fixed-rate code that the search picks for block j given stream s. */
-int oracle_fr_code(const void *x, int dtype, uint64_t n, uint32_t N, uint64_t j, int s,
-                   uint64_t budget, int search, int *code)
+int oracle_fr_code(const void *x, int dtype, uint64_t n, uint32_t N, int fmt, uint64_t j,
+                   int s, uint64_t budget, int search, int *code)
 {
     fmt_t F;
-    int st = fmt_init(&F, dtype, N);
+    int st = fmt_init(&F, dtype, N, fmt);
     if (st) return st;
     blk_t *b = (blk_t *)malloc(sizeof(blk_t));
     *code = fr_search(&F, x, n, j, s, budget, b, &st, search);
@@ -1209,12 +1243,12 @@ int oracle_fr_code(const void *x, int dtype, uint64_t n, uint32_t N, uint64_t j,
  * written back to back into out (for sampled parity at full size).  For
  * fixed rate, the packets are padded to their budgets; for fixed quality to
  * 32 bits.  lens[j-b0] receives each packet length. */
-int oracle_encode_blocks(const void *x, int dtype, uint64_t n, uint32_t N, int mode,
+int oracle_encode_blocks(const void *x, int dtype, uint64_t n, uint32_t N, int fmt, int mode,
                          uint32_t num, uint32_t den, int cfq, int search, uint64_t b0,
                          uint64_t b1, uint8_t *out, uint64_t cap, uint64_t *lens)
 {
     fmt_t F;
-    int st = fmt_init(&F, dtype, N);
+    int st = fmt_init(&F, dtype, N, fmt);
     if (st) return st;
     st = check_params(&F, mode, num, den, cfq);
     if (st) return st;
@@ -1322,7 +1356,7 @@ int oracle_threads(int threads) { return mt_threads(threads, (uint64_t)1 << 40);
 typedef struct {
     /* encode */
     const void *x;
-    int dtype, mode, cfq, search;
+    int dtype, fmt, mode, cfq, search;
     uint64_t n;
     uint32_t N, num, den;
     uint64_t b0, b1;
@@ -1342,8 +1376,8 @@ typedef struct {
 static void *enc_worker(void *p)
 {
     mt_job *J = (mt_job *)p;
-    J->st = oracle_encode_blocks(J->x, J->dtype, J->n, J->N, J->mode, J->num, J->den, J->cfq,
-                                 J->search, J->b0, J->b1, J->buf, J->cap, J->lens);
+    J->st = oracle_encode_blocks(J->x, J->dtype, J->n, J->N, J->fmt, J->mode, J->num, J->den,
+                                 J->cfq, J->search, J->b0, J->b1, J->buf, J->cap, J->lens);
     return NULL;
 }
 
@@ -1390,19 +1424,19 @@ static void mt_split(mt_job *jobs, int T, uint64_t nb)
 }
 
 /* oracle_encode, block ranges on `threads` threads. */
-int oracle_encode_mt(const void *x, int dtype, uint64_t n, uint32_t N, int mode, uint32_t num,
-                     uint32_t den, int cfq, int search, uint8_t *out, uint64_t cap,
+int oracle_encode_mt(const void *x, int dtype, uint64_t n, uint32_t N, int fmt, int mode,
+                     uint32_t num, uint32_t den, int cfq, int search, uint8_t *out, uint64_t cap,
                      uint64_t *bytes, int threads)
 {
     fmt_t F;
-    int st = fmt_init(&F, dtype, N);
+    int st = fmt_init(&F, dtype, N, fmt);
     if (st) return st;
     st = check_params(&F, mode, num, den, cfq);
     if (st) return st;
     const uint64_t nb = nblocks_of(n, N);
     if (cap < 40) return ST_CAPACITY;
     const uint64_t B = (mode == MODE_FR) ? fr_budget(&F, (int)N, num, den) : 0;
-    write_container_header(out, dtype, N, mode, cfq, B, n);
+    write_container_header(out, &F, mode, cfq, B, n);
     const uint64_t payload_off = 40 + ((mode == MODE_FQ) ? table_bytes(nb) : 0);
     if (payload_off > cap) return ST_CAPACITY;
     if (mode == MODE_FQ) memset(out + 40, 0, payload_off - 40);
@@ -1411,7 +1445,7 @@ int oracle_encode_mt(const void *x, int dtype, uint64_t n, uint32_t N, int mode,
      * the full width (the worst case the size bound also uses) */
     const uint64_t maxp = mode == MODE_FR
                               ? fr_budget(&F, (int)N, num, den)
-                              : pad32_bytes((uint64_t)F.hbits + 8ull * (N / 4) + (uint64_t)F.width * N);
+                              : pad32_bytes((uint64_t)F.hbits + 8ull * (N / F.gs) + (uint64_t)F.width * N);
     mt_job jobs[256];
     memset(jobs, 0, sizeof jobs);
     mt_split(jobs, T, nb);
@@ -1419,7 +1453,7 @@ int oracle_encode_mt(const void *x, int dtype, uint64_t n, uint32_t N, int mode,
     int fail = lens == NULL;
     for (int i = 0; i < T && !fail; ++i) {
         mt_job *J = &jobs[i];
-        J->x = x; J->dtype = dtype; J->n = n; J->N = N; J->mode = mode;
+        J->x = x; J->dtype = dtype; J->fmt = fmt; J->n = n; J->N = N; J->mode = mode;
         J->num = num; J->den = den; J->cfq = cfq; J->search = search;
         J->cap = maxp * (J->b1 - J->b0);
         /* the last block's fixed-rate budget may exceed B (minimum packet) */
@@ -1488,7 +1522,7 @@ int oracle_metrics_mt(const void *x, const void *y, int dtype, uint64_t n, uint3
                       double *out, int threads)
 {
     fmt_t F;
-    int st = fmt_init(&F, dtype, N);
+    int st = fmt_init(&F, dtype, N, 0);
     if (st) return st;
     const uint64_t nb = nblocks_of(n, N);
     double *bs = (double *)malloc(sizeof(double) * 6 * (nb ? nb : 1));
@@ -1521,11 +1555,12 @@ int oracle_metrics_mt(const void *x, const void *y, int dtype, uint64_t n, uint3
 }
 
 /* oracle_profile with the threaded encode, decode and sums. */
-int oracle_profile_mt(const void *x, int dtype, uint64_t n, uint32_t N, const uint16_t *cand,
-                      int ncand, double target, oracle_point *pts, int *recommended, int threads)
+int oracle_profile_mt(const void *x, int dtype, uint64_t n, uint32_t N, int fmt,
+                      const uint16_t *cand, int ncand, double target, oracle_point *pts,
+                      int *recommended, int threads)
 {
     fmt_t F;
-    int st = fmt_init(&F, dtype, N);
+    int st = fmt_init(&F, dtype, N, fmt);
     if (st) return st;
     if (ncand < 1) return ST_INVALID_ARG;
     for (int i = 0; i < ncand; ++i) {
@@ -1533,7 +1568,7 @@ int oracle_profile_mt(const void *x, int dtype, uint64_t n, uint32_t N, const ui
         if (i > 0 && cand[i] <= cand[i - 1]) return ST_INVALID_ARG;
     }
     uint64_t cap;
-    st = oracle_encoded_size(dtype, n, N, MODE_FQ, 1, 1, 0, &cap);
+    st = oracle_encoded_size(dtype, n, N, fmt, MODE_FQ, 1, 1, 0, &cap);
     if (st) return st;
     uint8_t *buf = (uint8_t *)malloc(cap);
     void *y = malloc((size_t)(n ? n : 1) * F.size);
@@ -1545,8 +1580,8 @@ int oracle_profile_mt(const void *x, int dtype, uint64_t n, uint32_t N, const ui
     int rec = -1, ok_prefix = 1;
     for (int i = 0; i < ncand; ++i) {
         uint64_t bytes;
-        st = oracle_encode_mt(x, dtype, n, N, MODE_FQ, 1, 1, cand[i], SEARCH_BISECT, buf, cap,
-                              &bytes, threads);
+        st = oracle_encode_mt(x, dtype, n, N, fmt, MODE_FQ, 1, 1, cand[i], SEARCH_BISECT, buf,
+                              cap, &bytes, threads);
         if (st) break;
         st = oracle_decode_mt(buf, bytes, y, dtype, n, threads);
         if (st) break;

@@ -5,8 +5,9 @@ reading, used only to cross-check the C oracle on small random arrays.  It
 rounds with exact rationals (``fractions.Fraction``) and assembles packets as
 one big Python integer, where the oracle uses integer shifts and a bit
 writer.  Paper passages: Sec. 6 (blocks, attenuator, redundancy remover,
-one-block-lag stream decision, 4/6-byte headers, BFPE groups of 4 and JEE
-tokens) and Sec. 4 (profiler formula).
+one-block-lag stream decision, 4/6-byte headers, BFPE groups of 4 or 8 and
+JEE tokens; the sum stream of the second container version) and Sec. 4
+(profiler formula).
 """
 from __future__ import annotations
 
@@ -74,13 +75,14 @@ def streams(q, W):
         else:
             v = q[i] - 2 * q[i - 1] + q[i - 2]
         s2.append(signed_w(v, W))
-    return [s0, s1, s2]
+    s3 = [signed_w(q[i] + (q[i - 1] if i else 0), W) for i in range(n)]
+    return [s0, s1, s2, s3]
 
 
-def exps(u):
+def exps(u, gs=4):
     out = []
-    for g in range(len(u) // 4):
-        e = max(nbits(v) for v in u[4 * g:4 * g + 4])
+    for g in range(len(u) // gs):
+        e = max(nbits(v) for v in u[gs * g:gs * g + gs])
         out.append(32 if e == 31 else e)
     return out
 
@@ -106,13 +108,13 @@ def tokens(e):
     return nib
 
 
-def pkt_bits(u, H):
-    e = exps(u)
-    return H + 4 * len(tokens(e)) + 4 * sum(e)
+def pkt_bits(u, H, gs=4):
+    e = exps(u, gs)
+    return H + 4 * len(tokens(e)) + gs * sum(e)
 
 
-def build_packet(u, s, c, Eb, H, plen):
-    e = exps(u)
+def build_packet(u, s, c, Eb, H, plen, gs=4):
+    e = exps(u, gs)
     val, pos = 0, 0
 
     def put(v, n):
@@ -128,7 +130,7 @@ def build_packet(u, s, c, Eb, H, plen):
     for t in tokens(e):
         put(t, 4)
     for g, eg in enumerate(e):
-        for v in u[4 * g:4 * g + 4]:
+        for v in u[gs * g:gs * g + gs]:
             if eg:
                 put(v, eg)
     return val.to_bytes(plen, "little")
@@ -138,27 +140,28 @@ def _blocks(x, N):
     return [x[j:j + N] for j in range(0, len(x), N)]
 
 
-def _padded_q(xb, dt, c, Eb):
+def _padded_q(xb, dt, c, Eb, gs=4):
     q = quant(xb, dt, c, Eb)
-    G = (len(q) + 3) // 4
-    return q + [q[-1]] * (4 * G - len(q))
+    G = -(-len(q) // gs)
+    return q + [q[-1]] * (gs * G - len(q))
 
 
-def _best(xb, dt):
+def _best(xb, dt, gs=4, ns=3):
+    """Fewest bits at code 0 among the first ns streams (ties to the lower)."""
     W, H = INFO[dt][2], INFO[dt][4]
     Eb = block_exp(xb) if INFO[dt][3] else 0
-    q = _padded_q(xb, dt, 0, Eb)
-    sizes = [pkt_bits(u, H) for u in streams(q, W)]
+    q = _padded_q(xb, dt, 0, Eb, gs)
+    sizes = [pkt_bits(u, H, gs) for u in streams(q, W)[:ns]]
     return sizes.index(min(sizes))
 
 
-def minpacket(L, H):
-    G = (L + 3) // 4
+def minpacket(L, H, gs=4):
+    G = -(-L // gs)
     return 4 * -(-(H + 8 + 4 * ((G - 1 + 1) // 2)) // 32)
 
 
-def budget(L, size, num, den, H):
-    return max((L * size * den // (4 * num)) * 4, minpacket(L, H))
+def budget(L, size, num, den, H, gs=4):
+    return max((L * size * den // (4 * num)) * 4, minpacket(L, H, gs))
 
 
 LADDER_M = [0, 11, 21, 31, 41, 50, 59, 67, 75, 83, 90, 97, 104, 110, 116, 122]
@@ -169,18 +172,18 @@ def ladder():
     return sorted({128 * k + m for k in range(32) for m in LADDER_M}) + [4095]
 
 
-def predict_start(xb, dt, s, bud):
+def predict_start(xb, dt, s, bud, gs=4):
     """PREDICT's start code on one block (None when code 0 fits): the excess
     bits over the budget at code 0 against the bits predicted to go at
     attenuation 2^-k, interpolated between two powers of two."""
     W, H = INFO[dt][2], INFO[dt][4]
     Eb = block_exp(xb) if INFO[dt][3] else 0
-    b0 = pkt_bits(streams(_padded_q(xb, dt, 0, Eb), W)[s], H)
+    b0 = pkt_bits(streams(_padded_q(xb, dt, 0, Eb, gs), W)[s], H, gs)
     if 4 * -(-b0 // 32) <= bud:
         return None
-    e = exps(streams(_padded_q(xb, dt, 0, Eb), W)[s])
+    e = exps(streams(_padded_q(xb, dt, 0, Eb, gs), W)[s], gs)
     D = b0 - 8 * bud
-    red = [4 * sum(min(v, k) for v in e) for k in range(32)]
+    red = [gs * sum(min(v, k) for v in e) for k in range(32)]
     k1 = next((k for k in range(1, 32) if red[k] >= D), 31)
     num, den = 16 * (D - red[k1 - 1]), red[k1] - red[k1 - 1]
     f = 16 if den == 0 else -(-num // den)
@@ -188,16 +191,16 @@ def predict_start(xb, dt, s, bud):
     return 128 * (k1 - 1) + LADDER_M[f] if f < 16 else 128 * k1
 
 
-def predict_code(xb, dt, s, bud):
+def predict_code(xb, dt, s, bud, gs=4):
     """PREDICT fixed-rate search on one block: code 0 if it fits, else up
     the ladder from the predicted start until the packet fits."""
     W, H = INFO[dt][2], INFO[dt][4]
     Eb = block_exp(xb) if INFO[dt][3] else 0
 
     def bits_at(cc):
-        return pkt_bits(streams(_padded_q(xb, dt, cc, Eb), W)[s], H)
+        return pkt_bits(streams(_padded_q(xb, dt, cc, Eb, gs), W)[s], H, gs)
 
-    c = predict_start(xb, dt, s, bud)
+    c = predict_start(xb, dt, s, bud, gs)
     if c is None:
         return 0
     lad = ladder()
@@ -207,34 +210,38 @@ def predict_code(xb, dt, s, bud):
     return lad[i]
 
 
-def encode(x: np.ndarray, N: int, mode: int, num=1, den=1, code=0, search=0) -> bytes:
+def encode(x: np.ndarray, N: int, mode: int, num=1, den=1, code=0, search=0, fmt=0) -> bytes:
+    """fmt bit 0: groups of 8; bit 1: the sum stream (either makes a
+    version-2 container)."""
     dt = x.dtype
     code_dt, size, W, Q, H = INFO[dt]
+    gs = 8 if fmt & 1 else 4
+    ns = 4 if fmt & 2 else 3
     x = list(x.reshape(-1).tolist())
     n = len(x)
     blocks = _blocks(x, N)
     nb = len(blocks)
-    best = [_best(b, dt) for b in blocks]
+    best = [_best(b, dt, gs, ns) for b in blocks]
     packets = []
-    B = budget(N, size, num, den, H) if mode == 0 else 0
+    B = budget(N, size, num, den, H, gs) if mode == 0 else 0
     for j, xb in enumerate(blocks):
         s = best[0] if j == 0 else best[j - 1]
         Eb = block_exp(xb) if Q else 0
         if mode == 1:
             c = code
-            u = streams(_padded_q(xb, dt, c, Eb), W)[s]
-            plen = 4 * -(-pkt_bits(u, H) // 32)
+            u = streams(_padded_q(xb, dt, c, Eb, gs), W)[s]
+            plen = 4 * -(-pkt_bits(u, H, gs) // 32)
         else:
-            bud = budget(len(xb), size, num, den, H)
+            bud = budget(len(xb), size, num, den, H, gs)
             if search == 1:
-                c = predict_code(xb, dt, s, bud)
-                u = streams(_padded_q(xb, dt, c, Eb), W)[s]
-                packets.append(build_packet(u, s, c, Eb, H, bud))
+                c = predict_code(xb, dt, s, bud, gs)
+                u = streams(_padded_q(xb, dt, c, Eb, gs), W)[s]
+                packets.append(build_packet(u, s, c, Eb, H, bud, gs))
                 continue
 
             def fits(cc):
-                uu = streams(_padded_q(xb, dt, cc, Eb), W)[s]
-                return 4 * -(-pkt_bits(uu, H) // 32) <= bud
+                uu = streams(_padded_q(xb, dt, cc, Eb, gs), W)[s]
+                return 4 * -(-pkt_bits(uu, H, gs) // 32) <= bud
             if fits(0):
                 c = 0
             else:
@@ -246,10 +253,10 @@ def encode(x: np.ndarray, N: int, mode: int, num=1, den=1, code=0, search=0) -> 
                     else:
                         lo = mid
                 c = hi
-            u = streams(_padded_q(xb, dt, c, Eb), W)[s]
+            u = streams(_padded_q(xb, dt, c, Eb, gs), W)[s]
             plen = bud
-        packets.append(build_packet(u, s, c, Eb, H, plen))
-    head = b"APX1" + bytes([1, code_dt, mode, 1 if mode == 1 else 0])
+        packets.append(build_packet(u, s, c, Eb, H, plen, gs))
+    head = b"APX1" + bytes([2 if fmt else 1, code_dt, mode, (1 if mode == 1 else 0) | (fmt << 1)])
     head += struct.pack("<IHHIQ", N, code if mode == 1 else 0, 0, B, n)
     payload = b"".join(packets)
     head += struct.pack("<Q", len(payload)) + b"\0" * 4
