@@ -405,7 +405,8 @@ def run_ours(args, rank, world, local_rank):
     if world == 1 and rank == 0 and not args.no_extra:
         # the other single-GPU workloads, measured in the same run
         line["workloads"] = {"sensor_i16_fr4": run_sensor(args, compact=True),
-                             "field3d_f64_512": run_field3d(args, compact=True)}
+                             "field3d_f64_512": run_field3d(args, compact=True),
+                             "formats_v2": run_formats(args)}
     return line
 
 
@@ -746,6 +747,63 @@ def run_field3d(args, compact=False):
         "ratio": round(xb / r.bytes, 4), "corr": pt.r, "recommended_code": int(sm.recommended_code),
         "peak_source": f"{peak_kind} hbm_gbs", "clocks": clk.summary(),
     }
+
+
+def run_formats(args):
+    """Container version 2 (BFPE groups of 8, the sum stream) against
+    version 1: the float32 4096x4096 field at fixed quality, code 2048 (the
+    code the profiler recommends for it), and 1,024 copies of the int16
+    Nyquist-band trace (512 MiB) lossless (code 0).  Bytes and device time of
+    one encode and one decode call per format."""
+    import torch
+
+    from paper_1303_4994_gb300 import apax as A
+    from paper_1303_4994_gb300 import build as B
+    from paper_1303_4994_gb300 import synth
+
+    B.build()
+    A.lib()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    names = {0: "v1", A.FORMAT_GROUP8: "group8", A.FORMAT_SUM_STREAM: "sum",
+             A.FORMAT_GROUP8 | A.FORMAT_SUM_STREAM: "group8_sum"}
+
+    def timed(fn):
+        return _median(_events(fn, max(args.steps, 20), stream))
+
+    def one(x, dc, code):
+        xb = x.numel() * x.element_size()
+        res = {}
+        for fmt, name in names.items():
+            p = A.params(N_BLOCK, A.FIXED_QUALITY, (1, 1), code, fmt=fmt)
+            out = torch.empty(A.encoded_size(dc, x.numel(), p), dtype=torch.uint8, device=dev)
+            ews = torch.empty(A.workspace_size(dc, x.numel(), p), dtype=torch.uint8, device=dev)
+            dws = torch.empty(A.decode_workspace_size(), dtype=torch.uint8, device=dev)
+            y = torch.empty_like(x)
+            er, dr = A.new_result(dev), A.new_result(dev)
+            for _ in range(max(args.warmup, 3)):
+                A.encode_into(x, p, out, ews, er, stream)
+                A.decode_into(out, y, dws, dr, stream)
+            torch.cuda.synchronize()
+            r = A.read_result(er)
+            assert r.status == 0 and A.read_result(dr).status == 0
+            assert torch.equal(y.view(torch.uint8), y.view(torch.uint8))
+            ms_e = timed(lambda: A.encode_into(x, p, out, ews, er, stream))
+            ms_d = timed(lambda: A.decode_into(out, y, dws, dr, stream))
+            res[name] = {"ratio": round(xb / r.bytes, 4),
+                         "encode_gbs_uncompressed": round(xb / ms_e / 1e6, 2),
+                         "decode_gbs_uncompressed": round(xb / ms_d / 1e6, 2)}
+        return res
+
+    field = torch.from_numpy(synth.grf2d(4096, 4096, seed=1).reshape(-1)).to(dev)
+    out = {"workload": "float32 4096x4096 field (seed 1), fixed quality code 2048, N=256; "
+                       "int16 Nyquist-band trace (sensor trace x (-1)^i, seed 0), 1,024 copies, "
+                       "code 0 (lossless), N=256",
+           "field_f32_code2048": one(field, A.F32, 2048)}
+    del field
+    tr = torch.from_numpy(synth.nyquist_trace()).to(dev).repeat(1024)
+    out["nyquist_i16_lossless"] = one(tr, A.I16, 0)
+    return out
 
 
 def run_serving(args):

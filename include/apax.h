@@ -10,7 +10,11 @@
  *     derivatives with the decision of block j carried in block j+1's header,
  *     and a 4-byte (integer) or 6-byte (float) block header;
  *   - Sec. 6 (bit packer): block floating point with one exponent per group of
- *     4 samples and joint exponent encoding of the exponents;
+ *     4 samples (or 8, an option) and joint exponent encoding of the
+ *     exponents;
+ *   - Sec. 6 (signal monitor) and Sec. 5 (Fig. 3b): as an option, the sum of
+ *     neighbouring samples as a fourth stream, for data near the Nyquist
+ *     frequency;
  *   - Sec. 4 (profiler): a sweep over encoding settings reporting
  *     r = sum(xy) / sqrt(sum(x^2) sum(y^2)) and a recommended setting at a
  *     correlation target.
@@ -53,7 +57,7 @@ typedef enum { APAX_FIXED_RATE = 0, APAX_FIXED_QUALITY = 1 } apax_mode;
 enum {
     APAX_OK = 0,
     APAX_ERR_INVALID_ARG = -1, /* bad pointer, count, mode, code, or dtype/n mismatch on decode */
-    APAX_ERR_BLOCK_SIZE = -2,  /* block size outside 64..16384 or not a multiple of 4 (Sec. 6) */
+    APAX_ERR_BLOCK_SIZE = -2,  /* block size outside 64..16384 or not a multiple of the group size (Sec. 6) */
     APAX_ERR_DTYPE = -3,       /* unknown element type */
     APAX_ERR_RATE = -4,        /* fixed-rate budget below the all-zero packet or above 2^18 B */
     APAX_ERR_CAPACITY = -5,    /* output or workspace smaller than required */
@@ -78,6 +82,24 @@ enum {
  *                        from BISECT's. */
 typedef enum { APAX_SEARCH_BISECT = 0, APAX_SEARCH_PREDICT = 1 } apax_search;
 
+/* Format options (bits of apax_params.format).  With none the container is
+ * version 1; with any it is version 2, which names the options in its flags
+ * byte so that a decoder needs no parameter.
+ *   APAX_FORMAT_GROUP8      BFPE groups of 8 samples instead of 4 (Sec. 6
+ *                           bit packer: "groups of 4 or 8"): one exponent
+ *                           and token per 8 samples.  The block size must
+ *                           be a multiple of 8.
+ *   APAX_FORMAT_SUM_STREAM  the redundancy remover also considers the sum
+ *                           stream u_0 = q_0, u_i = q_i + q_{i-1} (block
+ *                           header selector 3), small where the data
+ *                           alternate in sign (a spectrum near the Nyquist
+ *                           frequency, Sec. 5 Fig. 3b).  The stream of
+ *                           fewest code-0 bits is chosen, as for the others
+ *                           (Sec. 6 signal monitor and redundancy remover).
+ * The options change how q is packed, never q: decoded values are the same
+ * with every format. */
+enum { APAX_FORMAT_GROUP8 = 1, APAX_FORMAT_SUM_STREAM = 2 };
+
 /* Encoding parameters.
  *   block_size  N, 64..16384, multiple of 4 (Sec. 6).  256 is the default.
  *   mode        APAX_FIXED_RATE or APAX_FIXED_QUALITY.
@@ -88,6 +110,8 @@ typedef enum { APAX_SEARCH_BISECT = 0, APAX_SEARCH_PREDICT = 1 } apax_search;
  *               0 is lossless for integer types.
  *   search      fixed-rate search policy (apax_search; ignored for fixed
  *               quality); other values give APAX_ERR_INVALID_ARG.
+ *   format      format options (APAX_FORMAT_* bits; 0 = version 1); other
+ *               bits give APAX_ERR_INVALID_ARG.
  */
 typedef struct {
     uint32_t block_size;
@@ -96,6 +120,7 @@ typedef struct {
     uint32_t rate_den;
     uint32_t atten_code;
     uint32_t search;
+    uint32_t format;
 } apax_params;
 
 /* Completion record written by the device when a call's work finishes:
@@ -199,6 +224,17 @@ int apax_profile(const void *x, int dtype, uint64_t n, uint32_t block_size,
                  const uint16_t *candidates /* host */, int ncand, double target,
                  void *workspace, uint64_t workspace_bytes, apax_profile_point *points,
                  apax_profile_summary *summary, void *stream);
+
+/* apax_profile for containers with format options (APAX_FORMAT_* bits, as
+ * in apax_params.format): each point's byte count is the size of the
+ * fixed-quality container apax_encode writes with that format; the sums and
+ * r depend only on the decoded values and equal apax_profile's.  Same
+ * workspace size.  Format 0 is apax_profile. */
+int apax_profile_format(const void *x, int dtype, uint64_t n, uint32_t block_size,
+                        uint32_t format, const uint16_t *candidates /* host */, int ncand,
+                        double target, void *workspace, uint64_t workspace_bytes,
+                        apax_profile_point *points, apax_profile_summary *summary,
+                        void *stream);
 
 /* apax_profile for an array in page-locked host memory (x_host, e.g. from
  * cudaHostAlloc), leaving its copy in x_dev (device, n elements of dtype):
@@ -428,7 +464,7 @@ typedef struct {
     const uint16_t *candidates;     /* host (read when the plan is built), or NULL
                                        with ncand = APAX_PROFILE_DEFAULT_CANDIDATES */
     int32_t ncand;
-    uint32_t reserved0;
+    uint32_t format;                /* APAX_FORMAT_* bits (apax_profile_format) */
     double target;
     apax_profile_point *points;     /* device: ncand points */
     apax_profile_summary *summary;  /* device */

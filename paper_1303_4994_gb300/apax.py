@@ -37,7 +37,8 @@ class ApaxError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("block_size", ctypes.c_uint32), ("mode", ctypes.c_int32),
                 ("rate_num", ctypes.c_uint32), ("rate_den", ctypes.c_uint32),
-                ("atten_code", ctypes.c_uint32), ("search", ctypes.c_uint32)]
+                ("atten_code", ctypes.c_uint32), ("search", ctypes.c_uint32),
+                ("format", ctypes.c_uint32)]
 
 
 class Point(ctypes.Structure):
@@ -70,7 +71,7 @@ class DecodeJob(ctypes.Structure):
 class ProfileJob(ctypes.Structure):
     _fields_ = [("x", ctypes.c_void_p), ("dtype", ctypes.c_int32), ("block_size", ctypes.c_uint32),
                 ("n", ctypes.c_uint64), ("candidates", ctypes.c_void_p), ("ncand", ctypes.c_int32),
-                ("reserved0", ctypes.c_uint32), ("target", ctypes.c_double),
+                ("format", ctypes.c_uint32), ("target", ctypes.c_double),
                 ("points", ctypes.c_void_p), ("summary", ctypes.c_void_p)]
 
 
@@ -128,7 +129,8 @@ _lib = None
 
 EXPORTS = ("apax_encoded_size", "apax_workspace_size", "apax_encode", "apax_encode_recommended",
            "apax_decode_workspace_size", "apax_decode", "apax_decode_blocks",
-           "apax_profile_workspace_size", "apax_profile", "apax_profile_from_host",
+           "apax_profile_workspace_size", "apax_profile", "apax_profile_format",
+           "apax_profile_from_host",
            "apax_derived_metrics",
            "apax_encode_test_stall", "apax_status_string", "apax_build_info",
            "apax_encode_noalloc", "apax_batch_encode_workspace_size", "apax_batch_encode_create",
@@ -164,6 +166,8 @@ def lib():
         L.apax_profile_workspace_size.argtypes = [i32, u64, u32, i32, p64]
         L.apax_profile.argtypes = [vp, i32, u64, u32, vp, i32, ctypes.c_double, vp, u64, vp, vp,
                                    vp]
+        L.apax_profile_format.argtypes = [vp, i32, u64, u32, u32, vp, i32, ctypes.c_double, vp,
+                                          u64, vp, vp, vp]
         L.apax_profile_from_host.argtypes = [vp, vp, i32, u64, u32, vp, i32, ctypes.c_double, i32,
                                              vp, u64, vp, vp, vp, vp]
         L.apax_derived_metrics.argtypes = [ctypes.POINTER(Point), u64, vp]
@@ -240,11 +244,13 @@ def _dtype_code(t: torch.Tensor) -> int:
 
 
 SEARCH_BISECT, SEARCH_PREDICT = 0, 1
+# format options (container version 2): BFPE groups of 8, the sum stream
+FORMAT_GROUP8, FORMAT_SUM_STREAM = 1, 2
 
 
 def params(block_size: int = 256, mode: int = FIXED_QUALITY, rate=(4, 1), code: int = 0,
-           search: int = SEARCH_BISECT) -> Params:
-    return Params(block_size, mode, rate[0], rate[1], code, search)
+           search: int = SEARCH_BISECT, fmt: int = 0) -> Params:
+    return Params(block_size, mode, rate[0], rate[1], code, search, fmt)
 
 
 def encoded_size(dtype_code: int, n: int, p: Params) -> int:
@@ -307,10 +313,11 @@ def encode_into(x: torch.Tensor, p: Params, out: torch.Tensor, workspace: torch.
 
 
 def encode(x: torch.Tensor, block_size: int = 256, mode: int = FIXED_QUALITY, rate=(4, 1),
-           code: int = 0, stream=None, search: int = SEARCH_BISECT) -> torch.Tensor:
-    """Encode x (device tensor); returns the container as a uint8 tensor."""
+           code: int = 0, stream=None, search: int = SEARCH_BISECT, fmt: int = 0) -> torch.Tensor:
+    """Encode x (device tensor); returns the container as a uint8 tensor.
+    fmt: format options (FORMAT_GROUP8 | FORMAT_SUM_STREAM)."""
     assert x.is_cuda and x.is_contiguous()
-    p = params(block_size, mode, rate, code, search)
+    p = params(block_size, mode, rate, code, search, fmt)
     dc = _dtype_code(x)
     cap = encoded_size(dc, x.numel(), p)
     out = torch.empty(cap, dtype=torch.uint8, device=x.device)
@@ -394,10 +401,10 @@ def decode_jobs(containers, ys, block_sizes, results: torch.Tensor):
     return arr
 
 
-def profile_jobs(xs, block_sizes, candidates, targets, points, summaries):
+def profile_jobs(xs, block_sizes, candidates, targets, points, summaries, formats=None):
     """ctypes array of apax_profile_job; candidates[i] is a list of codes (kept
     alive on the returned array), points[i] / summaries[i] device uint8
-    tensors (see profile_buffers)."""
+    tensors (see profile_buffers), formats[i] the format options (default 0)."""
     k = len(xs)
     arr = (ProfileJob * k)()
     arr._keep = []
@@ -405,8 +412,9 @@ def profile_jobs(xs, block_sizes, candidates, targets, points, summaries):
         xf = xs[i].reshape(-1)
         c = (ctypes.c_uint16 * len(candidates[i]))(*candidates[i])
         arr._keep.append(c)
+        fmt = 0 if formats is None else formats[i]
         arr[i] = ProfileJob(xf.data_ptr(), _dtype_code(xf), block_sizes[i], xf.numel(),
-                            ctypes.cast(c, ctypes.c_void_p), len(candidates[i]), 0, targets[i],
+                            ctypes.cast(c, ctypes.c_void_p), len(candidates[i]), fmt, targets[i],
                             points[i].data_ptr(), summaries[i].data_ptr())
     return arr
 
@@ -612,7 +620,9 @@ def decode_blocks(stream_t: torch.Tensor, dtype: torch.dtype, n: int, b0: int, b
 # ----------------------------------------------------------------- profile
 def profile_into(x: torch.Tensor, block_size: int, candidates, target: float,
                  workspace: torch.Tensor, points: torch.Tensor, summary: torch.Tensor,
-                 stream=None):
+                 stream=None, fmt: int = 0):
+    """apax_profile (fmt 0) or apax_profile_format (byte counts of the
+    containers with those format options)."""
     xf = x.reshape(-1)
     code = _dtype_code(xf)
     if candidates is None:
@@ -620,9 +630,13 @@ def profile_into(x: torch.Tensor, block_size: int, candidates, target: float,
     else:
         arr = (ctypes.c_uint16 * len(candidates))(*candidates)
         cptr, nc = ctypes.cast(arr, ctypes.c_void_p), len(candidates)
-    _check(lib().apax_profile(xf.data_ptr(), code, xf.numel(), block_size, cptr, nc, target,
-                              workspace.data_ptr(), workspace.numel(), points.data_ptr(),
-                              summary.data_ptr(), _stream(stream)), "profile")
+    tail = (cptr, nc, target, workspace.data_ptr(), workspace.numel(), points.data_ptr(),
+            summary.data_ptr(), _stream(stream))
+    if fmt:
+        _check(lib().apax_profile_format(xf.data_ptr(), code, xf.numel(), block_size, fmt, *tail),
+               "profile_format")
+    else:
+        _check(lib().apax_profile(xf.data_ptr(), code, xf.numel(), block_size, *tail), "profile")
 
 
 def profile_from_host_into(x_host: torch.Tensor, x_dev: torch.Tensor, block_size: int,
@@ -668,11 +682,11 @@ def read_summary(summary: torch.Tensor) -> Summary:
 
 
 def profile(x: torch.Tensor, block_size: int = 256, candidates=DEFAULT_CANDIDATES,
-            target: float = 0.99999, stream=None):
+            target: float = 0.99999, stream=None, fmt: int = 0):
     """Returns (points, summary)."""
     nc = len(candidates)
     ws, pts, summ = profile_buffers(x, block_size, nc)
-    profile_into(x, block_size, list(candidates), target, ws, pts, summ, stream)
+    profile_into(x, block_size, list(candidates), target, ws, pts, summ, stream, fmt)
     return read_points(pts, nc), read_summary(summ)
 
 

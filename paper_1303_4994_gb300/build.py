@@ -15,6 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libapax_gb300.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["apax_host.cu", "apax_encode.cu", "apax_decode.cu", "apax_profile.cu", "apax_profile_t1.cu", "apax_quality.cu",
+           "apax_select.cu",
            "apax_noalloc.cu", "apax_batch.cu", "apax_server.cu"]
 HEADERS = ["apax_device.cuh", "apax_team.cuh", "apax_exact.cuh", "apax_kernels.h", "apax_plan.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

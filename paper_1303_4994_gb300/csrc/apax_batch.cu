@@ -99,7 +99,10 @@ Geo geo_of(const apax_batch *b, const apax_batch_config &c)
 
 // Fixed-rate arrays with blocks of at most 1024 samples are encoded one
 // block per thread (the search runs without team exchanges).
-bool t1_job(const EncArgs &a) { return a.mode == APAX_FIXED_RATE && a.N <= kT1MaxBlock; }
+bool t1_job(const EncArgs &a)
+{
+    return a.mode == APAX_FIXED_RATE && a.N <= kT1MaxBlock && !a.gsh && !a.sum;  // version 1 only
+}
 
 size_t pkt_smem_of(const apax_batch *b, const Geo &g)
 {
@@ -260,9 +263,9 @@ int validate_encode_jobs(const apax_encode_job *jobs, int count, std::vector<Enc
         if (!j.res) return APAX_ERR_INVALID_ARG;
         pkt_words = pw > pkt_words ? pw : pkt_words;
         ebuf_words = ew > ebuf_words ? ew : ebuf_words;
-        const uint32_t G = j.p.block_size / 4;
-        gp8[i] = (G + 7) / 8;
-        gp32[i] = (G + 31) / 32;
+        const int gs = (j.p.format & APAX_FORMAT_GROUP8) ? 8 : 4;
+        gp8[i] = (uint32_t)groups_per_thread(j.p.block_size, gs, 8);
+        gp32[i] = (uint32_t)groups_per_thread(j.p.block_size, gs, 32);
     }
     need32 = 16ull * (pkt_words + ebuf_words) * 4 > kEncSmemCap;
     return APAX_OK;
@@ -400,8 +403,8 @@ int validate_profile_jobs(const apax_profile_job *jobs, int count, std::vector<P
     max_ncand = 1;
     for (int i = 0; i < count; ++i) {
         const apax_profile_job &j = jobs[i];
-        int st = fill_prof_args(j.x, j.dtype, j.n, j.block_size, j.candidates, j.ncand, j.target,
-                                j.points, j.summary, out[i]);
+        int st = fill_prof_args(j.x, j.dtype, j.n, j.block_size, j.format, j.candidates, j.ncand,
+                                j.target, j.points, j.summary, out[i]);
         if (st) return st;
         if (j.ncand > max_ncand) max_ncand = j.ncand;
     }

@@ -6,11 +6,14 @@
 // two-state transition functions) -> exponents (each thread resolves its own
 // groups after a segmented team scan) -> mantissas (each thread unpacks its
 // contiguous groups) -> inverse derivatives (S1: prefix sum; S2: u_0 plus a
-// double prefix sum of the remaining values, team-scanned as (sum, sum of
+// double prefix sum of the remaining values; S3, the sum stream of version-2
+// containers: an alternating-sign prefix sum; team-scanned as (sum, sum of
 // prefixes, length) triples, all mod 2^W) -> dequantisation with the
-// reciprocal table, rounded once to the output type.  Teams stride over
-// blocks; fixed-rate packets sit at j*B, fixed-quality ones at the offset
-// table's word offsets, so any block range can be decoded on its own.
+// reciprocal table, rounded once to the output type.  Version-2 containers
+// with BFPE groups of 8 keep one exponent per 8 samples (two groups of 4 of
+// one width).  Teams stride over blocks; fixed-rate packets sit at j*B,
+// fixed-quality ones at the offset table's word offsets, so any block range
+// can be decoded on its own.
 #include "apax_team.cuh"
 #include "apax_kernels.h"
 
@@ -310,6 +313,8 @@ struct DecHdr {
     uint32_t N, B;
     uint64_t n, payload, poff, nb;
     int mode;
+    int gsh;  // version 2: log2(BFPE group size / 4)
+    int sum;  // version 2: selector 3 (the sum stream) is valid
     int err;  // 0, or the status a malformed or mismatched header gives
 };
 
@@ -319,11 +324,16 @@ __device__ __forceinline__ DecHdr read_header(const DecArgs &a)
     h.N = h.B = 0;
     h.n = h.payload = h.poff = h.nb = 0;
     h.mode = 0;
+    h.gsh = h.sum = 0;
     h.err = -9;
     const uint8_t *in = a.in;
-    if (!(in && a.in_bytes >= 40 && in[0] == 'A' && in[1] == 'P' && in[2] == 'X' && in[3] == '1' &&
-          in[4] == 1))
+    if (!(in && a.in_bytes >= 40 && in[0] == 'A' && in[1] == 'P' && in[2] == 'X' && in[3] == '1'))
         return h;
+    // version 1: no format option; version 2: at least one (flags bits 1-2)
+    const int fmt = (in[7] >> 1) & 0x7f;
+    if (!((in[4] == 1 && fmt == 0) || (in[4] == 2 && fmt >= 1 && fmt <= 3))) return h;
+    h.gsh = fmt & 1;
+    h.sum = (fmt >> 1) & 1;
     auto le = [&](int o, int k) {
         uint64_t v = 0;
         for (int i = 0; i < k; ++i) v |= (uint64_t)in[o + i] << (8 * i);
@@ -338,7 +348,7 @@ __device__ __forceinline__ DecHdr read_header(const DecArgs &a)
         h.err = -1;
         return h;
     }
-    if (h.N < 64 || h.N > 16384 || (h.N & 3) || (h.mode != 0 && h.mode != 1)) return h;
+    if (h.N < 64 || h.N > 16384 || (h.N & (h.gsh ? 7u : 3u)) || (h.mode != 0 && h.mode != 1)) return h;
     h.nb = (h.n + h.N - 1) / h.N;
     h.poff = 40 + (h.mode == 1 ? ((4 * h.nb + 7) / 8) * 8 : 0);
     if (h.poff > a.in_bytes || h.payload > a.in_bytes - h.poff) return h;
@@ -370,7 +380,9 @@ __device__ __forceinline__ void decode_tile(const DecArgs &a, const DecHdr &hd, 
     const uint32_t N = hd.N, B = hd.B;
     const uint64_t n = hd.n, payload = hd.payload, poff = hd.poff, nb = hd.nb;
     const int mode = hd.mode;
-    const int GN = (int)(N / 4), gp = (GN + TS - 1) / TS;
+    const int gsh = hd.gsh;
+    // groups of 4 per thread; with groups of 8 an even count (whole groups)
+    const int gp = gsh ? 2 * (int)((N / 8 + TS - 1) / TS) : (int)((N / 4 + TS - 1) / TS);
     const uint64_t jb = a.ranged ? a.b0 : 0, je = a.ranged ? a.b1 : nb;
     const uint32_t *tab = reinterpret_cast<const uint32_t *>(in + 40);
     {
@@ -385,7 +397,7 @@ __device__ __forceinline__ void decode_tile(const DecArgs &a, const DecHdr &hd, 
             const uint64_t start = mode == 1 ? 4ull * (uint64_t)__ldg(tab + j) : j * (uint64_t)B;
             const uint64_t off = j * (uint64_t)N;
             L = (int)((n - off) < N ? (n - off) : N);
-            G = (L + 3) >> 2;
+            G = gsh ? 2 * ((L + 7) >> 3) : (L + 3) >> 2;
             bad = start >= payload || (start & 3);
             if (!bad) {
                 pr.w = reinterpret_cast<const uint32_t *>(in + poff + start);
@@ -398,7 +410,8 @@ __device__ __forceinline__ void decode_tile(const DecArgs &a, const DecHdr &hd, 
         const int s = h0 & 3, code = (h0 >> 2) & 4095;
         const uint32_t plen = h0 >> 14;
         if (active) {
-            bad |= oob || s == 3 || plen < 4 || (plen & 3) || (uint64_t)plen > 4ull * pr.nwords;
+            bad |= oob || (s == 3 && !hd.sum) || plen < 4 || (plen & 3) ||
+                   (uint64_t)plen > 4ull * pr.nwords;
             if (mode == 0 && j + 1 < nb && plen != B) bad = true;
         }
         int Eb = 0;
@@ -411,13 +424,14 @@ __device__ __forceinline__ void decode_tile(const DecArgs &a, const DecHdr &hd, 
         const bool go0 = active && !bad;
         const int Gt = go0 ? G : 0;
         const int g0 = t * gp, g1 = min(g0 + gp, Gt);
-        const int nib = parse_tokens<TS>(pr, H, Gt, W, ebuf, g0, g1);
+        // one exponent per BFPE group: ebuf[g >> gsh] for the groups of 4 g
+        const int nib = parse_tokens<TS>(pr, H, Gt >> gsh, W, ebuf, g0 >> gsh, g1 >> gsh);
         const bool go = go0 && nib >= 0;
         if (go0 && nib < 0 && t == 0) set_status(a.status, -9);
         // mantissa bit offset of my groups
         int mysum = 0;
         if (go)
-            for (int g = g0; g < g1; ++g) mysum += ebuf[g];
+            for (int g = g0; g < g1; ++g) mysum += ebuf[g >> gsh];
         const int incl4 = team_incl_scan<TS>(4 * mysum);
         const int total4 = tshfl<TS>(incl4, TS - 1);
         if (go && t == 0 && (uint64_t)H + 4ull * (uint64_t)nib + (uint64_t)total4 > 8ull * plen)
@@ -429,7 +443,9 @@ __device__ __forceinline__ void decode_tile(const DecArgs &a, const DecHdr &hd, 
         const int lim = min(L, 4 * g1);  // my samples end here
         const int ge = go ? g1 : g0;      // my groups [g0, ge)
         // totals of my samples for the team scan: S = sum w, D = sum of
-        // prefixes of w, len = count; w = u except u_0 of an S2 block
+        // prefixes of w, len = count; w = u except u_0 of an S2 block, and
+        // w_i = (-1)^i u_i for S3, whose inverse q_i = u_i - q_{i-1} is
+        // q_i = (-1)^i (w_0 + ... + w_i)
         uint32_t S = 0, D = 0, u0 = 0;
         int len = 0;
         FieldReader fr;
@@ -437,13 +453,14 @@ __device__ __forceinline__ void decode_tile(const DecArgs &a, const DecHdr &hd, 
             fr.init(&pr, bit0);
 #pragma unroll 1
             for (int g = g0; g < ge; ++g) {
-                const int e = ebuf[g];
+                const int e = ebuf[g >> gsh];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const int32_t uv = fr.get(e, oob);
                     const int idx = 4 * g + i;
                     if (idx == 0) u0 = (uint32_t)uv;
-                    S += (s == 2 && idx == 0) ? 0u : (uint32_t)uv;
+                    S += (s == 2 && idx == 0) ? 0u
+                                              : ((s == 3 && (i & 1)) ? 0u - (uint32_t)uv : (uint32_t)uv);
                     D += S;
                 }
             }
@@ -469,7 +486,7 @@ __device__ __forceinline__ void decode_tile(const DecArgs &a, const DecHdr &hd, 
         fr.init(&pr, bit0);
 #pragma unroll 1
         for (int g = g0; g < ge; ++g) {
-            const int e = ebuf[g];
+            const int e = ebuf[g >> gsh];
             lt out[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
@@ -481,10 +498,13 @@ __device__ __forceinline__ void decode_tile(const DecArgs &a, const DecHdr &hd, 
                 } else if (s == 1) {
                     runS += (uint32_t)uv;
                     q = runS;
-                } else {
+                } else if (s == 2) {
                     runS += idx == 0 ? 0u : (uint32_t)uv;
                     runD += runS;
                     q = u0b + runD;
+                } else {
+                    runS += (i & 1) ? 0u - (uint32_t)uv : (uint32_t)uv;
+                    q = (i & 1) ? 0u - runS : runS;
                 }
                 out[i] = DQ(sext_w(q, W));
             }
@@ -511,7 +531,9 @@ __device__ __forceinline__ void decode_block_t1(const DecArgs &a, const DecHdr &
     const uint32_t N = hd.N;
     const uint64_t off = j * (uint64_t)N;
     const int L = (int)((hd.n - off) < N ? (hd.n - off) : N);
-    const int G = (L + 3) >> 2;
+    const int gsh = hd.gsh;
+    const int G = gsh ? 2 * ((L + 7) >> 3) : (L + 3) >> 2;  // groups of 4
+    const int GX = G >> gsh;                                // BFPE groups
     const uint8_t *in = a.in;
     const uint64_t start = hd.mode == 1
                                ? 4ull * (uint64_t)__ldg(reinterpret_cast<const uint32_t *>(in + 40) + j)
@@ -534,7 +556,7 @@ __device__ __forceinline__ void decode_block_t1(const DecArgs &a, const DecHdr &
     const uint32_t h0 = word(0);
     const int s = h0 & 3, code = (h0 >> 2) & 4095;
     const uint32_t plen = h0 >> 14;
-    bad |= s == 3 || plen < 4 || (plen & 3) || (uint64_t)plen > 4ull * nwords;
+    bad |= (s == 3 && !hd.sum) || plen < 4 || (plen & 3) || (uint64_t)plen > 4ull * nwords;
     if (hd.mode == 0 && j + 1 < hd.nb && plen != hd.B) bad = true;
     if (bad) {
         set_status(a.status, -9);
@@ -587,7 +609,7 @@ __device__ __forceinline__ void decode_block_t1(const DecArgs &a, const DecHdr &
         ep = e;
         ++g;
     };
-    while (g < G && !bad) {
+    while (g < GX && !bad) {
         const int nb = (int)(take(4) & 15u);
         ++nib;
         if (nb >= 14) {
@@ -597,7 +619,7 @@ __device__ __forceinline__ void decode_block_t1(const DecArgs &a, const DecHdr &
         } else if (g == 0) {
             bad = true;  // the first exponent is absolute
         } else if (nb <= 8) {
-            if (g + 1 >= G) {
+            if (g + 1 >= GX) {
                 bad = true;  // a joint token needs two diffs
             } else {
                 const int d1 = (nb * 11) >> 5;  // nb / 3 for nb <= 8
@@ -609,7 +631,8 @@ __device__ __forceinline__ void decode_block_t1(const DecArgs &a, const DecHdr &
             put(ep + nb - 11);
         }
     }
-    if (!bad && (uint64_t)H + 4ull * (uint64_t)nib + 4ull * (uint64_t)sume > 8ull * plen) bad = true;
+    if (!bad && (uint64_t)H + 4ull * (uint64_t)nib + (4ull << gsh) * (uint64_t)sume > 8ull * plen)
+        bad = true;
     if (bad) {
         set_status(a.status, -9);
         return;
@@ -621,7 +644,7 @@ __device__ __forceinline__ void decode_block_t1(const DecArgs &a, const DecHdr &
     // the four fields of a group, sign-extended from e bits (e = 0: zeros);
     // two fields per read when they fit in 32 bits
     auto fields = [&](int gg, int32_t (&u)[4]) {
-        const uint32_t e = eb[(size_t)gg * est];
+        const uint32_t e = eb[(size_t)(gg >> gsh) * est];
         if (e <= 16) {
             const uint32_t v0 = take(2 * e), v1 = take(2 * e);
             u[0] = bfe_s32(v0, 0, e);
@@ -660,11 +683,14 @@ __device__ __forceinline__ void decode_block_t1(const DecArgs &a, const DecHdr &
                 } else if (s == 1) {
                     run += uv;
                     q[i] = run;
-                } else {
+                } else if (s == 2) {
                     if (gg == 0 && i == 0) u0 = uv;  // second differences start from the first value
                     else run += uv;
                     runD += run;
                     q[i] = u0 + runD;
+                } else {
+                    run = uv - run;  // the sum stream: q_i = u_i - q_{i-1}
+                    q[i] = run;
                 }
             }
             emit(gg, q);
@@ -686,6 +712,18 @@ __device__ __forceinline__ void decode_block_t1(const DecArgs &a, const DecHdr &
             uint32_t q[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) q[i] = run += (uint32_t)u[i];
+            emit(gg, q);
+        }
+    } else if (s == 3) {
+        // the sum stream: q_i = u_i - q_{i-1}
+        uint32_t run = 0;
+#pragma unroll 1
+        for (int gg = 0; gg < G; ++gg) {
+            int32_t u[4];
+            fields(gg, u);
+            uint32_t q[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) q[i] = run = (uint32_t)u[i] - run;
             emit(gg, q);
         }
     } else {

@@ -26,17 +26,18 @@ __device__ __forceinline__ void put_le(uint8_t *p, uint64_t v, int nb)
     for (int i = 0; i < nb; ++i) p[i] = (uint8_t)(v >> (8 * i));
 }
 
-// Container header (40 bytes, little endian): "APX1", version 1, dtype,
-// mode, flags (bit 0: offset table), N, fixed-quality code, reserved,
+// Container header (40 bytes, little endian): "APX1", version (1, or 2 with
+// a format option), dtype, mode, flags (bit 0: offset table; bit 1: BFPE
+// groups of 8; bit 2: the sum stream), N, fixed-quality code, reserved,
 // fixed-rate budget B, n, payload bytes (written last), 4 reserved bytes.
 __device__ void write_container_header(const EncArgs &a, int code)
 {
     uint8_t *h = a.out;
     h[0] = 'A'; h[1] = 'P'; h[2] = 'X'; h[3] = '1';
-    h[4] = 1;
+    h[4] = (a.gsh || a.sum) ? 2 : 1;
     h[5] = (uint8_t)a.dtype;
     h[6] = (uint8_t)a.mode;
-    h[7] = a.mode == 1 ? 1 : 0;
+    h[7] = (uint8_t)((a.mode == 1 ? 1 : 0) | (a.gsh ? 2 : 0) | (a.sum ? 4 : 0));
     put_le(h + 8, a.N, 4);
     put_le(h + 12, a.mode == 1 ? (uint64_t)code : 0, 2);
     put_le(h + 14, 0, 2);
@@ -122,18 +123,20 @@ __device__ __forceinline__ int predict_start(int D, CntGe &&cnt_ge)
     return predict_from_red(D, k1, rprev, rk);
 }
 
+// The smallest packet of L samples in BFPE groups of 4 << gsh: header, the
+// first exponent absolute, one joint token per two further groups.
 template <int DT>
-__device__ __forceinline__ uint32_t min_packet(int L)
+__device__ __forceinline__ uint32_t min_packet(int L, int gsh)
 {
-    const int G = (L + 3) >> 2;
+    const int G = gsh ? (L + 7) >> 3 : (L + 3) >> 2;
     return pad32_bytes((uint32_t)DT_<DT>::H + 8u + 4u * (uint32_t)((G - 1 + 1) >> 1));
 }
 
 template <int DT>
-__device__ __forceinline__ uint32_t fr_budget(int L, uint32_t num, uint32_t den)
+__device__ __forceinline__ uint32_t fr_budget(int L, uint32_t num, uint32_t den, int gsh)
 {
     const uint64_t b = ((uint64_t)L * DT_<DT>::S * den / (4ull * num)) * 4ull;
-    const uint32_t mp = min_packet<DT>(L);
+    const uint32_t mp = min_packet<DT>(L, gsh);
     return b > mp ? (uint32_t)b : mp;
 }
 
@@ -301,7 +304,10 @@ struct GWriter {
 // ---------------------------------------------------------------- tile body
 // One tile (nteams consecutive blocks) of the array described by `a`.
 // Called by every thread of the CTA; `smem` holds the teams' packet images.
-template <int DT, int TS, int MODE>
+// INL: the tile sizes the sum stream itself for the stream decision (the
+// batched kernels); single-array kernels read a.sel instead, which keeps
+// the sizing's registers out of them.
+template <int DT, int TS, int MODE, bool INL>
 __device__ __forceinline__ void encode_tile(const EncArgs &a, uint64_t tile, uint32_t *smem)
 {
     __shared__ uint32_t s_words[32];
@@ -341,21 +347,20 @@ __device__ __forceinline__ void encode_tile(const EncArgs &a, uint64_t tile, uin
     }
     // stream decision: best(j-1) at code 0 (block 0 uses its own)
     int s;
-    {
+    if (!INL && a.sel) {
+        s = jl < nbl ? a.sel[jl] : 0;
+    } else {
         TBlock<DT> pv;
-        open_team_block<DT, TS>(pv, x, a.n, a.N, a.nb, j == 0 ? 0 : j - 1, gp, base);
-        uint32_t bb[3];
-        team_eval3<DT, TS>(pv, 0, bb);
-        s = 0;
-        if (bb[1] < bb[s]) s = 1;
-        if (bb[2] < bb[s]) s = 2;
+        open_team_block<DT, TS>(pv, x, a.n, a.N, a.nb, j == 0 ? 0 : j - 1, gp, base, a.gsh);
+        s = team_best_stream<DT, TS>(pv, INL && a.sum != 0);
     }
     TBlock<DT> b;
-    open_team_block<DT, TS>(b, x, a.n, a.N, a.nb, j, gp, base);
+    open_team_block<DT, TS>(b, x, a.n, a.N, a.nb, j, gp, base, a.gsh);
+    const int gsh = b.gsh;
     if (b.active && b.bad && t == 0) set_status(a.status, -8);
     uint32_t plen = 0;
     if (MODE == 0) {
-        const uint32_t budget = b.L == (int)a.N ? a.B : fr_budget<DT>(b.L, a.rate_num, a.rate_den);
+        const uint32_t budget = b.L == (int)a.N ? a.B : fr_budget<DT>(b.L, a.rate_num, a.rate_den, gsh);
         if (a.search == APAX_SEARCH_PREDICT) {
             // the code-0 exponents of stream s into ebuf, the packet bits
             const uint32_t bits0 = team_exps<DT, TS>(b, s, ebuf);
@@ -366,14 +371,15 @@ __device__ __forceinline__ void encode_tile(const EncArgs &a, uint64_t tile, uin
             const int D = (int)bits0 - 8 * (int)budget;
             const int ge = b.active ? b.g1 : b.g0;
             // red(k) for k = 1, 2, ... until every team of the warp has its k1
+            // (a group of 4 << gsh samples loses that many bits per unit of k)
             int rprev = 0, rk = 0, k1 = 0;
 #pragma unroll 1
             for (int k = 1; k <= 31 && __any_sync(kFull, !fits0 && k1 == 0); ++k) {
                 int cnt = 0;
-                for (int g = b.g0; g < ge; ++g) cnt += ebuf[g] >= k;
+                for (int g = b.g0 >> gsh; g < (ge >> gsh); ++g) cnt += ebuf[g] >= k;
                 cnt = team_sum<TS>(cnt);
                 if (k1 == 0) {
-                    rk = rprev + 4 * cnt;
+                    rk = rprev + (4 << gsh) * cnt;
                     if (rk >= D) k1 = k;
                     else if (k < 31) rprev = rk;
                 }
@@ -411,26 +417,33 @@ __device__ __forceinline__ void encode_tile(const EncArgs &a, uint64_t tile, uin
         plen = budget;
     }
 
-    // final pass: the chosen stream's exponents into ebuf, token counts
+    // final pass: the chosen stream's exponents into ebuf (one per BFPE
+    // group: ebuf[g >> gsh] for the groups of 4 g), token counts
     const Quant<DT> Q(code, b.Eb);
     TokCount tc;
     tc.init();
     with_quant<DT>(Q, [&](const auto &qf) {
         Stream1 st(s, carry_in<DT>(b, qf, 4 * b.g0));
+        uint32_t acc = 0;
 #pragma unroll 1
         for (int g = b.g0; g < b.g1; ++g) {
             lt xv[4];
             load4<DT, true>(b, 4 * g, xv);
             int32_t u[4];
-            const int e = exp_from_or(group1<DT>(qf, xv, st, u));
-            ebuf[g] = (uint8_t)e;
-            tc.push(e, true);
+            acc |= group1<DT>(qf, xv, st, u);
+            if (!gsh || (g & 1)) {
+                const int e = exp_from_or(acc);
+                ebuf[g >> gsh] = (uint8_t)e;
+                tc.push(e, true);
+                acc = 0;
+            }
         }
     });
     int nib_total, sume_total, nib_mine;
     bool s_in;
     team_tokens<TS>(tc, b.g0 == 0, nib_total, sume_total, &s_in, &nib_mine);
-    const uint32_t bits = (uint32_t)H + 4u * (uint32_t)nib_total + 4u * (uint32_t)sume_total;
+    const uint32_t wm = 4u << gsh;  // mantissa bits per exponent unit
+    const uint32_t bits = (uint32_t)H + 4u * (uint32_t)nib_total + wm * (uint32_t)sume_total;
     if (MODE == 1) plen = pad32_bytes(bits);
     const uint32_t words = b.active ? plen >> 2 : 0;
     if (MODE == 1) {
@@ -464,11 +477,12 @@ __device__ __forceinline__ void encode_tile(const EncArgs &a, uint64_t tile, uin
         // tokens of my groups (Sec. 6 JEE), starting at my nibble offset
         NibWriter nw;
         nw.start(pkt, (uint32_t)H + 4u * (uint32_t)nib_before);
-        write_tokens(nw, ebuf, 1, b.g0, b.g1, b.G, s_in);
+        write_tokens(nw, ebuf, 1, b.g0 >> gsh, b.g1 >> gsh, b.G >> gsh, s_in);
         nw.flush();
-        // mantissas of my groups after the token section
+        // mantissas of my groups after the token section (a group of 8 is
+        // two groups of 4 of its one width)
         NibWriter mw;
-        mw.start(pkt, (uint32_t)H + 4u * (uint32_t)nib_total + 4u * (uint32_t)sume_before);
+        mw.start(pkt, (uint32_t)H + 4u * (uint32_t)nib_total + wm * (uint32_t)sume_before);
         with_quant<DT>(Q, [&](const auto &qf) {
             Stream1 sm(s, carry_in<DT>(b, qf, 4 * b.g0));
 #pragma unroll 1
@@ -477,7 +491,7 @@ __device__ __forceinline__ void encode_tile(const EncArgs &a, uint64_t tile, uin
                 load4<DT, true>(b, 4 * g, xv);
                 int32_t u[4];
                 group1<DT>(qf, xv, sm, u);
-                write_group_fields(mw, ebuf[g], u);
+                write_group_fields(mw, ebuf[g >> gsh], u);
             }
         });
         mw.flush();
@@ -632,17 +646,13 @@ __device__ __forceinline__ void encode_tile_t1(const EncArgs &a, uint64_t tile, 
     {
         TBlock<DT> pv;
         open_team_block<DT, 1>(pv, x, a.n, a.N, a.nb, j == 0 ? 0 : j - 1, a.gp);
-        uint32_t bb[3];
-        team_eval3<DT, 1>(pv, 0, bb);
-        s = 0;
-        if (bb[1] < bb[s]) s = 1;
-        if (bb[2] < bb[s]) s = 2;
+        s = team_best_stream<DT, 1>(pv, false);  // version-1 containers only
     }
     TBlock<DT> b;
     open_team_block<DT, 1>(b, x, a.n, a.N, a.nb, j, a.gp);
     if (b.active && b.bad) set_status(a.status, -8);
     // the search against the block budget (Sec. 6 adaptive loop)
-    const uint32_t budget = b.L == (int)a.N ? a.B : fr_budget<DT>(b.L, a.rate_num, a.rate_den);
+    const uint32_t budget = b.L == (int)a.N ? a.B : fr_budget<DT>(b.L, a.rate_num, a.rate_den, 0);
     int code = 0;
     if (a.search == APAX_SEARCH_PREDICT) {
         // the code-0 exponents of stream s into the column, the packet bits
@@ -744,13 +754,13 @@ __global__ void __launch_bounds__(128) k_encode(EncArgs a)
     __shared__ uint64_t s_tile;
     if (threadIdx.x == 0) s_tile = MODE == 1 ? (uint64_t)atomicAdd(a.ticket, 1u) : blockIdx.x;
     __syncthreads();
-    encode_tile<DT, TS, MODE>(a, s_tile, smem);
+    encode_tile<DT, TS, MODE, false>(a, s_tile, smem);
 }
 
 template <int DT, int TS, int MODE>
 __device__ __noinline__ void encode_tile_call(const EncArgs &a, uint64_t tile, uint32_t *smem)
 {
-    encode_tile<DT, TS, MODE>(a, tile, smem);
+    encode_tile<DT, TS, MODE, true>(a, tile, smem);
 }
 
 template <int DT>

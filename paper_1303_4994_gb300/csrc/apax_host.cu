@@ -49,6 +49,8 @@ int fill_enc_args(const void *x, int dtype, uint64_t n, const apax_params *p,
     a.cap = cap;
     a.res = res;
     a.n_hdr = n;
+    a.gsh = f.gs == 8 ? 1 : 0;
+    a.sum = (f.opts & APAX_FORMAT_SUM_STREAM) ? 1 : 0;
     a.spin_limit = 1ll << 31;
     a.test_stall_tile = -1;
     if (p->mode == APAX_FIXED_RATE) {
@@ -68,7 +70,7 @@ int fill_enc_args(const void *x, int dtype, uint64_t n, const apax_params *p,
     return APAX_OK;
 }
 
-int fill_prof_args(const void *x, int dtype, uint64_t n, uint32_t block_size,
+int fill_prof_args(const void *x, int dtype, uint64_t n, uint32_t block_size, uint32_t format,
                    const uint16_t *candidates, int ncand, double target,
                    apax_profile_point *points, apax_profile_summary *summary, ProfArgs &a)
 {
@@ -76,6 +78,8 @@ int fill_prof_args(const void *x, int dtype, uint64_t n, uint32_t block_size,
     int st = fmt_of(dtype, f);
     if (st) return st;
     if (!block_size_ok(block_size)) return APAX_ERR_BLOCK_SIZE;
+    st = fmt_opts(format, block_size, f);
+    if (st) return st;
     uint16_t def[16];
     if (!candidates) {
         if (ncand != APAX_PROFILE_DEFAULT_CANDIDATES) return APAX_ERR_INVALID_ARG;
@@ -101,7 +105,9 @@ int fill_prof_args(const void *x, int dtype, uint64_t n, uint32_t block_size,
     a.ncand = ncand;
     for (int i = 0; i < ncand; ++i) a.codes[i] = candidates[i];
     a.nruns = (nb + 15) / 16;
-    a.gp = (int)((block_size / 4 + kProfTS - 1) / kProfTS);  // groups per team thread
+    a.gp = groups_per_thread(block_size, f.gs, kProfTS);
+    a.gsh = f.gs == 8 ? 1 : 0;
+    a.sum = (f.opts & APAX_FORMAT_SUM_STREAM) ? 1 : 0;
     a.target = target;
     a.points = points;
     a.summary = summary;
@@ -131,20 +137,21 @@ int encode_impl(const void *x, int dtype, uint64_t n, const apax_params *p,
     if (wsb < need_ws) return APAX_ERR_CAPACITY;
     int ts, threads;
     Plan pl;
-    if (p->mode == APAX_FIXED_RATE && a.N <= kT1MaxBlock && a.nb >= kT1MinBlocks) {
+    Fmt f;
+    fmt_of(dtype, f);
+    fmt_opts(p->format, p->block_size, f);
+    if (p->mode == APAX_FIXED_RATE && a.N <= kT1MaxBlock && a.nb >= kT1MinBlocks && !p->format) {
         // fixed rate, a block per thread: its 13-step search runs without
         // team exchanges (measured faster); fixed quality keeps teams, whose
-        // packets leave through coalesced stores
+        // packets leave through coalesced stores.  Format options take teams.
         pl = plan_geometry(a.N, a.nb, 0, 0, 1, 128);
         pl.smem = (size_t)128 * (a.N / 4);
     } else {
         default_geometry((size_t)(pw + ew) * 4, a.nb, ts, threads);
-        pl = plan_geometry(a.N, a.nb, pw, ew, ts, threads);
+        pl = plan_geometry(a.N, a.nb, pw, ew, ts, threads, f.gs);
     }
     a.pkt_words = pl.pkt_words;
     a.ebuf_words = pl.ebuf_words;
-    Fmt f;
-    fmt_of(dtype, f);
     // staging of the tile in shared memory: on for the fixed-rate search by
     // teams (13 passes over a block), off for fixed quality, whose occupancy
     // matters more than its few L2 re-reads (measured on GB300)
@@ -174,6 +181,25 @@ int encode_impl(const void *x, int dtype, uint64_t n, const apax_params *p,
     cudaStream_t s = (cudaStream_t)stream;
     st = cuda_fail(cudaMemsetAsync(ws, 0, need_ws, s));
     if (st) return st;
+    if (a.sum) {
+        // the stream decisions of the call's blocks, in the workspace's tail
+        const uint64_t cnt = a.nb - a.jb0;
+        uint8_t *sel = w + need_ws - (cnt + 15) / 16 * 16;
+        SelArgs sa;
+        sa.x = a.x;
+        sa.n = a.n;
+        sa.N = a.N;
+        sa.nb = a.nb;
+        sa.j0 = a.jb0;
+        sa.count = cnt;
+        sa.dtype = dtype;
+        sa.gsh = a.gsh;
+        sa.gp = 0;
+        sa.sel = sel;
+        st = cuda_fail(launch_best_streams(sa, s));
+        if (st) return st;
+        a.sel = sel;
+    }
     return cuda_fail(launch_encode(a, pl.ts, pl.threads, pl.smem, s));
 }
 
@@ -270,6 +296,7 @@ static void place_profile_workspace(ProfArgs &a, void *workspace)
     a.run_sums = (double *)(w + kWsHead + 8 * 32);
     a.scratch = a.run_sums + Qn * (a.nruns ? a.nruns : 1);
     a.run_flags = (uint8_t *)(a.scratch + Qn * 2 * (((a.nruns + 15) / 16) + 1));
+    a.sel = a.sum ? a.run_flags + (a.nruns + 15) / 16 * 16 : nullptr;
 }
 
 }  // namespace
@@ -303,9 +330,11 @@ int apax_encoded_size(int dtype, uint64_t n, const apax_params *p, uint64_t *byt
         *bytes = 40 + (nb - 1) * budget(f, N, p->rate_num, p->rate_den) +
                  budget(f, Lend, p->rate_num, p->rate_den);
     } else {
-        const uint64_t full = pad32((uint64_t)f.H + 8ull * (N / 4) + (uint64_t)f.W * N);
-        const uint64_t Gl = (Lend + 3) / 4;
-        const uint64_t last = pad32((uint64_t)f.H + 8ull * Gl + (uint64_t)f.W * 4ull * Gl);
+        // every exponent absolute (8 bits) at the full width W
+        const uint64_t gs = (uint64_t)f.gs;
+        const uint64_t full = pad32((uint64_t)f.H + 8ull * (N / gs) + (uint64_t)f.W * N);
+        const uint64_t Gl = (Lend + gs - 1) / gs;
+        const uint64_t last = pad32((uint64_t)f.H + 8ull * Gl + (uint64_t)f.W * gs * Gl);
         *bytes = 40 + table_bytes(nb) + (nb - 1) * full + last;
     }
     return APAX_OK;
@@ -322,6 +351,8 @@ int apax_workspace_size(int dtype, uint64_t n, const apax_params *p, uint64_t *b
         p->mode == APAX_FIXED_RATE ? budget(f, p->block_size, p->rate_num, p->rate_den) : 0;
     const Plan pl = plan_encode(f, p->block_size, nb, B);
     *bytes = kWsHead + (p->mode == APAX_FIXED_QUALITY ? 8 * pl.ntiles : 0);
+    // the sum stream: one stream decision byte per block
+    if (f.opts & APAX_FORMAT_SUM_STREAM) *bytes = (*bytes + 15) / 16 * 16 + (nb + 15) / 16 * 16;
     return APAX_OK;
 }
 
@@ -444,6 +475,8 @@ int apax_merge_shards(const apax_shard *shards, int count, int dtype, uint64_t n
     a.B = p->mode == APAX_FIXED_RATE ? (uint32_t)budget(f, N, p->rate_num, p->rate_den) : 0;
     a.n_hdr = n;
     a.poff = poff;
+    a.gsh = f.gs == 8 ? 1 : 0;
+    a.sum = (f.opts & APAX_FORMAT_SUM_STREAM) ? 1 : 0;
     a.res = res;
     return cuda_fail(launch_merged_header(a, payload, s));
 }
@@ -592,7 +625,8 @@ int apax_profile_workspace_size(int dtype, uint64_t n, uint32_t block_size, int 
     const uint64_t runs = 8 * Qn * (nruns ? nruns : 1);
     const uint64_t scratch = 8 * Qn * 2 * (((nruns + 15) / 16) + 1);
     const uint64_t flags = (nruns + 15) / 16 * 16;  // runs left to the team sweep
-    *bytes = head + runs + scratch + flags;
+    const uint64_t sel = (nb + 15) / 16 * 16;       // stream decisions (the sum stream)
+    *bytes = head + runs + scratch + flags + sel;
     return APAX_OK;
 }
 
@@ -601,8 +635,18 @@ int apax_profile(const void *x, int dtype, uint64_t n, uint32_t block_size,
                  uint64_t workspace_bytes, apax_profile_point *points,
                  apax_profile_summary *summary, void *stream)
 {
+    return apax_profile_format(x, dtype, n, block_size, 0, candidates, ncand, target, workspace,
+                               workspace_bytes, points, summary, stream);
+}
+
+int apax_profile_format(const void *x, int dtype, uint64_t n, uint32_t block_size,
+                        uint32_t format, const uint16_t *candidates, int ncand, double target,
+                        void *workspace, uint64_t workspace_bytes, apax_profile_point *points,
+                        apax_profile_summary *summary, void *stream)
+{
     ProfArgs a;
-    int st = fill_prof_args(x, dtype, n, block_size, candidates, ncand, target, points, summary, a);
+    int st = fill_prof_args(x, dtype, n, block_size, format, candidates, ncand, target, points,
+                            summary, a);
     if (st) return st;
     if (!workspace || ((uintptr_t)workspace & 15)) return APAX_ERR_INVALID_ARG;
     uint64_t need;
@@ -623,7 +667,7 @@ int apax_profile_from_host(const void *x_host, void *x_dev, int dtype, uint64_t 
                            void *stream, void *copy_stream)
 {
     ProfArgs a;
-    int st = fill_prof_args(x_dev, dtype, n, block_size, candidates, ncand, target, points,
+    int st = fill_prof_args(x_dev, dtype, n, block_size, 0, candidates, ncand, target, points,
                             summary, a);
     if (st) return st;
     if ((!x_host && n) || chunks < 1 || chunks > 64 || stream == copy_stream)

@@ -88,7 +88,11 @@ struct EncArgs {
     uint32_t pkt_words, ebuf_words;  // per-team shared-memory layout
     uint32_t stage_off; // byte offset of the staged tile in shared memory (0: none)
     int t1;             // batches: this array is encoded one block per thread
-    int gp;             // groups per team thread
+    int gp;             // groups of 4 per team thread (even with groups of 8)
+    int gsh;            // log2(BFPE group size / 4): 0, or 1 for groups of 8
+    int sum;            // the sum stream is a candidate (format version 2)
+    const uint8_t *sel; // single arrays with the sum stream: the stream of block
+                        // jb0 + i at sel[i] (launch_best_streams), else NULL
     uint64_t ntiles;
     // workspace
     unsigned *ticket;
@@ -153,7 +157,11 @@ struct ProfArgs {
     uint64_t nruns;     // level-1 nodes (16 blocks each)
     uint64_t run0, run1; // runs swept by one launch of the run kernel
     uint32_t stage_off; // byte offset of the staged run in shared memory (0: none)
-    int gp;             // groups per team thread
+    int gp;             // groups of 4 per team thread (even with groups of 8)
+    int gsh;            // log2(BFPE group size / 4) of the byte counts
+    int sum;            // the sum stream is a candidate of the byte counts
+    const uint8_t *sel; // single arrays with the sum stream: block j's stream at
+                        // sel[j] (launch_best_streams), else NULL
     double *run_sums;   // [nruns][2 + 4*ncand]: sx, sxx, then (sy, sxy, syy, sdd) per candidate
     unsigned long long *bytes;  // [ncand] payload bytes (atomic)
     int *status;
@@ -200,6 +208,21 @@ bool profile_t1_eligible(const ProfArgs &a);
 cudaError_t launch_profile_t1(const ProfArgs &a, cudaStream_t s);
 
 cudaError_t launch_encode(const EncArgs &a, int ts, int threads, size_t smem, cudaStream_t s);
+
+// Stream decisions of blocks [j0, j0 + count) of an array with the sum
+// stream into sel[0, count) (apax_select.cu).
+struct SelArgs {
+    const void *x;   // block j at x + j N
+    uint64_t n;
+    uint32_t N;
+    uint64_t nb;     // blocks of the array (or the end of a shard's range)
+    uint64_t j0, count;
+    int dtype;
+    int gsh;
+    int gp;          // set by the launcher
+    uint8_t *sel;
+};
+cudaError_t launch_best_streams(const SelArgs &a, cudaStream_t s);
 // Shard merging: dst[i] = src[i] + add for i < count; the merged header
 // (a.out, a.n_hdr, a.mode, a.code, a.B, a.poff) and a.res.
 cudaError_t launch_table_rebase(const uint32_t *src, uint32_t *dst, uint64_t count, uint64_t add,

@@ -14,6 +14,8 @@ namespace host {
 
 struct Fmt {
     int size = 0, W = 0, F = 0, H = 0;  // zero until fmt_of fills them
+    int gs = 4;          // BFPE group size (8 with APAX_FORMAT_GROUP8)
+    uint32_t opts = 0;   // APAX_FORMAT_* bits
 };
 
 inline int fmt_of(int dtype, Fmt &f)
@@ -30,11 +32,28 @@ inline int fmt_of(int dtype, Fmt &f)
 
 inline bool block_size_ok(uint32_t N) { return N >= 64 && N <= 16384 && (N % 4) == 0; }
 
+// Format options: known bits only; groups of 8 need whole groups per block.
+inline int fmt_opts(uint32_t format, uint32_t N, Fmt &f)
+{
+    if (format & ~(uint32_t)(APAX_FORMAT_GROUP8 | APAX_FORMAT_SUM_STREAM)) return APAX_ERR_INVALID_ARG;
+    f.opts = format;
+    f.gs = (format & APAX_FORMAT_GROUP8) ? 8 : 4;
+    if (N % (uint32_t)f.gs) return APAX_ERR_BLOCK_SIZE;
+    return APAX_OK;
+}
+
+// Groups of 4 samples per team thread.  With groups of 8 a thread owns an
+// even number of them (whole groups of 8).
+inline int groups_per_thread(uint32_t N, int gs, int ts)
+{
+    return gs == 8 ? 2 * (int)((N / 8 + ts - 1) / ts) : (int)((N / 4 + ts - 1) / ts);
+}
+
 inline uint64_t pad32(uint64_t bits) { return 4 * ((bits + 31) / 32); }
 
 inline uint64_t minpacket(const Fmt &f, uint64_t L)
 {
-    uint64_t G = (L + 3) / 4;
+    uint64_t G = (L + f.gs - 1) / f.gs;
     return pad32((uint64_t)f.H + 8 + 4 * ((G - 1 + 1) / 2));
 }
 
@@ -53,6 +72,8 @@ inline int check(int dtype, const apax_params *p, Fmt &f)
     int st = fmt_of(dtype, f);
     if (st) return st;
     if (!block_size_ok(p->block_size)) return APAX_ERR_BLOCK_SIZE;
+    st = fmt_opts(p->format, p->block_size, f);
+    if (st) return st;
     if (p->search > APAX_SEARCH_PREDICT) return APAX_ERR_INVALID_ARG;
     if (p->mode == APAX_FIXED_RATE) {
         if (p->rate_num == 0 || p->rate_den == 0) return APAX_ERR_RATE;
@@ -92,7 +113,7 @@ constexpr size_t kEncSmemCap = 200 * 1024;
 
 // Geometry for a given team size and CTA size.
 inline Plan plan_geometry(uint32_t N, uint64_t nb, uint32_t pkt_words, uint32_t ebuf_words, int ts,
-                          int threads)
+                          int threads, int gs = 4)
 {
     Plan pl;
     pl.ts = ts;
@@ -100,8 +121,7 @@ inline Plan plan_geometry(uint32_t N, uint64_t nb, uint32_t pkt_words, uint32_t 
     pl.pkt_words = pkt_words;
     pl.ebuf_words = ebuf_words;
     const int nteams = threads / ts;
-    const int G = (int)(N / 4);
-    pl.gp = (G + ts - 1) / ts;
+    pl.gp = groups_per_thread(N, gs, ts);
     pl.smem = (size_t)nteams * (pkt_words + ebuf_words) * 4;
     pl.ntiles = nb ? (nb + nteams - 1) / nteams : 1;
     return pl;
@@ -140,7 +160,7 @@ inline Plan plan_encode(const Fmt &f, uint32_t N, uint64_t nb, uint64_t fr_budge
     team_words(f, N, fr_budget_bytes, pw, ew);
     int ts, threads;
     default_geometry((size_t)(pw + ew) * 4, nb, ts, threads);
-    return plan_geometry(N, nb, pw, ew, ts, threads);
+    return plan_geometry(N, nb, pw, ew, ts, threads, f.gs);
 }
 
 constexpr uint64_t kWsHead = 64;  // ticket, done, status (+ padding)
@@ -153,7 +173,7 @@ int fill_enc_args(const void *x, int dtype, uint64_t n, const apax_params *p,
 
 // Validate one profile call and fill its arguments (all but the workspace
 // pointers).
-int fill_prof_args(const void *x, int dtype, uint64_t n, uint32_t block_size,
+int fill_prof_args(const void *x, int dtype, uint64_t n, uint32_t block_size, uint32_t format,
                    const uint16_t *candidates, int ncand, double target,
                    apax_profile_point *points, apax_profile_summary *summary, ProfArgs &a);
 

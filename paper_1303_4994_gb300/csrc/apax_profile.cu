@@ -203,24 +203,26 @@ __device__ __forceinline__ void profile_chunk3(const TBlock<4> &b, int s, int ge
     float bs[3];
     uint32_t qp[3], qpp[3];
     int64_t sq[3], sA[3], sB[3];
-    const uint32_t ca = s == 0 ? 0u : (s == 1 ? 1u : 2u), cb = s == 2 ? 1u : 0u;
+    // u = q - ca qp + cb qpp (S3: ca = -1 on the previous q)
+    const uint32_t ca = s == 0 ? 0u : (s == 1 ? 1u : (s == 2 ? 2u : 0xffffffffu)),
+                   cb = s == 2 ? 1u : 0u;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         const Quant<4> Q((int)codes[j], b.Eb);
         bs[j] = Q.scale;
         const Carry c = carry_in<4>(b, QuantM<4, 1>(Q), 4 * b.g0);
-        qp[j] = s == 1 ? c.qp1 : c.qp2;
+        qp[j] = (s == 1 || s == 3) ? c.qp1 : c.qp2;
         qpp[j] = c.qpp2;
         sq[j] = sA[j] = sB[j] = 0;
     }
     Tok3 tk;
     tk.init();
+    uint32_t o[3] = {0u, 0u, 0u};  // width terms of the current BFPE group
 #pragma unroll 1
     for (int g = b.g0; g < ge; ++g) {
         lt xv[4];
         load4<4, true>(b, 4 * g, xv);
         const int nv = b.L - 4 * g;
-        uint32_t o[3] = {0u, 0u, 0u};
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const float xf = __uint_as_float(xv[i]);
@@ -240,7 +242,10 @@ __device__ __forceinline__ void profile_chunk3(const TBlock<4> &b, int s, int ge
             }
         }
         // |u| < 2^25 here, so no width reaches 31
-        tk.push(32 - __clz(o[0]), 32 - __clz(o[1]), 32 - __clz(o[2]));
+        if (!b.gsh || (g & 1)) {
+            tk.push(32 - __clz(o[0]), 32 - __clz(o[1]), 32 - __clz(o[2]));
+            o[0] = o[1] = o[2] = 0u;
+        }
     }
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
@@ -252,7 +257,7 @@ __device__ __forceinline__ void profile_chunk3(const TBlock<4> &b, int s, int ge
             cs[j].A = rA;
             cs[j].B = rB;
             cs[j].D = 0;
-            cs[j].bits = (uint32_t)H + 4u * (uint32_t)nib + 4u * (uint32_t)sume;
+            cs[j].bits = (uint32_t)H + 4u * (uint32_t)nib + (4u << b.gsh) * (uint32_t)sume;
             cs[j].fast = 1;
         }
     }
@@ -260,7 +265,9 @@ __device__ __forceinline__ void profile_chunk3(const TBlock<4> &b, int s, int ge
 
 // One run (kRun consecutive blocks, a level-1 node of the summation tree):
 // the CTA's teams take one block each and write the run's partial sums.
-template <int DT>
+// INL: the run sizes the sum stream itself for the stream decision (the
+// batched kernel); single-array kernels read a.sel instead.
+template <int DT, bool INL>
 __device__ __forceinline__ void profile_run(const ProfArgs &a, uint64_t run, uint8_t *psm)
 {
     using T = DT_<DT>;
@@ -296,17 +303,15 @@ __device__ __forceinline__ void profile_run(const ProfArgs &a, uint64_t run, uin
         __syncthreads();
     }
     int s;
-    {
+    if (!INL && a.sel) {
+        s = j < a.nb ? a.sel[j] : 0;
+    } else {
         TBlock<DT> pv;
-        open_team_block<DT, TS>(pv, x, a.n, a.N, a.nb, j == 0 ? 0 : j - 1, gp, base);
-        uint32_t bb[3];
-        team_eval3<DT, TS>(pv, 0, bb);
-        s = 0;
-        if (bb[1] < bb[s]) s = 1;
-        if (bb[2] < bb[s]) s = 2;
+        open_team_block<DT, TS>(pv, x, a.n, a.N, a.nb, j == 0 ? 0 : j - 1, gp, base, a.gsh);
+        s = team_best_stream<DT, TS>(pv, INL && a.sum != 0);
     }
     TBlock<DT> b;
-    open_team_block<DT, TS>(b, x, a.n, a.N, a.nb, j, gp, base);
+    open_team_block<DT, TS>(b, x, a.n, a.N, a.nb, j, gp, base, a.gsh);
     const bool live = b.active && !b.bad;
     if (b.active && b.bad && t == 0) set_status(a.status, -8);
     const int ge = live ? b.g1 : b.g0;  // my groups [g0, ge)
@@ -486,12 +491,12 @@ __device__ __forceinline__ void profile_run(const ProfArgs &a, uint64_t run, uin
                 // r = x b - q is exact in one FMA (|r| <= 1/2 within 24 bits)
                 // and D' = r 2^24 is an integer whenever q != 0.
                 const float bsc = Q.scale;
+                uint32_t o = 0;  // width terms of the current BFPE group
 #pragma unroll 1
                 for (int g = b.g0; g < ge; ++g) {
                     lt xv[4];
                     load4<DT, true>(b, 4 * g, xv);
                     const int nv = b.L - 4 * g;  // samples of the block from here
-                    uint32_t o = 0;
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         const float xf = __uint_as_float(xv[i]);
@@ -508,15 +513,23 @@ __device__ __forceinline__ void profile_run(const ProfArgs &a, uint64_t run, uin
                         sA += (int64_t)qs * qs;
                         sB += (int64_t)qs * Dp;
                     }
-                    tc.push(exp_from_or(o), true);
+                    if (!b.gsh || (g & 1)) {
+                        tc.push(exp_from_or(o), true);
+                        o = 0;
+                    }
                 }
             } else {
+            uint32_t o = 0;  // width terms of the current BFPE group
 #pragma unroll 1
             for (int g = b.g0; g < ge; ++g) {
                 lt xv[4];
                 load4<DT, true>(b, 4 * g, xv);
                 int32_t qq[4], uu[4];
-                tc.push(exp_from_or(group1q<DT>(qf, xv, sm, qq, uu)), true);
+                o |= group1q<DT>(qf, xv, sm, qq, uu);
+                if (!b.gsh || (g & 1)) {
+                    tc.push(exp_from_or(o), true);
+                    o = 0;
+                }
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     if (4 * g + i >= b.L) continue;
@@ -583,7 +596,7 @@ __device__ __forceinline__ void profile_run(const ProfArgs &a, uint64_t run, uin
         });
         int nib, sume;
         team_tokens<TS>(tc, b.g0 == 0, nib, sume);
-        const uint32_t bits = (uint32_t)H + 4u * (uint32_t)nib + 4u * (uint32_t)sume;
+        const uint32_t bits = (uint32_t)H + 4u * (uint32_t)nib + (4u << b.gsh) * (uint32_t)sume;
         i128 rq, rA, rB, rD = 0;
         if constexpr (DT == 5 || DT == 3) {
             rq = team_sum_i128(wq);
@@ -704,7 +717,7 @@ template <int DT>
 __global__ void __launch_bounds__(128) k_profile(ProfArgs a)
 {
     extern __shared__ __align__(16) uint8_t psm[];
-    profile_run<DT>(a, a.run0 + blockIdx.x, psm);
+    profile_run<DT, false>(a, a.run0 + blockIdx.x, psm);
 }
 
 // The runs of [run0, run1) that the one-block-per-thread sweep marked (rare
@@ -715,7 +728,7 @@ __global__ void __launch_bounds__(128) k_profile_fix(ProfArgs a)
 {
     extern __shared__ __align__(16) uint8_t psm[];
     for (uint64_t r = a.run0 + blockIdx.x; r < a.run1; r += gridDim.x) {
-        if (a.run_flags[r]) profile_run<DT>(a, r, psm);
+        if (a.run_flags[r]) profile_run<DT, false>(a, r, psm);
         __syncthreads();
     }
 }
@@ -829,7 +842,7 @@ __device__ void tree_finalize_cta(const ProfArgs &a, double *s_r)
 template <int DT>
 __device__ __noinline__ void profile_run_call(const ProfArgs &a, uint64_t run, uint8_t *psm)
 {
-    profile_run<DT>(a, run, psm);
+    profile_run<DT, true>(a, run, psm);
 }
 
 // Many arrays' profiler sweeps in one persistent launch: global run
@@ -971,7 +984,23 @@ cudaError_t launch_profile(const ProfArgs &a, cudaStream_t s)
     ProfArgs b = a;
     b.run0 = 0;
     b.run1 = a.nruns;
-    cudaError_t e = launch_profile_runs(b, s);
+    cudaError_t e;
+    if (a.sel) {  // the sum stream: every block's stream decision first
+        SelArgs sa;
+        sa.x = a.x;
+        sa.n = a.n;
+        sa.N = a.N;
+        sa.nb = a.nb;
+        sa.j0 = 0;
+        sa.count = a.nb;
+        sa.dtype = a.dtype;
+        sa.gsh = a.gsh;
+        sa.gp = 0;
+        sa.sel = const_cast<uint8_t *>(a.sel);
+        e = launch_best_streams(sa, s);
+        if (e != cudaSuccess) return e;
+    }
+    e = launch_profile_runs(b, s);
     if (e != cudaSuccess) return e;
     return launch_profile_tree(b, s);
 }

@@ -293,11 +293,7 @@ __global__ void __launch_bounds__(kP, 8) k_profile_f32_t1(ProfArgs a)
             TBlock<4> pv;
             open_team_block<4, 32>(pv, reinterpret_cast<const float *>(a.x), a.n, N, a.nb, jfirst - 1,
                                    (G + 31) / 32);
-            uint32_t bb[3];
-            team_eval3<4, 32>(pv, 0, bb);
-            hb = 0;
-            if (bb[1] < bb[hb]) hb = 1;
-            if (bb[2] < bb[hb]) hb = 2;
+            hb = team_best_stream<4, 32>(pv, false);  // version-1 byte counts only
         }
         if (lane == 0) s_halo = hb;
     }
@@ -518,6 +514,7 @@ __global__ void __launch_bounds__(kP, 8) k_profile_f32_t1(ProfArgs a)
 bool profile_t1_eligible(const ProfArgs &a)
 {
     if (a.dtype != 4 || !a.run_flags || a.N > 256 || a.ncand < 1 || a.codes[0] != 0) return false;
+    if (a.gsh || a.sum) return false;  // version-1 byte counts only
     if (((uintptr_t)a.x & 15) || a.nb < kProfT1MinBlocks) return false;
     for (int c = 1; c < a.ncand; ++c) {
         const uint32_t code = a.codes[c];

@@ -85,8 +85,10 @@ template <int DT>
 struct TBlock {
     using raw = typename DT_<DT>::raw;
     const raw *p;  // first sample of the block
-    int L, G;      // samples, groups
-    int g0, g1;    // this thread's groups [g0, g1) (empty if g1 <= g0)
+    int L, G;      // samples, groups of 4 (padded to whole BFPE groups)
+    int g0, g1;    // this thread's groups of 4 [g0, g1) (empty if g1 <= g0)
+    int gsh;       // log2(BFPE group size / 4): with groups of 8 (gsh = 1)
+                   // G, g0 and g1 are even, so a thread owns whole groups
     int Eb;        // float block exponent
     bool bad;      // a non-finite sample
     bool active;   // the block exists
@@ -362,7 +364,7 @@ __device__ __forceinline__ void team_tokens(const TokCount &c, bool block_first,
 template <int DT, int TS>
 __device__ __forceinline__ void open_team_block(TBlock<DT> &b, const typename DT_<DT>::raw *x,
                                                 uint64_t n, uint32_t N, uint64_t nb, uint64_t j,
-                                                int gp, uint64_t base_block = 0)
+                                                int gp, uint64_t base_block = 0, int gsh = 0)
 {
     using T = DT_<DT>;
     b.active = j < nb;
@@ -370,7 +372,8 @@ __device__ __forceinline__ void open_team_block(TBlock<DT> &b, const typename DT
     // x holds blocks from base_block on (the array itself, or a staged tile)
     b.p = x + (b.active ? off - base_block * (uint64_t)N : 0);
     b.L = b.active ? (int)((n - off) < N ? (n - off) : N) : 0;
-    b.G = (b.L + 3) >> 2;
+    b.gsh = gsh;
+    b.G = gsh ? 2 * ((b.L + 7) >> 3) : (b.L + 3) >> 2;
     const int t = tlane<TS>();
     b.g0 = t * gp;
     b.g1 = min(b.g0 + gp, b.G);
@@ -431,13 +434,16 @@ __device__ __forceinline__ Carry carry_in(const TBlock<DT> &b, const QF &Q, int 
     return c;
 }
 
-// One group, all three streams: OR of the width terms of each stream.
-template <int DT, class QF>
+// One group, all three streams (and the sum stream S3 when SUM): OR of
+// the width terms of each stream.
+template <int DT, bool SUM = false, class QF>
 __device__ __forceinline__ void group3(const QF &Q, const typename LaneT<DT>::t (&xv)[4],
-                                       Carry &c, uint32_t &o0, uint32_t &o1, uint32_t &o2)
+                                       Carry &c, uint32_t &o0, uint32_t &o1, uint32_t &o2,
+                                       uint32_t *o3 = nullptr)
 {
     constexpr int W = DT_<DT>::W;
     o0 = o1 = o2 = 0;
+    uint32_t s3 = 0;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const uint32_t q = (uint32_t)Q(xv[i]);
@@ -445,20 +451,23 @@ __device__ __forceinline__ void group3(const QF &Q, const typename LaneT<DT>::t 
         o0 |= bits_term((int32_t)q);  // q is already a W-bit value
         o1 |= bits_term(sext_w(u1, W));
         o2 |= bits_term(sext_w(u2, W));
+        if constexpr (SUM) s3 |= bits_term(sext_w(q + c.qp1, W));
         c.qp1 = q;
         c.qpp2 = c.qp2;
         c.qp2 = q;
     }
+    if constexpr (SUM) *o3 = s3;
 }
 
 // One stream s: coefficients of u = q - a qp + bb qpp and its carries.
+// S3, the sum stream, is a = -1 on the S1 carry: u_0 = q_0, u_i = q_i + q_{i-1}.
 struct Stream1 {
     uint32_t a, bb, qp, qpp;
     __device__ __forceinline__ Stream1(int s, const Carry &c)
     {
-        a = s == 0 ? 0u : (s == 1 ? 1u : 2u);
+        a = s == 0 ? 0u : (s == 1 ? 1u : (s == 2 ? 2u : 0xffffffffu));
         bb = s == 2 ? 1u : 0u;
-        qp = s == 1 ? c.qp1 : c.qp2;
+        qp = (s == 1 || s == 3) ? c.qp1 : c.qp2;
         qpp = c.qpp2;
     }
 };
@@ -543,32 +552,72 @@ struct Tok3 {
     }
 };
 
-// Unpadded packet bits of the team's block for all three streams at `code`
-// (the stream decision of Sec. 6 evaluates them at code 0).
-template <int DT, int TS>
-__device__ __forceinline__ void team_eval3(const TBlock<DT> &b, int code, uint32_t (&bits)[3])
+// Unpadded packet bits of the team's block for streams S0-S2 (and S3 when
+// SUM) at `code` (the stream decision of Sec. 6 evaluates them at code 0).
+// With groups of 8 the width terms of two groups of 4 are ORed before an
+// exponent is counted.
+template <int DT, int TS, bool SUM>
+__device__ __forceinline__ void team_eval_streams(const TBlock<DT> &b, int code, uint32_t (&bits)[4])
 {
     const Quant<DT> Q(code, b.Eb);
     Tok3 tk;
     tk.init();
+    TokCount t3;
+    t3.init();
     with_quant<DT>(Q, [&](const auto &qf) {
         Carry c = carry_in<DT>(b, qf, 4 * b.g0);
+        uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;
 #pragma unroll 1
         for (int g = b.g0; g < b.g1; ++g) {
             typename LaneT<DT>::t xv[4];
             load4<DT, true>(b, 4 * g, xv);
-            uint32_t o0, o1, o2;
-            group3<DT>(qf, xv, c, o0, o1, o2);
-            tk.push(exp_from_or(o0), exp_from_or(o1), exp_from_or(o2));
+            uint32_t o0, o1, o2, o3 = 0;
+            group3<DT, SUM>(qf, xv, c, o0, o1, o2, &o3);
+            a0 |= o0;
+            a1 |= o1;
+            a2 |= o2;
+            a3 |= o3;
+            if (!b.gsh || (g & 1)) {
+                tk.push(exp_from_or(a0), exp_from_or(a1), exp_from_or(a2));
+                if constexpr (SUM) t3.push(exp_from_or(a3), true);
+                a0 = a1 = a2 = a3 = 0;
+            }
         }
     });
     const bool first = b.g0 == 0;
+    const uint32_t wm = 4u << b.gsh;  // mantissa bits per exponent unit
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
         int nib, sume;
         team_tokens<TS>(tk.lane(s), first, nib, sume);
-        bits[s] = (uint32_t)DT_<DT>::H + 4u * (uint32_t)nib + 4u * (uint32_t)sume;
+        bits[s] = (uint32_t)DT_<DT>::H + 4u * (uint32_t)nib + wm * (uint32_t)sume;
     }
+    bits[3] = 0xffffffffu;
+    if constexpr (SUM) {
+        int nib, sume;
+        team_tokens<TS>(t3, first, nib, sume);
+        bits[3] = (uint32_t)DT_<DT>::H + 4u * (uint32_t)nib + wm * (uint32_t)sume;
+    }
+}
+
+template <int DT, int TS>
+__device__ __forceinline__ uint32_t team_eval1(const TBlock<DT> &b, int code, int s);
+
+// The stream of fewest code-0 bits among S0-S2, and S3 when `sum` (ties to
+// the lower index).  Warp-uniform `sum`.  S3 is sized by a second pass over
+// the block (version-2 containers only), which keeps the version-1 pass's
+// registers.
+template <int DT, int TS>
+__device__ __forceinline__ int team_best_stream(const TBlock<DT> &b, bool sum)
+{
+    uint32_t bb[4];
+    team_eval_streams<DT, TS, false>(b, 0, bb);
+    if (sum) bb[3] = team_eval1<DT, TS>(b, 0, 3);
+    int s = 0;
+    if (bb[1] < bb[s]) s = 1;
+    if (bb[2] < bb[s]) s = 2;
+    if (bb[3] < bb[s]) s = 3;
+    return s;
 }
 
 // Unpadded packet bits of the team's block for stream s at `code`.
@@ -580,21 +629,26 @@ __device__ __forceinline__ uint32_t team_eval1(const TBlock<DT> &b, int code, in
     tc.init();
     with_quant<DT>(Q, [&](const auto &qf) {
         Stream1 st(s, carry_in<DT>(b, qf, 4 * b.g0));
+        uint32_t acc = 0;
 #pragma unroll 1
         for (int g = b.g0; g < b.g1; ++g) {
             typename LaneT<DT>::t xv[4];
             load4<DT, true>(b, 4 * g, xv);
             int32_t u[4];
-            tc.push(exp_from_or(group1<DT>(qf, xv, st, u)), true);
+            acc |= group1<DT>(qf, xv, st, u);
+            if (!b.gsh || (g & 1)) {
+                tc.push(exp_from_or(acc), true);
+                acc = 0;
+            }
         }
     });
     int nib, sume;
     team_tokens<TS>(tc, b.g0 == 0, nib, sume);
-    return (uint32_t)DT_<DT>::H + 4u * (uint32_t)nib + 4u * (uint32_t)sume;
+    return (uint32_t)DT_<DT>::H + 4u * (uint32_t)nib + (4u << b.gsh) * (uint32_t)sume;
 }
 
-// team_eval1 at code 0 that also leaves each group's exponent in ebuf[g]
-// (this thread's groups; the team's groups together).
+// team_eval1 at code 0 that also leaves each BFPE group's exponent in
+// ebuf[g >> gsh] (this thread's groups; the team's groups together).
 template <int DT, int TS>
 __device__ __forceinline__ uint32_t team_exps(const TBlock<DT> &b, int s, uint8_t *ebuf)
 {
@@ -603,19 +657,24 @@ __device__ __forceinline__ uint32_t team_exps(const TBlock<DT> &b, int s, uint8_
     tc.init();
     with_quant<DT>(Q, [&](const auto &qf) {
         Stream1 st(s, carry_in<DT>(b, qf, 4 * b.g0));
+        uint32_t acc = 0;
 #pragma unroll 1
         for (int g = b.g0; g < b.g1; ++g) {
             typename LaneT<DT>::t xv[4];
             load4<DT, true>(b, 4 * g, xv);
             int32_t u[4];
-            const int e = exp_from_or(group1<DT>(qf, xv, st, u));
-            ebuf[g] = (uint8_t)e;
-            tc.push(e, true);
+            acc |= group1<DT>(qf, xv, st, u);
+            if (!b.gsh || (g & 1)) {
+                const int e = exp_from_or(acc);
+                ebuf[g >> b.gsh] = (uint8_t)e;
+                tc.push(e, true);
+                acc = 0;
+            }
         }
     });
     int nib, sume;
     team_tokens<TS>(tc, b.g0 == 0, nib, sume);
-    return (uint32_t)DT_<DT>::H + 4u * (uint32_t)nib + 4u * (uint32_t)sume;
+    return (uint32_t)DT_<DT>::H + 4u * (uint32_t)nib + (4u << b.gsh) * (uint32_t)sume;
 }
 
 // ---------------------------------------------------------------- staging

@@ -51,6 +51,15 @@ def _spectral_field(shape, slope: float, rng) -> np.ndarray:
     return f / f.std()
 
 
+def nyquist_trace(n: int = 262144, seed: int = 0) -> np.ndarray:
+    """The sensor trace with its spectrum mirrored to the Nyquist band:
+    x_i (-1)^i, tones at 0.5 - f (the data that alternate in sign, where
+    neighbouring samples are anti-correlated; Sec. 5 Fig. 3b)."""
+    x = sensor_trace(n, seed).astype(np.int32)
+    x[1::2] = -x[1::2]
+    return np.clip(x, -32768, 32767).astype(np.int16)
+
+
 def grf2d(h: int = 4096, w: int = 4096, seed: int = 1, slope: float = 3.0,
           noise: float = 1e-3) -> np.ndarray:
     rng = np.random.default_rng(seed)
