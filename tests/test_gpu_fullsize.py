@@ -56,15 +56,15 @@ def _packets(container: bytes, nb: int, mode: int, budget: int = 0):
     return out
 
 
-def _profiled_fq_parity(x, dtype, target):
+def _profiled_fq_parity(x, dtype, target, fmt=0):
     """Profile -> fixed-quality encode at the recommended code -> decode on
     the whole array, each result against the oracle's whole-array result."""
     n = x.size
     xt = torch.from_numpy(x).cuda()
     nc = 16
     pws, pts, summ = A.profile_buffers(xt, N, nc)
-    A.profile_into(xt, N, list(A.DEFAULT_CANDIDATES), target, pws, pts, summ)
-    p = A.params(N, A.FIXED_QUALITY)
+    A.profile_into(xt, N, list(A.DEFAULT_CANDIDATES), target, pws, pts, summ, fmt=fmt)
+    p = A.params(N, A.FIXED_QUALITY, fmt=fmt)
     tcode = A.F32 if dtype == np.float32 else A.F64
     out = torch.empty(A.encoded_size(tcode, n, p), dtype=torch.uint8, device="cuda")
     ws = torch.empty(A.workspace_size(tcode, n, p), dtype=torch.uint8, device="cuda")
@@ -81,7 +81,7 @@ def _profiled_fq_parity(x, dtype, target):
     assert point.bytes == r.bytes  # exact size prediction
     del ws, pws
     # every profile point of the whole array, bit for bit
-    opts, orec, omiss = O.profile(x, N, list(A.DEFAULT_CANDIDATES), target, threads=0)
+    opts, orec, omiss = O.profile(x, N, list(A.DEFAULT_CANDIDATES), target, threads=0, fmt=fmt)
     assert sm.recommended == orec and bool(sm.flags & 1) == omiss
     for g, o in zip(gpts, opts):
         assert (g.code, g.bytes) == (o.code, o.bytes)
@@ -89,7 +89,7 @@ def _profiled_fq_parity(x, dtype, target):
             assert struct.pack("<d", getattr(g, f)) == struct.pack("<d", getattr(o, f)), (g.code, f)
     # the whole container and the whole decoded array
     cont = out[:r.bytes].cpu().numpy().tobytes()
-    want = O.encode(x, N, O.MODE_FQ, 1, 1, code, threads=0)
+    want = O.encode(x, N, O.MODE_FQ, 1, 1, code, threads=0, fmt=fmt)
     assert len(cont) == len(want)
     assert cont == want
     y = A.decode(out[:r.bytes], torch.float32 if dtype == np.float32 else torch.float64, n)
@@ -102,6 +102,26 @@ def _profiled_fq_parity(x, dtype, target):
 
 def test_field_4096_full_size_parity():
     _profiled_fq_parity(synth.grf2d(4096, 4096, seed=1).reshape(-1), np.float32, 0.9999)
+
+
+def test_field_4096_full_size_parity_version2():
+    # the same workload in a version-2 container (groups of 8, the sum
+    # stream): the team sweep sizes the packets, the pre-pass picks streams
+    _profiled_fq_parity(synth.grf2d(4096, 4096, seed=1).reshape(-1), np.float32, 0.9999,
+                        fmt=A.FORMAT_GROUP8 | A.FORMAT_SUM_STREAM)
+
+
+def test_nyquist_replica_version2_parity():
+    # 1,024 copies of the Nyquist-band int16 trace, lossless, in every
+    # format: the sum stream's decoder paths at 1,024 x 1,024 blocks
+    x = np.tile(synth.nyquist_trace(), 1024)
+    xt = torch.from_numpy(x).cuda()
+    for fmt in (A.FORMAT_SUM_STREAM, A.FORMAT_GROUP8 | A.FORMAT_SUM_STREAM):
+        c = A.encode(xt, 256, A.FIXED_QUALITY, (1, 1), 0, fmt=fmt)
+        want = O.encode(x, 256, O.MODE_FQ, 1, 1, 0, threads=0, fmt=fmt)
+        assert c.cpu().numpy().tobytes() == want
+        y = A.decode(c, torch.int16, x.size)
+        assert torch.equal(y, xt)  # lossless
 
 
 def test_field3d_512_full_size_parity():
