@@ -15,9 +15,10 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libapax_gb300.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["apax_host.cu", "apax_encode.cu", "apax_decode.cu", "apax_profile.cu", "apax_profile_t1.cu", "apax_quality.cu",
-           "apax_select.cu",
+           "apax_select.cu", "apax_encode_res.cu",
            "apax_noalloc.cu", "apax_batch.cu", "apax_server.cu"]
-HEADERS = ["apax_device.cuh", "apax_team.cuh", "apax_exact.cuh", "apax_kernels.h", "apax_plan.h"]
+HEADERS = ["apax_device.cuh", "apax_team.cuh", "apax_exact.cuh", "apax_kernels.h", "apax_plan.h",
+           "apax_encode.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-fmad=false",
          "--expt-relaxed-constexpr", "-Xptxas", "-warn-spills"]

@@ -156,7 +156,9 @@ int encode_impl(const void *x, int dtype, uint64_t n, const apax_params *p,
     // teams (13 passes over a block), off for fixed quality, whose occupancy
     // matters more than its few L2 re-reads (measured on GB300)
     const bool want = p->mode == APAX_FIXED_RATE;
-    const size_t sb = (want && pl.ts != 1) ? stage_bytes(f.size, a.N, pl.threads / pl.ts, pl.smem) : 0;
+    // blocks that fit a team's registers are read from global memory once
+    const bool in_regs = pl.ts != 1 && encode_res_eligible(dtype, p->mode, a.N, pl.ts);
+    const size_t sb = (want && pl.ts != 1 && !in_regs) ? stage_bytes(f.size, a.N, pl.threads / pl.ts, pl.smem) : 0;
     a.stage_off = sb ? (uint32_t)((pl.smem + 15) / 16 * 16) : 0;
     if (sb) pl.smem = a.stage_off + sb;
     a.gp = pl.gp;
@@ -200,6 +202,7 @@ int encode_impl(const void *x, int dtype, uint64_t n, const apax_params *p,
         if (st) return st;
         a.sel = sel;
     }
+    if (in_regs) return cuda_fail(launch_encode_res(a, pl.threads, pl.smem, s));
     return cuda_fail(launch_encode(a, pl.ts, pl.threads, pl.smem, s));
 }
 

@@ -208,6 +208,10 @@ bool profile_t1_eligible(const ProfArgs &a);
 cudaError_t launch_profile_t1(const ProfArgs &a, cudaStream_t s);
 
 cudaError_t launch_encode(const EncArgs &a, int ts, int threads, size_t smem, cudaStream_t s);
+// Single arrays whose blocks fit the registers of a team of 8 (fixed
+// quality, at most 256 samples of int8, int16 or float32): apax_encode_res.cu.
+bool encode_res_eligible(int dtype, int mode, uint32_t N, int ts);
+cudaError_t launch_encode_res(const EncArgs &a, int threads, size_t smem, cudaStream_t s);
 
 // Stream decisions of blocks [j0, j0 + count) of an array with the sum
 // stream into sel[0, count) (apax_select.cu).
