@@ -10,8 +10,9 @@
 // with the padding of Sec. 6 packets already in place, and every pass runs on
 // the registers:
 //   1. the block maximum (float block exponent);
-//   2. its own code-0 stream sizes, i.e. the decision its successor uses; the
-//      tile's first team also sizes the block before the tile (the halo);
+//   2. its own code-0 stream sizes, i.e. the decision its successor uses;
+//      warp 0 also sizes the block before the tile (the halo), as one team
+//      of 32 so that the other warps' wait at the barrier is short;
 //   3. after one CTA barrier, the stream of block j is the decision of team
 //      j - 1 (block 0 keeps its own);
 //   4. exponents and JEE tokens at the given code, then the mantissas, into
@@ -225,11 +226,15 @@ __device__ __forceinline__ void encode_tile_res(const EncArgs &a, uint64_t tile,
     } else {
         const int own = res_best_stream<DT>(b, xr, l2, l3, t);
         if (t == 0) s_dec[team] = own;
-        if (threadIdx.x < 32) {  // warp 0: the block before the tile (team 0's lanes)
+        if (threadIdx.x < 32) {
+            // warp 0, as one team of 32: the block before the tile (the
+            // other warps wait for it at the barrier, so all its lanes share it)
             TBlock<DT> pv;
-            const bool halo = team == 0 && jb > 0 && jb < a.nb;
-            open_team_block<DT, TS>(pv, x, a.n, a.N, halo ? a.nb : 0, halo ? jb - 1 : 0, gp, 0, a.gsh);
-            const int hs = team_best_stream<DT, TS>(pv, false);
+            const bool halo = jb > 0 && jb < a.nb;
+            const int gp32 = b.gsh ? 2 * (int)((a.N / 8 + 31) / 32) : (int)((a.N / 4 + 31) / 32);
+            open_team_block<DT, 32>(pv, x, a.n, a.N, halo ? a.nb : 0, halo ? jb - 1 : 0, gp32, 0,
+                                    a.gsh);
+            const int hs = team_best_stream<DT, 32>(pv, false);
             if (threadIdx.x == 0) s_halo = hs;
         }
         __syncthreads();
