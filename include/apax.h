@@ -240,7 +240,7 @@ int apax_profile_format(const void *x, int dtype, uint64_t n, uint32_t block_siz
  * cudaHostAlloc), leaving its copy in x_dev (device, n elements of dtype):
  * the array goes to the device in `chunks` pieces (1..64, whole runs of 16
  * blocks each) with cudaMemcpyAsync on copy_stream, and each piece is swept
- * as soon as it is there, on one of four library-owned streams (created on
+ * as soon as it is there, on one of sixteen library-owned streams (created on
  * first use per device and kept for the process's CUDA context, so not
  * valid across cudaDeviceReset), so the copy hides behind the sweep.  The copies and
  * sweeps first wait for the work queued on `stream` before the call; work

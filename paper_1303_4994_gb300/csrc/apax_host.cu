@@ -264,7 +264,7 @@ int decode_impl(const void *in, uint64_t in_bytes, uint64_t b0, uint64_t b1, boo
 // Streams on which the host-input sweep runs its pieces: created once per
 // device (non-blocking, for the life of the process's CUDA context) and
 // reused.
-constexpr int kSweepStreams = 4;
+constexpr int kSweepStreams = 16;
 static bool sweep_streams(cudaStream_t (&out)[kSweepStreams])
 {
     static std::mutex mu;
