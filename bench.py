@@ -14,8 +14,10 @@ host-input sweep (the array crosses in pieces on a copy stream while pieces
 already there are swept), encode, decode, and the copy of the container, the
 profile points and the decoded array back.  `cpu_baseline` is the oracle on
 every host core (threads over block ranges) and, beside it, on one core.
-At N = 1 the default run also measures the int16 sensor trace at 4:1 and
-the float64 512^3 field (`workloads`).
+At N = 1 the default run also measures (`workloads`) the int16 sensor trace
+at 4:1, the float64 512^3 field, the version-2 container formats, the
+batched workload (all 8,192 arrays, 3 timed runs of each operation) and the
+serving workload (10 s of arrivals).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                   [--workload field|sensor|field3d|batched|serving]
@@ -29,7 +31,7 @@ Other workloads (one GPU):
            decode and the profiler sweep, against the plain per-array loop.
   sensor   int16 trace at 4:1: single-call latency, and GB/s on 8,192 copies.
   field3d  float64 512^3 field (1 GiB): profile -> fixed quality -> decode.
-  serving  Poisson arrivals (2,000 requests/s, 50/50 encode/decode, 64 KB..
+  serving  Poisson arrivals (2,000 requests/s for --serve-seconds, 50/50 encode/decode, 64 KB..
            256 MB of float32 field slices at a fixed quality or int16 traces
            at 4:1) through the request server with a 64 GB admission cap:
            open-loop p50/p99 latency, then a closed-loop replay of the same
@@ -404,9 +406,16 @@ def run_ours(args, rank, world, local_rank):
         line["cpu_baseline"]["single_core"] = cpu_baseline(rows=CPU_ROWS_1CORE, threads=None)
     if world == 1 and rank == 0 and not args.no_extra:
         # the other single-GPU workloads, measured in the same run
-        line["workloads"] = {"sensor_i16_fr4": run_sensor(args, compact=True),
-                             "field3d_f64_512": run_field3d(args, compact=True),
-                             "formats_v2": run_formats(args)}
+        import torch
+        wl = {}
+        for name, fn in (("sensor_i16_fr4", lambda: run_sensor(args, compact=True)),
+                         ("field3d_f64_512", lambda: run_field3d(args, compact=True)),
+                         ("formats_v2", lambda: run_formats(args)),
+                         ("batched_8192", lambda: run_batched(args, compact=True)),
+                         ("serving", lambda: run_serving(args, compact=True))):
+            wl[name] = fn()
+            torch.cuda.empty_cache()  # the next workload's arrays need the room
+        line["workloads"] = wl
     return line
 
 
@@ -479,7 +488,11 @@ def _wrapped(master, off, n):
     return torch.cat(parts) if len(parts) > 1 else parts[0].clone()
 
 
-def run_batched(args):
+def run_batched(args, compact=False):
+    """The batched workload (8,192 arrays, 56.6 GB by default): one persistent
+    launch per operation against the plain per-array loop.  compact: the
+    default run's version, 3 timed repetitions of each of the six runs and a
+    short summary."""
     import torch
 
     from paper_1303_4994_gb300 import apax as A
@@ -540,12 +553,13 @@ def run_batched(args):
     runs = {"batched_encode": lambda: eplan.run(stream), "plain_encode": plain_enc,
             "batched_decode": lambda: dplan.run(stream), "plain_decode": plain_dec,
             "batched_profile": lambda: pplan.run(stream), "plain_profile": plain_prof}
+    reps = 3 if compact else args.steps
     for fn in runs.values():
-        for _ in range(max(args.warmup, 3)):
+        for _ in range(2 if compact else max(args.warmup, 3)):
             fn()
     torch.cuda.synchronize()
     with Clocks(0) as clk:
-        ms = {name: timed(fn, args.steps) for name, fn in runs.items()}
+        ms = {name: timed(fn, reps) for name, fn in runs.items()}
     # the batched containers are the plain loop's, byte for byte
     eplan.run(stream)
     plain_enc()
@@ -557,6 +571,16 @@ def run_batched(args):
     gbs = {name: total / t / 1e6 for name, t in ms.items()}
     peak, peak_kind = _peaks()
     step_ms = ms["batched_encode"] + ms["batched_decode"]
+    if compact:
+        return {"workload": f"batched: {k} arrays 4 KB..64 MB ({total / 1e9:.1f} GB), "
+                            "int16/int32/float32/float64, fixed rate 2:1/3:1/4:1/6:1, N=256 "
+                            "(seed 3); medians of 3 runs of each",
+                "gbs_uncompressed": {n: round(v, 2) for n, v in gbs.items()},
+                "batched_vs_plain": {op: round(ms["plain_" + op] / ms["batched_" + op], 3)
+                                     for op in ("encode", "decode", "profile")},
+                "hbm_frac_batched_decode": round((total + comp) / ms["batched_decode"] / 1e6 / peak, 4),
+                "ratio": round(total / comp, 4),
+                "containers_identical_to_plain": bool(same), "clocks": clk.summary()}
     return {
         "metric": METRIC, "value": round(total / step_ms / 1e6, 3), "unit": "GB/s", "n_gpus": 1,
         "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(step_ms, 3),
@@ -806,7 +830,10 @@ def run_formats(args):
     return out
 
 
-def run_serving(args):
+def run_serving(args, compact=False):
+    """Poisson arrivals at 2,000 requests/s for --serve-seconds (the default
+    run: 10 s): open loop (latency) and closed loop (throughput) through the
+    request server, against the plain per-request path."""
     import torch
 
     from paper_1303_4994_gb300 import apax as A
@@ -817,7 +844,8 @@ def run_serving(args):
     A.lib()
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
-    trace = synth.serving_trace(args.serve_seconds)
+    seconds = 10.0 if compact else args.serve_seconds
+    trace = synth.serving_trace(seconds)
     # device-resident payload pools (float32 field, int16 trace), 4 GB each
     field = torch.from_numpy(synth.grf2d(4096, 4096, seed=1).reshape(-1)).to(dev)
     pool = {"float32": field.repeat(16),
@@ -898,15 +926,24 @@ def run_serving(args):
     torch.cuda.synchronize()
     plain_gbs = sum(r[5] for r in reqs) / (time.perf_counter() - t0) / 1e9
     total = sum(r[5] for r in reqs)
+    if compact:
+        return {"workload": f"serving: Poisson 2000 req/s for {seconds:g} s ({len(reqs)} requests, "
+                            f"{total / 1e9:.1f} GB), 50/50 encode/decode, 64 KB..256 MB float32 "
+                            f"(fixed quality, code {code}) / int16 (4:1) (seed 4)",
+                "open_loop": {"gbs": round(gbs_open, 3), "offered_gbs": round(total / seconds / 1e9, 3),
+                              "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
+                              "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3)},
+                "closed_loop_gbs": round(gbs_closed, 3), "plain_per_request_gbs": round(plain_gbs, 3),
+                "served_vs_plain": round(gbs_closed / plain_gbs, 3)}
     return {
         "metric": METRIC, "value": round(gbs_closed, 3), "unit": "GB/s", "n_gpus": 1,
         "steps": 1, "warmup": 0, "ms_per_step": None, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "mixed", "data": "synthetic",
-        "config": {"workload": f"serving: Poisson 2000 req/s for {args.serve_seconds} s, 50/50 "
+        "config": {"workload": f"serving: Poisson 2000 req/s for {seconds:g} s, 50/50 "
                                "encode/decode, 64 KB..256 MB float32 (fixed quality, code "
                                f"{code}) / int16 (4:1), 64 GB admission cap (seed 4)",
                    "requests": len(reqs), "bytes": total, "slots": 4, "max_batch": 256},
-        "open_loop": {"gbs": round(gbs_open, 3), "offered_gbs": round(total / args.serve_seconds / 1e9, 3),
+        "open_loop": {"gbs": round(gbs_open, 3), "offered_gbs": round(total / seconds / 1e9, 3),
                       "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
                       "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3),
                       "steps": st_open["steps"], "arena_peak_gb": round(st_open["arena_peak"] / 1e9, 3)},
@@ -932,7 +969,7 @@ def main():
                     choices=["field", "batched", "serving", "sensor", "field3d"])
     ap.add_argument("--field3d-n", type=int, default=512)
     ap.add_argument("--arrays", type=int, default=8192)
-    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
     args = ap.parse_args()
     if args.workload != "field" and args.impl == "ours":
         import torch
