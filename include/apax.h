@@ -162,6 +162,19 @@ int apax_encode_recommended(const void *x, int dtype, uint64_t n, const apax_par
                             uint64_t out_capacity, void *workspace, uint64_t workspace_bytes,
                             apax_result *res, void *stream);
 
+/* Copy a container out without a host round trip: the first
+ * min(res->bytes, capacity) bytes of src (as apax_encode and
+ * apax_encode_recommended leave them: res->bytes is read on the device when
+ * the copy runs) to dst, by a kernel on `stream`.  dst may be device memory
+ * or page-locked host memory mapped into the device address space (the
+ * kernel then writes it over the host link), so a caller need not wait for
+ * the encode to learn the size before moving the container to the host.
+ * src and dst must be 4-byte aligned and must not overlap; enqueue the copy
+ * after the encode that wrote src and res (same stream, or an event).  Not
+ * a step of the paper's method: a transfer helper for its output. */
+int apax_copy_container(const void *src, const apax_result *res, void *dst, uint64_t capacity,
+                        void *stream);
+
 /* Device workspace bytes of apax_decode / apax_decode_blocks (a status word,
  * one completion counter per launch and the block-per-thread tile counter). */
 uint64_t apax_decode_workspace_size(void);

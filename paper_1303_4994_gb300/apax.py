@@ -128,6 +128,7 @@ RESULT_BYTES = 16
 _lib = None
 
 EXPORTS = ("apax_encoded_size", "apax_workspace_size", "apax_encode", "apax_encode_recommended",
+           "apax_copy_container",
            "apax_decode_workspace_size", "apax_decode", "apax_decode_blocks",
            "apax_profile_workspace_size", "apax_profile", "apax_profile_format",
            "apax_profile_from_host",
@@ -159,6 +160,7 @@ def lib():
         L.apax_workspace_size.argtypes = [i32, u64, pP, p64]
         L.apax_encode.argtypes = [vp, i32, u64, pP, vp, u64, vp, u64, vp, vp]
         L.apax_encode_recommended.argtypes = [vp, i32, u64, pP, vp, vp, u64, vp, u64, vp, vp]
+        L.apax_copy_container.argtypes = [vp, vp, vp, u64, vp]
         L.apax_decode_workspace_size.argtypes = []
         L.apax_decode_workspace_size.restype = u64
         L.apax_decode.argtypes = [vp, u64, vp, i32, u64, vp, u64, vp, vp]
@@ -327,6 +329,14 @@ def encode(x: torch.Tensor, block_size: int = 256, mode: int = FIXED_QUALITY, ra
     r = read_result(res)
     _check(r.status, "encode (device)")
     return out[:r.bytes]
+
+
+def copy_container_into(out: torch.Tensor, res: torch.Tensor, dst: torch.Tensor, stream=None):
+    """Enqueue apax_copy_container: the container in `out` (its size read on
+    the device from `res`) into `dst` (a uint8 device tensor or a pinned
+    host tensor), with no host round trip."""
+    _check(lib().apax_copy_container(out.data_ptr(), res.data_ptr(), dst.data_ptr(), dst.numel(),
+                                     _stream(stream)), "copy_container")
 
 
 def encode_noalloc_into(x: torch.Tensor, p: Params, out: torch.Tensor, res: torch.Tensor,

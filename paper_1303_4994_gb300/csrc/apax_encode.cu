@@ -627,6 +627,25 @@ __global__ void k_table_rebase(const uint32_t *src, uint32_t *dst, uint64_t coun
         dst[i] = (uint32_t)((uint64_t)src[i] + add);  // the host checked the 2^32-word limit
 }
 
+// The first min(res->bytes, cap) bytes of src to dst (both 4-byte aligned,
+// containers are whole words); 16-byte pieces when both are 16-byte aligned.
+__global__ void k_copy_sized(const uint8_t *src, const apax_result *res, uint8_t *dst, uint64_t cap)
+{
+    const uint64_t rb = *(const volatile uint64_t *)&res->bytes;
+    const uint64_t bytes = (rb < cap ? rb : cap) & ~3ull;
+    const uint64_t t0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
+    uint64_t done = 0;
+    if ((((uintptr_t)src | (uintptr_t)dst) & 15) == 0) {
+        const uint64_t n16 = bytes >> 4;
+        for (uint64_t i = t0; i < n16; i += step)
+            reinterpret_cast<uint4 *>(dst)[i] = reinterpret_cast<const uint4 *>(src)[i];
+        done = n16 << 4;
+    }
+    for (uint64_t i = (done >> 2) + t0; i < (bytes >> 2); i += step)
+        reinterpret_cast<uint32_t *>(dst)[i] = reinterpret_cast<const uint32_t *>(src)[i];
+}
+
 __global__ void k_merged_header(EncArgs a, uint64_t payload)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -653,6 +672,17 @@ cudaError_t launch_table_rebase(const uint32_t *src, uint32_t *dst, uint64_t cou
 cudaError_t launch_merged_header(const EncArgs &a, uint64_t payload, cudaStream_t s)
 {
     k_merged_header<<<1, 32, 0, s>>>(a, payload);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_sized(const void *src, const apax_result *res, void *dst, uint64_t cap,
+                              cudaStream_t s)
+{
+    const uint64_t need = (cap + 16 * 256 - 1) / (16 * 256);  // CTAs for one 16-byte piece a thread
+    const uint64_t most = 4ull * (uint64_t)sm_count();
+    const unsigned ctas = (unsigned)(need < most ? (need ? need : 1) : most);
+    k_copy_sized<<<ctas, 256, 0, s>>>(reinterpret_cast<const uint8_t *>(src), res,
+                                      reinterpret_cast<uint8_t *>(dst), cap);
     return cudaGetLastError();
 }
 

@@ -343,6 +343,17 @@ int apax_encoded_size(int dtype, uint64_t n, const apax_params *p, uint64_t *byt
     return APAX_OK;
 }
 
+int apax_copy_container(const void *src, const apax_result *res, void *dst, uint64_t capacity,
+                        void *stream)
+{
+    if (!src || !res || !dst || ((uintptr_t)src & 3) || ((uintptr_t)dst & 3) || ((uintptr_t)res & 7))
+        return APAX_ERR_INVALID_ARG;
+    const uintptr_t s0 = (uintptr_t)src, d0 = (uintptr_t)dst;
+    if (capacity && s0 < d0 + capacity && d0 < s0 + capacity) return APAX_ERR_INVALID_ARG;
+    if (!capacity) return APAX_OK;
+    return cuda_fail(launch_copy_sized(src, res, dst, capacity, (cudaStream_t)stream));
+}
+
 int apax_workspace_size(int dtype, uint64_t n, const apax_params *p, uint64_t *bytes)
 {
     Fmt f;

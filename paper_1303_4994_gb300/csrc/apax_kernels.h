@@ -232,6 +232,9 @@ cudaError_t launch_best_streams(const SelArgs &a, cudaStream_t s);
 cudaError_t launch_table_rebase(const uint32_t *src, uint32_t *dst, uint64_t count, uint64_t add,
                                 cudaStream_t s);
 cudaError_t launch_merged_header(const EncArgs &a, uint64_t payload, cudaStream_t s);
+// dst[0, min(res->bytes, cap)) = src[...], the size read on the device.
+cudaError_t launch_copy_sized(const void *src, const apax_result *res, void *dst, uint64_t cap,
+                              cudaStream_t s);
 cudaError_t launch_encode_batch(const EncBatchArgs &b, int ts, int threads, size_t smem,
                                unsigned ctas, cudaStream_t s);
 int encode_batch_occupancy(int ts, int threads, size_t smem);  // CTAs per SM
