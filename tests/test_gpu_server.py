@@ -110,6 +110,7 @@ def test_server_mix_equals_alone():
             assert want.tobytes() == O.encode(x, 256, p.mode, p.rate_num, p.rate_den, p.atten_code)
         else:
             assert got[i].tobytes() == want.tobytes(), i
+            assert want.tobytes() == O.decode(c, x.dtype, x.size).tobytes(), i
 
 
 def test_server_small_arena_throttles_admission():
@@ -120,6 +121,8 @@ def test_server_small_arena_throttles_admission():
     assert st["completed"] == len(reqs) and peak <= cap
     for i, (op, x, p, c) in enumerate(reqs):
         assert got[i].tobytes() == _alone(op, x, p, c).tobytes(), i
+        if op == A.OP_DECODE:
+            assert got[i].tobytes() == O.decode(c, x.dtype, x.size).tobytes(), i
 
 
 def test_server_rejects_bad_requests_at_submit():
