@@ -256,14 +256,9 @@ def run_ours(args, rank, world, local_rank):
         enc()
         dec()
 
-    nruns = (n // N_BLOCK + 15) // 16
-    levels = 0
-    c = nruns
-    while c > 1:
-        c = (c + 15) // 16
-        levels += 1
-    # profile, tree levels, finalize, encode, decode (two size classes)
-    launches_per_step = 1 + levels + 1 + 1 + 2
+    # profile (the one-block-per-thread sweep, the fix-up sweep of the runs it
+    # marks, the tree with the finalisation), encode, decode (two size classes)
+    launches_per_step = _profile_launches(n, A.F32) + 1 + 2
 
     # the whole step (memsets and kernels of the three calls) as one CUDA
     # graph: the timed step replays it, without per-launch gaps (one eager
@@ -477,11 +472,12 @@ def run_reference(args, rank, world):
                     "d2h_bytes_per_step": 0}}
 
 
-def _tree_levels(n):
-    c, lv = (n // N_BLOCK + 15) // 16, 0
-    while c > 1:
-        c, lv = (c + 15) // 16, lv + 1
-    return lv
+def _profile_launches(n, dtype_code):
+    """Kernels of one apax_profile call at block size N_BLOCK: the float32
+    one-block-per-thread sweep and its fix-up sweep, or the team sweep;
+    then one tree launch."""
+    t1 = dtype_code == 4 and (n + N_BLOCK - 1) // N_BLOCK >= 16384 and N_BLOCK <= 256
+    return (2 if t1 else 1) + 1
 
 
 def _wrapped(master, off, n):
@@ -621,7 +617,8 @@ def run_batched(args, compact=False):
                      "unit": "GB/s",
                      "frac": (total + comp) / ms["batched_decode"] / 1e6 / peak,
                      "traffic": None, "peak_source": f"{peak_kind} hbm_gbs"},
-        "gpu_launches": args.steps * (3 + k + 2 * k + sum(2 + _tree_levels(x.numel()) for x in xs)),
+        "gpu_launches": reps * (3 + k + 2 * k + sum(_profile_launches(x.numel(), A.TORCH_CODE[x.dtype])
+                                                    for x in xs)),
         "clocks": clk.summary(),
     }
 

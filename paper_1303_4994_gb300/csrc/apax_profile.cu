@@ -733,19 +733,6 @@ __global__ void __launch_bounds__(128) k_profile_fix(ProfArgs a)
     }
 }
 
-// One level of the fan-in-16 tree: out[m][q] = in[16m][q] + ... (in order).
-__global__ void k_tree(const double *in, double *out, uint64_t cnt, int Qn)
-{
-    const uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint64_t nodes = (cnt + 15) / 16;
-    if (m >= nodes * (uint64_t)Qn) return;
-    const uint64_t node = m / Qn, q = m % Qn;
-    const uint64_t a0 = node * 16, a1 = min(a0 + 16, cnt);
-    double s = in[a0 * Qn + q];
-    for (uint64_t i = a0 + 1; i < a1; ++i) s = __dadd_rn(s, in[i * Qn + q]);
-    out[node * Qn + q] = s;
-}
-
 __device__ double corr_r(double sxx, double sxy, double syy)
 {
     // sums beyond binary64 give a quiet NaN with a fixed bit pattern
@@ -796,26 +783,13 @@ __device__ void finalize_points(const ProfArgs &a, const double *tot, uint64_t c
     }
 }
 
-__global__ void k_finalize(ProfArgs a, const double *tot, uint64_t container_fixed)
-{
-    __shared__ double s_r[32];
-    finalize_points(a, tot, container_fixed, s_r);
-}
-
-// The whole fan-in-16 tree over the array's run sums and the finalisation,
-// by one CTA (after every run of the array is written).  Same additions in
-// the same order as the k_tree levels.
-__device__ void tree_finalize_cta(const ProfArgs &a, double *s_r)
+// The levels of the fan-in-16 tree above `in` (cnt values per quantity;
+// the next level goes to scratch buffer pi) and the finalisation, by one
+// CTA.  Level by level, each value the in-order sum of 16 (or fewer) below it.
+__device__ void tree_rest_cta(const ProfArgs &a, const double *in, uint64_t cnt, int pi, double *s_r)
 {
     const int Qn = 2 + 4 * a.ncand;
-    uint64_t cnt = a.nruns;
-    const double *in = a.run_sums;
     double *bufs[2] = {a.scratch, a.scratch + ((a.nruns + 15) / 16 + 1) * (uint64_t)Qn};
-    int pi = 0;
-    if (cnt == 0) {
-        for (int q = threadIdx.x; q < Qn; q += blockDim.x) __stcg(a.scratch + q, 0.0);
-        in = a.scratch;
-    }
     while (cnt > 1) {
         const uint64_t nodes = (cnt + 15) / 16;
         for (uint64_t m = threadIdx.x; m < nodes * (uint64_t)Qn; m += blockDim.x) {
@@ -837,6 +811,55 @@ __device__ void tree_finalize_cta(const ProfArgs &a, double *s_r)
     __syncthreads();
     const uint64_t fixed = 40 + ((4 * a.nb + 7) / 8) * 8;
     finalize_points(a, s_tot, fixed, s_r);
+}
+
+// The whole tree over the array's run sums and the finalisation, by one CTA
+// (after every run of the array is written).
+__device__ void tree_finalize_cta(const ProfArgs &a, double *s_r)
+{
+    const int Qn = 2 + 4 * a.ncand;
+    const double *in = a.run_sums;
+    if (a.nruns == 0) {
+        for (int q = threadIdx.x; q < Qn; q += blockDim.x) __stcg(a.scratch + q, 0.0);
+        __syncthreads();
+        in = a.scratch;
+    }
+    tree_rest_cta(a, in, a.nruns, 0, s_r);
+}
+
+// Small arrays (at most 256 runs): the tree and the finalisation in one CTA.
+__global__ void __launch_bounds__(256) k_tree_one(ProfArgs a)
+{
+    __shared__ double s_r[32];
+    tree_finalize_cta(a, s_r);
+}
+
+// Larger arrays: the tree's first level by every CTA (grid-stride over
+// nodes x quantities), the levels above it and the finalisation by the CTA
+// that finishes last (a.done counts finished CTAs; cleared by the call).
+// One launch where the level-by-level kernels took one per level plus one.
+__global__ void __launch_bounds__(256) k_tree_fused(ProfArgs a)
+{
+    __shared__ double s_r[32];
+    __shared__ bool s_last;
+    const int Qn = 2 + 4 * a.ncand;
+    const uint64_t cnt = a.nruns, nodes = (cnt + 15) / 16;
+    for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < nodes * (uint64_t)Qn;
+         m += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t node = m / Qn, q = m % Qn;
+        const uint64_t a0 = node * 16, a1 = min(a0 + 16, cnt);
+        double sum = __ldcg(a.run_sums + a0 * Qn + q);
+        for (uint64_t i = a0 + 1; i < a1; ++i) sum = __dadd_rn(sum, __ldcg(a.run_sums + i * Qn + q));
+        __stcg(a.scratch + node * Qn + q, sum);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(a.done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        tree_rest_cta(a, a.scratch, nodes, 1, s_r);
+    }
 }
 
 template <int DT>
@@ -1007,28 +1030,15 @@ cudaError_t launch_profile(const ProfArgs &a, cudaStream_t s)
 
 cudaError_t launch_profile_tree(const ProfArgs &a, cudaStream_t s)
 {
-    cudaError_t e;
-    // upper levels of the fan-in-16 tree
-    const int Qn = 2 + 4 * a.ncand;
-    uint64_t cnt = a.nruns;
-    const double *in = a.run_sums;
-    double *bufs[2] = {a.scratch, a.scratch + ((a.nruns + 15) / 16 + 1) * (uint64_t)Qn};
-    int pi = 0;
-    if (cnt == 0) {
-        e = cudaMemsetAsync(a.scratch, 0, sizeof(double) * Qn, s);
-        if (e != cudaSuccess) return e;
-        in = a.scratch;
+    // a.done: the call's cleared completion counter (apax_profile's workspace)
+    if (a.nruns <= 256) {
+        k_tree_one<<<1, 256, 0, s>>>(a);
+    } else {
+        const uint64_t work = (a.nruns + 15) / 16 * (uint64_t)(2 + 4 * a.ncand);
+        const uint64_t most = 4ull * (uint64_t)sm_count();
+        const uint64_t ctas = (work + 255) / 256 < most ? (work + 255) / 256 : most;
+        k_tree_fused<<<(unsigned)ctas, 256, 0, s>>>(a);
     }
-    while (cnt > 1) {
-        const uint64_t nodes = (cnt + 15) / 16;
-        const uint64_t threads = nodes * Qn;
-        k_tree<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(in, bufs[pi], cnt, Qn);
-        in = bufs[pi];
-        pi ^= 1;
-        cnt = nodes;
-    }
-    const uint64_t fixed = 40 + ((4 * a.nb + 7) / 8) * 8;
-    k_finalize<<<1, 32, 0, s>>>(a, in, fixed);
     return cudaGetLastError();
 }
 
