@@ -9,7 +9,8 @@
 //      Sec. 6, shared with the next block's thread), candidate 0 and the
 //      block sums of x;
 //   3. the other candidates, five per walk, on the stream the predecessor
-//      block chose.
+//      block chose (codes with k >= 24 need no walk: they quantise every
+//      sample of a float32 block to 0).
 // Nothing is exchanged between threads inside a walk (no team scans): the
 // greedy JEE token count runs sequentially, three candidates at a time in
 // 10-bit lanes of one register.
@@ -450,6 +451,7 @@ __global__ void __launch_bounds__(kP, 8) k_profile_f32_t1(ProfArgs a)
 
     // candidate 0 and the block sums
     const i128 Sxx = ((i128)C0 << 48) + ((i128)A0 << 25) + (i128)B0;
+    double sxx_blk = 0.0;  // the block's sum x^2, rounded once
     {
         double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         if (go) {
@@ -473,6 +475,7 @@ __global__ void __launch_bounds__(kP, 8) k_profile_f32_t1(ProfArgs a)
             v[3] = round_scaled(((i128)C0 << 24) + (i128)A0, 2 * (Eb - 23) - 24);
             v[4] = __dmul_rn(__ll2double_rn(C0), pow2d(2 * (Eb - 23)));
         }
+        sxx_blk = v[1];
 #pragma unroll
         for (int i = 0; i < 6; ++i) s_v[i][t] = v[i];
         const uint32_t bs = s == 0 ? bits3[0] : (s == 1 ? bits3[1] : bits3[2]);
@@ -485,16 +488,37 @@ __global__ void __launch_bounds__(kP, 8) k_profile_f32_t1(ProfArgs a)
     run_partials(a, s_v, 6, 0, jfirst);
     __syncthreads();
 
-    // ---- 3. the other candidates, kC per walk
-    for (int c0 = 1; c0 < a.ncand; c0 += kC) {
-        const int m = min(kC, a.ncand - c0);
+    // ---- 3. the other candidates, kC per walk.  An attenuation 2^-k with
+    // k >= 24 quantises every sample to 0 (|X| < 2^23, so |X 2^-k| < 1/2):
+    // such a candidate's sums of y, xy and y^2 are 0, its sum d^2 is the
+    // block's sum x^2, and its packet has every exponent 0 (the first one
+    // absolute, the rest zero diffs, two to a joint token), so it takes no
+    // walk.  The codes increase, so these candidates end the list.
+    int ct = a.ncand;
+    while (ct > 1 && (a.codes[ct - 1] >> 7) >= 24) --ct;
+    const uint32_t zero_bytes = 4u * ((48u + 4u * (uint32_t)(2 + B.Gt / 2) + 31u) >> 5);
+    for (int c0 = 1; c0 < a.ncand;) {
+        const bool trivial = c0 >= ct;
+        const int m = min(kC, (trivial ? a.ncand : ct) - c0);
         uint32_t bytes[kC];
 #pragma unroll
         for (int i = 0; i < kC; ++i) bytes[i] = 0u;
-        if (go)
+        if (go && !trivial) {
             walk_dispatch<kC>(m, B, Eb, s, s_codes + c0, b0, b24, Sxx, tiny, s_txx[t], s_v, t, bytes);
-        else
+        } else if (go) {
+#pragma unroll
+            for (int i = 0; i < kC; ++i) {
+                if (i < m) {
+                    s_v[4 * i + 0][t] = 0.0;
+                    s_v[4 * i + 1][t] = 0.0;
+                    s_v[4 * i + 2][t] = 0.0;
+                    s_v[4 * i + 3][t] = sxx_blk;
+                    bytes[i] = zero_bytes;
+                }
+            }
+        } else {
             for (int i = 0; i < 4 * m; ++i) s_v[i][t] = 0.0;
+        }
 #pragma unroll
         for (int c = 0; c < kC; ++c) {
             if (c >= m) break;
@@ -506,6 +530,7 @@ __global__ void __launch_bounds__(kP, 8) k_profile_f32_t1(ProfArgs a)
         __syncthreads();
         run_partials(a, s_v, 4 * m, 2 + 4 * c0, jfirst);
         __syncthreads();
+        c0 += m;
     }
 }
 
