@@ -447,12 +447,37 @@ __device__ __forceinline__ void profile_run(const ProfArgs &a, uint64_t run, uin
 
     // ---- candidates
     uint32_t fbmask = tiny ? 1u : 0u;
+    // Codes that quantise every sample to 0 (code 4095, or k >= Q + 1 for
+    // floats, |X| < 2^Q, and k >= W for integers, |x| <= 2^(W-1)): sums of
+    // y, xy and y^2 are 0, sum d^2 is the block's sum x^2, and the packet has
+    // every exponent 0 (the first absolute, then zero diffs two to a joint
+    // token).  They need no pass over the block when the block's own sums
+    // are exact (no fallback); the codes increase, so they end the list.
+    constexpr int kZeroK = T::F ? T::Q + 1 : T::W;
+    int ct = nc;
+    while (ct > 0 && (a.codes[ct - 1] == 4095 || (int)(a.codes[ct - 1] >> 7) >= kZeroK)) --ct;
+    uint32_t zeromask = 0;  // candidates taken as all-zero
+    const uint32_t zero_bits =
+        (uint32_t)H + 4u * (uint32_t)(2 + ((b.G >> b.gsh) > 0 ? (b.G >> b.gsh) / 2 : 0));
 #pragma unroll 1
     for (int ci = 0; ci < nc; ++ci) {
+        if (ci >= ct && __all_sync(kFull, !(fbmask & 1u) || !b.active)) {
+            // warp-uniform: every team of the warp skips this candidate
+            zeromask |= 1u << ci;
+            if (t == 0) {
+                cs[ci].sq = 0;
+                cs[ci].A = 0;
+                cs[ci].B = 0;
+                cs[ci].D = 0;
+                cs[ci].bits = zero_bits;
+                cs[ci].fast = 1;
+            }
+            continue;
+        }
         if constexpr (DT == 4) {
             // three float32 candidates in one walk (FMA form, all k >= 1, no
             // fallback); warp-uniform, so the team collectives stay in step
-            if (ci + 3 <= nc) {
+            if (ci + 3 <= ct) {
                 bool ok = !tiny && b.Eb >= -80;
 #pragma unroll
                 for (int jj = 0; jj < 3; ++jj) {
@@ -630,7 +655,9 @@ __device__ __forceinline__ void profile_run(const ProfArgs &a, uint64_t run, uin
         const CandStage<DT> &st = cs[ci];
         const int k = (int)(a.codes[ci] >> 7);
         double v[4] = {0.0, 0.0, 0.0, 0.0};
-        if (live) {
+        if (live && ((zeromask >> ci) & 1u)) {
+            v[3] = blk_x[1];  // d = x: the block's sum x^2, rounded once
+        } else if (live) {
             if constexpr (DT == 4) {
                 if (st.fast) {
                     const int s2 = b.Eb - 23 + k;
