@@ -772,7 +772,10 @@ __global__ void __launch_bounds__(128) k_decode(DecArgs a)
     __syncthreads();
     const DecHdr hd = s_h;
     constexpr bool LARGE = EB > 1024;
-    if (my_class<EB>(a, hd)) {
+    // the other size class's container: this launch has nothing to do (its
+    // completion counter is only read by the class that owns the container)
+    if (!my_class<EB>(a, hd)) return;
+    {
         if (hd.err) {
             if (threadIdx.x == 0) set_status(a.status, hd.err);
         } else if (!LARGE && hd.N <= kT1MaxBlock &&

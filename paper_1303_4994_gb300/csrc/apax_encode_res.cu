@@ -73,11 +73,12 @@ __device__ __forceinline__ Carry res_carry_at(const Quant<DT> &Q, const Regs<DT>
     return res_carry(q2, q3, qs, t);
 }
 
-// Stream s at code Q over my groups: the greedy token counter, and (EB) each
-// BFPE group's exponent in ebuf[g >> gsh].
-template <int DT, bool EB>
-__device__ __forceinline__ TokCount res_pass(const TBlock<DT> &b, const Regs<DT> &xr,
-                                             const Quant<DT> &Q, const Carry &c, int s, uint8_t *ebuf)
+// Stream s at code Q over my groups: the greedy token counter and each BFPE
+// group's exponent in ebuf[g >> gsh].  The stream values replace the samples
+// in xr (the mantissa writer reads them there).
+template <int DT>
+__device__ __forceinline__ TokCount res_pass(const TBlock<DT> &b, Regs<DT> &xr, const Quant<DT> &Q,
+                                             const Carry &c, int s, uint8_t *ebuf)
 {
     TokCount tc;
     tc.init();
@@ -90,10 +91,12 @@ __device__ __forceinline__ TokCount res_pass(const TBlock<DT> &b, const Regs<DT>
             if (i < ng) {
                 int32_t u[4];
                 acc |= group1<DT>(qf, xr[i], st, u);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) xr[i][k] = (typename LaneT<DT>::t)u[k];
                 const int g = b.g0 + i;
                 if (!b.gsh || (g & 1)) {
                     const int e = exp_from_or(acc);
-                    if (EB) ebuf[g >> b.gsh] = (uint8_t)e;
+                    ebuf[g >> b.gsh] = (uint8_t)e;
                     tc.push(e, true);
                     acc = 0;
                 }
@@ -244,7 +247,7 @@ __device__ __forceinline__ void encode_tile_res(const EncArgs &a, uint64_t tile,
     // ---- 4. exponents and tokens at the code, then the packet
     const Quant<DT> Q(code, b.Eb);
     const Carry cq = res_carry_at<DT>(Q, xr, l2, l3, t);
-    const TokCount tc = res_pass<DT, true>(b, xr, Q, cq, s, ebuf);
+    const TokCount tc = res_pass<DT>(b, xr, Q, cq, s, ebuf);  // xr now holds the stream values
     int nib_total, sume_total, nib_mine;
     bool s_in;
     team_tokens<TS>(tc, b.g0 == 0, nib_total, sume_total, &s_in, &nib_mine);
@@ -285,17 +288,14 @@ __device__ __forceinline__ void encode_tile_res(const EncArgs &a, uint64_t tile,
         NibWriter mw;
         mw.start(pkt, (uint32_t)H + 4u * (uint32_t)nib_total + wm * (uint32_t)sume_before);
         const int ng = b.g1 - b.g0;
-        with_quant<DT>(Q, [&](const auto &qf) {
-            Stream1 sm(s, cq);
 #pragma unroll
-            for (int i = 0; i < kGM; ++i) {
-                if (i < ng) {
-                    int32_t u[4];
-                    group1<DT>(qf, xr[i], sm, u);
-                    write_group_fields(mw, ebuf[(b.g0 + i) >> b.gsh], u);
-                }
+        for (int i = 0; i < kGM; ++i) {
+            if (i < ng) {
+                const int32_t u[4] = {(int32_t)xr[i][0], (int32_t)xr[i][1], (int32_t)xr[i][2],
+                                      (int32_t)xr[i][3]};
+                write_group_fields(mw, ebuf[(b.g0 + i) >> b.gsh], u);
             }
-        });
+        }
         mw.flush();
     }
     __syncthreads();
