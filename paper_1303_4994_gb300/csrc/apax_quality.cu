@@ -32,8 +32,10 @@ namespace {
 
 constexpr int kSel = 256;        // radix-select buckets (a byte)
 constexpr int kSpecL = 4096;     // segment length
-constexpr int kSpecCtas = 256;   // CTAs adding periodograms (fixed: reproducible sums)
-constexpr int kSpecThreads = 256;
+// CTAs adding periodograms: fixed, so the sums are reproducible; one per SM
+// of a GB300 (about 146 KB of shared memory each, so one CTA a SM), one wave
+constexpr int kSpecCtas = 152;
+constexpr int kSpecThreads = 512;
 
 
 template <int DT>
@@ -117,22 +119,23 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b)
 }
 
 // In-place radix-2 decimation-in-time FFT of z[0..L) (bit-reversed copy in,
-// natural order out), twiddles tw[j] = exp(-2 pi i j / L), j < L/2.
+// natural order out), twiddles tw[j] = exp(-2 pi i j / L), j < L/2.  L is a
+// power of two: butterfly b of the stage with groups of 2 half sits at
+// (b >> stage) 2 half + (b & (half - 1)), its twiddle at pos L / (2 half).
 __device__ void fft_smem(double2 *z, const double2 *tw, int L, int logL)
 {
     for (int half = 1, stage = 0; half < L; half <<= 1, ++stage) {
-        const int tstride = L / (2 * half);
+        const int tshift = logL - 1 - stage;  // log2(L / (2 half))
         for (int b = threadIdx.x; b < L / 2; b += blockDim.x) {
-            const int grp = b / half, pos = b % half;
-            const int i0 = grp * 2 * half + pos, i1 = i0 + half;
-            const double2 w = tw[pos * tstride];
+            const int grp = b >> stage, pos = b & (half - 1);
+            const int i0 = (grp << (stage + 1)) + pos, i1 = i0 + half;
+            const double2 w = tw[pos << tshift];
             const double2 u = z[i0], v = cmul(z[i1], w);
             z[i0] = make_double2(__dadd_rn(u.x, v.x), __dadd_rn(u.y, v.y));
             z[i1] = make_double2(__dsub_rn(u.x, v.x), __dsub_rn(u.y, v.y));
         }
         __syncthreads();
     }
-    (void)logL;
 }
 
 __device__ __forceinline__ int bitrev(int i, int logL) { return (int)(__brev((unsigned)i) >> (32 - logL)); }
