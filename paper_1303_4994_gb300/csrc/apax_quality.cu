@@ -120,19 +120,50 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b)
 
 // In-place radix-2 decimation-in-time FFT of z[0..L) (bit-reversed copy in,
 // natural order out), twiddles tw[j] = exp(-2 pi i j / L), j < L/2.  L is a
-// power of two: butterfly b of the stage with groups of 2 half sits at
-// (b >> stage) 2 half + (b & (half - 1)), its twiddle at pos L / (2 half).
+// power of two.  Stage s combines pairs half = 2^s apart, butterfly b at
+// (b >> s) 2 half + (b & (half - 1)) with twiddle tw[pos L / (2 half)].
+// Two stages run per pass over shared memory: a thread takes the four points
+// of two stages' butterflies and does both in registers, the same operations
+// on the same values as the stage-by-stage order, with half the barriers.
+__device__ __forceinline__ void bfly(double2 &u, double2 &v, double2 w)
+{
+    const double2 t = cmul(v, w);
+    const double2 a = u;
+    u = make_double2(__dadd_rn(a.x, t.x), __dadd_rn(a.y, t.y));
+    v = make_double2(__dsub_rn(a.x, t.x), __dsub_rn(a.y, t.y));
+}
+
 __device__ void fft_smem(double2 *z, const double2 *tw, int L, int logL)
 {
-    for (int half = 1, stage = 0; half < L; half <<= 1, ++stage) {
-        const int tshift = logL - 1 - stage;  // log2(L / (2 half))
+    int stage = 0;
+    for (; stage + 1 < logL; stage += 2) {
+        const int half = 1 << stage;
+        const int sh1 = logL - 1 - stage, sh2 = logL - 2 - stage;
+        for (int b = threadIdx.x; b < L / 4; b += blockDim.x) {
+            const int grp = b >> stage, pos = b & (half - 1);
+            const int i0 = (grp << (stage + 2)) + pos;
+            double2 p0 = z[i0], p1 = z[i0 + half], p2 = z[i0 + 2 * half], p3 = z[i0 + 3 * half];
+            const double2 w1 = tw[pos << sh1];
+            bfly(p0, p1, w1);  // stage s: (i0, i0 + half), (i0 + 2 half, i0 + 3 half)
+            bfly(p2, p3, w1);
+            bfly(p0, p2, tw[pos << sh2]);           // stage s + 1: pairs 2 half apart
+            bfly(p1, p3, tw[(pos + half) << sh2]);
+            z[i0] = p0;
+            z[i0 + half] = p1;
+            z[i0 + 2 * half] = p2;
+            z[i0 + 3 * half] = p3;
+        }
+        __syncthreads();
+    }
+    if (stage < logL) {  // an odd number of stages: the last one alone
+        const int half = 1 << stage;
         for (int b = threadIdx.x; b < L / 2; b += blockDim.x) {
             const int grp = b >> stage, pos = b & (half - 1);
-            const int i0 = (grp << (stage + 1)) + pos, i1 = i0 + half;
-            const double2 w = tw[pos << tshift];
-            const double2 u = z[i0], v = cmul(z[i1], w);
-            z[i0] = make_double2(__dadd_rn(u.x, v.x), __dadd_rn(u.y, v.y));
-            z[i1] = make_double2(__dsub_rn(u.x, v.x), __dsub_rn(u.y, v.y));
+            const int i0 = (grp << (stage + 1)) + pos;
+            double2 p0 = z[i0], p1 = z[i0 + half];
+            bfly(p0, p1, tw[pos]);
+            z[i0] = p0;
+            z[i0 + half] = p1;
         }
         __syncthreads();
     }
