@@ -112,10 +112,13 @@ __global__ void k_s2r_pick(SelState *st, unsigned long long *hist, apax_quality 
 }
 
 // ---------------------------------------------------------------- spectra
+// a b with one product of each part fused: re = fma(a.x, b.x, -(a.y b.y)),
+// im = fma(a.x, b.y, a.y b.x) (four binary64 operations instead of six;
+// the spectra are compared within a tolerance, not bit for bit)
 __device__ __forceinline__ double2 cmul(double2 a, double2 b)
 {
-    return make_double2(__dsub_rn(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y)),
-                        __dadd_rn(__dmul_rn(a.x, b.y), __dmul_rn(a.y, b.x)));
+    return make_double2(__fma_rn(a.x, b.x, -__dmul_rn(a.y, b.y)),
+                        __fma_rn(a.x, b.y, __dmul_rn(a.y, b.x)));
 }
 
 // In-place radix-2 decimation-in-time FFT of z[0..L) (bit-reversed copy in,
