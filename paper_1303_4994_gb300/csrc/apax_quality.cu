@@ -15,7 +15,10 @@
 // Spectra.  Welch-Bartlett averages over full segments of L = 4096 samples
 // (the largest power of two <= n below that): mean removed, periodic Hann
 // window, |FFT|^2 / sum(w^2) in binary64, bins 1..L/2.  x and y share one
-// complex FFT (x + i y, split by symmetry), d has its own.  A fixed number of
+// complex FFT (x + i y, split by symmetry); d, real, packs its even and odd
+// samples into one complex FFT of L/2 points (the real-input FFT by
+// splitting: D[k] = E[k] + W^k O[k], E and O the half-length spectra of the
+// even and odd samples, read off by the same symmetry).  A fixed number of
 // CTAs (kSpecCtas, independent of the device) each add the periodograms of
 // their segments in order; the bins' sums over the CTAs follow in CTA order,
 // so the result does not depend on scheduling.  Peak = max, floor = lower
@@ -122,8 +125,9 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b)
 }
 
 // In-place radix-2 decimation-in-time FFT of z[0..L) (bit-reversed copy in,
-// natural order out), twiddles tw[j] = exp(-2 pi i j / L), j < L/2.  L is a
-// power of two.  Stage s combines pairs half = 2^s apart, butterfly b at
+// natural order out), twiddles exp(-2 pi i j / L) = tw[j << tws], j < L/2
+// (tws = 1: a half-length transform reading the full table).  L is a power
+// of two.  Stage s combines pairs half = 2^s apart, butterfly b at
 // (b >> s) 2 half + (b & (half - 1)) with twiddle tw[pos L / (2 half)].
 // Two stages run per pass over shared memory: a thread takes the four points
 // of two stages' butterflies and does both in registers, the same operations
@@ -136,12 +140,12 @@ __device__ __forceinline__ void bfly(double2 &u, double2 &v, double2 w)
     v = make_double2(__dsub_rn(a.x, t.x), __dsub_rn(a.y, t.y));
 }
 
-__device__ void fft_smem(double2 *z, const double2 *tw, int L, int logL)
+__device__ void fft_smem(double2 *z, const double2 *tw, int L, int logL, int tws)
 {
     int stage = 0;
     for (; stage + 1 < logL; stage += 2) {
         const int half = 1 << stage;
-        const int sh1 = logL - 1 - stage, sh2 = logL - 2 - stage;
+        const int sh1 = logL - 1 - stage + tws, sh2 = logL - 2 - stage + tws;
         for (int b = threadIdx.x; b < L / 4; b += blockDim.x) {
             const int grp = b >> stage, pos = b & (half - 1);
             const int i0 = (grp << (stage + 2)) + pos;
@@ -164,12 +168,19 @@ __device__ void fft_smem(double2 *z, const double2 *tw, int L, int logL)
             const int grp = b >> stage, pos = b & (half - 1);
             const int i0 = (grp << (stage + 1)) + pos;
             double2 p0 = z[i0], p1 = z[i0 + half];
-            bfly(p0, p1, tw[pos]);
+            bfly(p0, p1, tw[pos << tws]);
             z[i0] = p0;
             z[i0 + half] = p1;
         }
         __syncthreads();
     }
+}
+
+// The periodic Hann window (1 - cos(2 pi m / L)) / 2 from the twiddles.
+__device__ __forceinline__ double hann(const double2 *tw, int m, int H)
+{
+    const double c_ = m < H ? tw[m].x : -tw[m - H].x;
+    return __dmul_rn(0.5, __dsub_rn(1.0, c_));
 }
 
 __device__ __forceinline__ int bitrev(int i, int logL) { return (int)(__brev((unsigned)i) >> (32 - logL)); }
@@ -228,34 +239,54 @@ __global__ void __launch_bounds__(kSpecThreads) k_spectra(const void *x, const v
             sd = __dadd_rn(sd, __dsub_rn(xv, yv));
         }
         const double mx = cta_sum(red, sx) / L, my = cta_sum(red, sy) / L, md = cta_sum(red, sd) / L;
-        for (int pass = 0; pass < 2; ++pass) {
-            // pass 0: z = w (x - mx) + i w (y - my); pass 1: z = w (d - md)
-            for (int m = threadIdx.x; m < L; m += blockDim.x) {
-                // periodic Hann window (1 - cos(2 pi m / L)) / 2 from the twiddles
-                const double c_ = m < H ? tw[m].x : -tw[m - H].x;
-                const double w = __dmul_rn(0.5, __dsub_rn(1.0, c_));
-                const double xv = as_double<DT>(x, base + m), yv = as_double<DT>(y, base + m);
-                double2 v;
-                if (pass == 0) v = make_double2(__dmul_rn(w, __dsub_rn(xv, mx)), __dmul_rn(w, __dsub_rn(yv, my)));
-                else v = make_double2(__dmul_rn(w, __dsub_rn(__dsub_rn(xv, yv), md)), 0.0);
-                z[bitrev(m, logL_)] = v;
-            }
-            __syncthreads();
-            fft_smem(z, tw, L, logL_);
-            for (int k = 1 + threadIdx.x; k <= H; k += blockDim.x) {
-                const double2 a = z[k], b = z[(L - k) & (L - 1)];
-                if (pass == 0) {
-                    // X = (Z[k] + conj Z[L-k]) / 2, Y = (Z[k] - conj Z[L-k]) / (2i)
-                    const double xr = 0.5 * __dadd_rn(a.x, b.x), xi = 0.5 * __dsub_rn(a.y, b.y);
-                    const double yr = 0.5 * __dadd_rn(a.y, b.y), yi = -0.5 * __dsub_rn(a.x, b.x);
-                    acc[k - 1] = __dadd_rn(acc[k - 1], __dadd_rn(__dmul_rn(xr, xr), __dmul_rn(xi, xi)) / wnorm);
-                    acc[H + k - 1] = __dadd_rn(acc[H + k - 1], __dadd_rn(__dmul_rn(yr, yr), __dmul_rn(yi, yi)) / wnorm);
-                } else {
-                    acc[2 * H + k - 1] = __dadd_rn(acc[2 * H + k - 1], __dadd_rn(__dmul_rn(a.x, a.x), __dmul_rn(a.y, a.y)) / wnorm);
-                }
-            }
-            __syncthreads();
+        // x and y: z = w (x - mx) + i w (y - my), one L-point FFT
+        for (int m = threadIdx.x; m < L; m += blockDim.x) {
+            const double xv = as_double<DT>(x, base + m), yv = as_double<DT>(y, base + m);
+            const double w = hann(tw, m, H);
+            z[bitrev(m, logL_)] = make_double2(__dmul_rn(w, __dsub_rn(xv, mx)), __dmul_rn(w, __dsub_rn(yv, my)));
         }
+        __syncthreads();
+        fft_smem(z, tw, L, logL_, 0);
+        for (int k = 1 + threadIdx.x; k <= H; k += blockDim.x) {
+            const double2 a = z[k], b = z[(L - k) & (L - 1)];
+            // X = (Z[k] + conj Z[L-k]) / 2, Y = (Z[k] - conj Z[L-k]) / (2i)
+            const double xr = 0.5 * __dadd_rn(a.x, b.x), xi = 0.5 * __dsub_rn(a.y, b.y);
+            const double yr = 0.5 * __dadd_rn(a.y, b.y), yi = -0.5 * __dsub_rn(a.x, b.x);
+            acc[k - 1] = __dadd_rn(acc[k - 1], __dadd_rn(__dmul_rn(xr, xr), __dmul_rn(xi, xi)) / wnorm);
+            acc[H + k - 1] = __dadd_rn(acc[H + k - 1], __dadd_rn(__dmul_rn(yr, yr), __dmul_rn(yi, yi)) / wnorm);
+        }
+        __syncthreads();
+        // d: v = w (d - md); z[m] = v[2m] + i v[2m+1], one L/2-point FFT
+        for (int m = threadIdx.x; m < H; m += blockDim.x) {
+            double v[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int mm = 2 * m + e;
+                const double xv = as_double<DT>(x, base + mm), yv = as_double<DT>(y, base + mm);
+                v[e] = __dmul_rn(hann(tw, mm, H), __dsub_rn(__dsub_rn(xv, yv), md));
+            }
+            z[bitrev(m, logL_ - 1)] = make_double2(v[0], v[1]);
+        }
+        __syncthreads();
+        fft_smem(z, tw, H, logL_ - 1, 1);
+        for (int k = 1 + threadIdx.x; k <= H; k += blockDim.x) {
+            double dr, di;
+            if (k < H) {
+                // E = (Z[k] + conj Z[H-k]) / 2, O = (Z[k] - conj Z[H-k]) / (2i), D = E + W^k O
+                const double2 a = z[k], b = z[H - k];
+                const double er = 0.5 * __dadd_rn(a.x, b.x), ei = 0.5 * __dsub_rn(a.y, b.y);
+                const double orr = 0.5 * __dadd_rn(a.y, b.y), oi = -0.5 * __dsub_rn(a.x, b.x);
+                const double2 t = cmul(make_double2(orr, oi), tw[k]);
+                dr = __dadd_rn(er, t.x);
+                di = __dadd_rn(ei, t.y);
+            } else {
+                // D[L/2] = E[0] - O[0], both real
+                dr = __dsub_rn(z[0].x, z[0].y);
+                di = 0.0;
+            }
+            acc[2 * H + k - 1] = __dadd_rn(acc[2 * H + k - 1], __dadd_rn(__dmul_rn(dr, dr), __dmul_rn(di, di)) / wnorm);
+        }
+        __syncthreads();
     }
     for (int j = threadIdx.x; j < 3 * H; j += blockDim.x) part[(uint64_t)blockIdx.x * 3 * H + j] = acc[j];
 }
