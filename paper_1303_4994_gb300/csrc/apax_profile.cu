@@ -754,9 +754,17 @@ template <int DT>
 __global__ void __launch_bounds__(128) k_profile_fix(ProfArgs a)
 {
     extern __shared__ __align__(16) uint8_t psm[];
-    for (uint64_t r = a.run0 + blockIdx.x; r < a.run1; r += gridDim.x) {
-        if (a.run_flags[r]) profile_run<DT, false>(a, r, psm);
-        __syncthreads();
+    // This CTA's runs are r0 + i gridDim.x.  The flags of blockDim.x of them
+    // are read together (most sweeps flag none), and only a chunk with a
+    // flagged run is walked run by run.
+    const uint64_t stride = gridDim.x;
+    for (uint64_t r0 = a.run0 + blockIdx.x; r0 < a.run1; r0 += stride * blockDim.x) {
+        const uint64_t r = r0 + stride * threadIdx.x;
+        if (!__syncthreads_or(r < a.run1 && a.run_flags[r])) continue;
+        for (uint64_t rr = r0; rr < a.run1 && rr < r0 + stride * blockDim.x; rr += stride) {
+            if (a.run_flags[rr]) profile_run<DT, false>(a, rr, psm);
+            __syncthreads();
+        }
     }
 }
 
