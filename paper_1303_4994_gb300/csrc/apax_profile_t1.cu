@@ -21,11 +21,16 @@
 //   sum y    = 2^(Eb-23+k) S,                    S = sum q
 //   sum y^2  = 2^(2(Eb-23+k)) C,                 C = sum q^2
 //   sum xy   = 2^(2(Eb-23)+k-24) (2^24 A + B),   A = sum q0 q, B = sum R0 q
+//   A        = 2^k C + E,                        E = sum (q0 - 2^k q) q
 //   sum d^2  = 2^(2Eb-94) (Sxx - 2^(k+49) A - 2^(k+25) B + 2^(2k+48) C)
 //   sum x^2  = 2^(2Eb-94) Sxx,  Sxx = 2^48 sum q0^2 + 2^25 sum q0 R0 + sum R0^2
+// E's terms are small: |q0 - 2^k q| <= 2^(k-1) (both round X, at steps 1
+// and 2^k) and |q| <= 2^(23-k), so |(q0 - 2^k q) q| <= 2^22 and E over a
+// block of at most 256 samples is a 32-bit sum; only B and C need 64 bits.
 // q0 and R0 are recomputed per walk from x; every candidate sample then
 // costs one FMA (quantiser), two integer multiply-adds (derivative), the
-// width term and four integer multiply-adds (sums).  Each block sum is
+// width term, a shift and three integer multiply-adds (sums), two of them
+// 64-bit.  Each block sum is
 // rounded once to binary64 and the run's partial adds its 16 block values in
 // block order, as the team kernel does, so the results are identical.
 //
@@ -129,8 +134,9 @@ __device__ __forceinline__ void walk(const Blk &B, int Eb, int s, const uint32_t
 {
     float bk[M];
     uint32_t qp[M], qpp[M];
-    int S[M], se[M];
-    int64_t Cs[M], As[M], Bs[M];
+    int S[M], se[M], Es[M];
+    uint32_t kk[M];
+    int64_t Cs[M], Bs[M];
     Jee3 jj[(M + 2) / 3];
     const uint32_t ca = s == 0 ? 0u : (s == 1 ? 1u : 2u), cb = s == 2 ? 1u : 0u;
     const float x0 = __uint_as_float(__ldg(reinterpret_cast<const uint32_t *>(B.xp)));
@@ -143,7 +149,9 @@ __device__ __forceinline__ void walk(const Blk &B, int Eb, int s, const uint32_t
         qpp[c] = 2u * qf;
         S[c] = 0;
         se[c] = 0;
-        Cs[c] = As[c] = Bs[c] = 0;
+        kk[c] = (uint32_t)k;
+        Es[c] = 0;
+        Cs[c] = Bs[c] = 0;
     }
     uint4 vn = B.group(0);  // the next group's samples are loaded one iteration ahead
 #pragma unroll 1
@@ -171,7 +179,9 @@ __device__ __forceinline__ void walk(const Blk &B, int Eb, int s, const uint32_t
                 qp[c] = (uint32_t)q;
                 S[c] += q;
                 Cs[c] += (int64_t)q * q;
-                As[c] += (int64_t)q0[i] * q;  // (a tiny sample has q = 0: its R0 adds nothing)
+                // sum q0 q = 2^k sum q^2 + sum e q, e = q0 - 2^k q, |e q| <= 2^22
+                // (a tiny sample has q0 = q = 0 and its R0 adds nothing)
+                Es[c] += (q0[i] - (int)((uint32_t)q << kk[c])) * q;
                 Bs[c] += (int64_t)R0[i] * q;
             }
             ev[c] = ewidth(o);
@@ -202,17 +212,18 @@ __device__ __forceinline__ void walk(const Blk &B, int Eb, int s, const uint32_t
             const int q = __float_as_int(__fmaf_rn(pxf, bk[c], kMagic)) - kMagicBits;
             S[c] -= pad * q;
             Cs[c] -= (int64_t)pad * ((int64_t)q * q);
-            As[c] -= (int64_t)pad * ((int64_t)pq0 * q);
+            Es[c] -= pad * ((pq0 - (int)((uint32_t)q << kk[c])) * q);
             Bs[c] -= (int64_t)pad * ((int64_t)pR0 * q);
         }
         const int nib = jj[c / 3].lane(c % 3);
         const uint32_t bits = 48u + 4u * (uint32_t)nib + 4u * (uint32_t)se[c];
         bytes[c] = 4u * ((bits + 31u) >> 5);
+        const int64_t Ac = (Cs[c] << k) + (int64_t)Es[c];  // sum q0 q
         const int sy = Eb - 23 + k;
         sv[4 * c + 0][t] = __dmul_rn((double)S[c], pow2d(sy));
-        sv[4 * c + 1][t] = round_scaled(((i128)As[c] << 24) + (i128)Bs[c], 2 * (Eb - 23) + k - 24);
+        sv[4 * c + 1][t] = round_scaled(((i128)Ac << 24) + (i128)Bs[c], 2 * (Eb - 23) + k - 24);
         sv[4 * c + 2][t] = __dmul_rn(__ll2double_rn(Cs[c]), pow2d(2 * sy));
-        const i128 D = Sxx - ((i128)As[c] << (k + 49)) - ((i128)Bs[c] << (k + 25)) +
+        const i128 D = Sxx - ((i128)Ac << (k + 49)) - ((i128)Bs[c] << (k + 25)) +
                        ((i128)Cs[c] << (2 * k + 48));
         if (tiny) {
             // D >= 0: sum (X - y)^2 of the other samples, in units of 2^-48
