@@ -57,7 +57,7 @@ METRIC = "encode/decode GB/s (uncompressed) and % of GB300 HBM roofline at ratio
 WORKLOAD = "float32 4096x4096 k^-3 random field (seed 1): profile 16 codes -> fixed-quality encode at r>=0.9999 -> decode"
 TARGET = 0.9999
 N_BLOCK = 256
-E2E_CHUNKS = 8  # pieces of the host-to-device copy that the sweep overlaps
+E2E_CHUNKS = 16  # pieces of the host-to-device copy that the sweep overlaps
 
 
 CPU_ROWS = 1024  # rows of the field in the oracle's timed sample (16 MiB)
@@ -395,7 +395,7 @@ def run_ours(args, rank, world, local_rank):
                 "h2d_bytes_per_step": xb,
                 "d2h_bytes_per_step": er.bytes + pts.numel() + y.numel() * y.element_size(),
                 "ms_per_step": round(e2e, 4),
-                "path": "apax_profile_from_host (H2D in 8 pieces under the sweep) -> "
+                "path": "apax_profile_from_host (H2D in 16 pieces under the sweep) -> "
                         "apax_encode_recommended -> apax_copy_container to pinned host "
                         "memory (size read on the device) beside apax_decode -> D2H of points "
                         "and decoded array; median of K steps"},

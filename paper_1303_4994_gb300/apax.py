@@ -652,7 +652,7 @@ def profile_into(x: torch.Tensor, block_size: int, candidates, target: float,
 def profile_from_host_into(x_host: torch.Tensor, x_dev: torch.Tensor, block_size: int,
                            candidates, target: float, workspace: torch.Tensor,
                            points: torch.Tensor, summary: torch.Tensor, stream=None,
-                           copy_stream=None, chunks: int = 8):
+                           copy_stream=None, chunks: int = 16):
     """apax_profile_from_host: x_host (pinned CPU tensor) is copied into x_dev
     in `chunks` pieces on copy_stream (default: a side stream of this module)
     while the sweep runs on stream."""
