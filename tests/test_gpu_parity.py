@@ -374,6 +374,33 @@ def test_profile_from_host_matches_device(dt):
     assert A.read_summary(summ3).status == 0 and A.read_summary(summ3).n == 0
 
 
+def test_profile_from_host_two_in_flight():
+    # two host-input sweeps enqueued back to back on their own streams (they
+    # share the library's sweep streams) each give the device sweep's points;
+    # a field large enough for the one-block-per-thread device sweep
+    x = synth.grf2d(2048, 2048, seed=21).reshape(-1)  # 16,384 blocks
+    xt = torch.from_numpy(x).cuda()
+    N, nc = 256, 16
+    ws, pts, summ = A.profile_buffers(xt, N, nc)
+    A.profile_into(xt, N, list(A.DEFAULT_CANDIDATES), 0.9999, ws, pts, summ)
+    torch.cuda.synchronize()
+    want_p, want_s = pts.cpu().clone(), summ.cpu().clone()
+    xh = torch.from_numpy(x).pin_memory()
+    slots = []
+    for _ in range(2):
+        xd = torch.zeros_like(xt)
+        b = A.profile_buffers(xt, N, nc)
+        slots.append((xd, b, torch.cuda.Stream(), torch.cuda.Stream()))
+    for rep in range(3):
+        for xd, (w2, p2, s2), st, cs in slots:
+            A.profile_from_host_into(xh, xd, N, list(A.DEFAULT_CANDIDATES), 0.9999, w2, p2, s2,
+                                     stream=st, copy_stream=cs, chunks=16)
+        torch.cuda.synchronize()
+        for xd, (w2, p2, s2), st, cs in slots:
+            assert torch.equal(p2.cpu(), want_p) and torch.equal(s2.cpu(), want_s), rep
+            assert torch.equal(xd, xt)
+
+
 @pytest.mark.parametrize("dt", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("N", [128, 200, 512])
 def test_large_arrays_block_sizes_decode(dt, N):
