@@ -374,6 +374,37 @@ def test_profile_from_host_matches_device(dt):
     assert A.read_summary(summ3).status == 0 and A.read_summary(summ3).n == 0
 
 
+def test_profile_from_host_graph_capture():
+    # the host-input sweep (copies, events, the library's sweep streams)
+    # captured into a CUDA graph and replayed gives the device sweep's points
+    x = synth.grf2d(1024, 1024, seed=22).reshape(-1)
+    xt = torch.from_numpy(x).cuda()
+    N, nc = 256, 16
+    ws, pts, summ = A.profile_buffers(xt, N, nc)
+    A.profile_into(xt, N, list(A.DEFAULT_CANDIDATES), 0.9999, ws, pts, summ)
+    torch.cuda.synchronize()
+    want_p = pts.cpu().clone()
+    xh = torch.from_numpy(x).pin_memory()
+    xd = torch.zeros_like(xt)
+    w2, p2, s2 = A.profile_buffers(xt, N, nc)
+    st, cs = torch.cuda.Stream(), torch.cuda.Stream()
+    A.profile_from_host_into(xh, xd, N, list(A.DEFAULT_CANDIDATES), 0.9999, w2, p2, s2,
+                             stream=st, copy_stream=cs, chunks=8)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st, capture_error_mode="relaxed"):
+        A.profile_from_host_into(xh, xd, N, list(A.DEFAULT_CANDIDATES), 0.9999, w2, p2, s2,
+                                 stream=st, copy_stream=cs, chunks=8)
+    for _ in range(2):
+        xd.zero_()
+        p2.zero_()
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(p2.cpu(), want_p)
+        assert torch.equal(xd, xt)
+
+
 def test_profile_from_host_two_in_flight():
     # two host-input sweeps enqueued back to back on their own streams (they
     # share the library's sweep streams) each give the device sweep's points;
