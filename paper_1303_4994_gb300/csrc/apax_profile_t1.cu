@@ -317,18 +317,33 @@ __global__ void __launch_bounds__(kP, 8) k_profile_f32_t1(ProfArgs a)
     uint32_t mx = 0;
     const bool whole = (j + 1) * (uint64_t)N <= a.n && j < jend;
     if (__all_sync(kFull, whole) && (G & 31) == 0) {
+        // four blocks per step, their loads issued together (the reads come
+        // from DRAM; one block at a time left a load's latency per block)
         const uint4 *wb = reinterpret_cast<const uint4 *>(a.x) + (j - (uint64_t)lane) * (uint64_t)G;
 #pragma unroll 1
-        for (int b = 0; b < 32; ++b) {
-            uint32_t lm = 0;
-#pragma unroll 2
-            for (int i = 0; i < (G >> 5); ++i) {
-                const uint4 v = __ldg(wb + (uint64_t)b * G + 32 * i + lane);
-                lm = max(lm, max(max(v.x & 0x7fffffffu, v.y & 0x7fffffffu),
-                                 max(v.z & 0x7fffffffu, v.w & 0x7fffffffu)));
+        for (int b = 0; b < 32; b += 4) {
+            uint32_t lm[4] = {0u, 0u, 0u, 0u};
+#pragma unroll 1
+            for (int i = 0; i < (G >> 5); i += 2) {
+                uint4 v[4][2];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int h = 0; h < 2; ++h)
+                        v[u][h] = i + h < (G >> 5) ? __ldg(wb + (uint64_t)(b + u) * G + 32 * (i + h) + lane)
+                                                   : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int h = 0; h < 2; ++h)
+                        lm[u] = max(lm[u], max(max(v[u][h].x & 0x7fffffffu, v[u][h].y & 0x7fffffffu),
+                                               max(v[u][h].z & 0x7fffffffu, v[u][h].w & 0x7fffffffu)));
             }
-            const uint32_t r = __reduce_max_sync(kFull, lm);
-            if (lane == b) mx = r;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t r = __reduce_max_sync(kFull, lm[u]);
+                if (lane == b + u) mx = r;
+            }
         }
     } else {
 #pragma unroll 4
@@ -357,9 +372,14 @@ __global__ void __launch_bounds__(kP, 8) k_profile_f32_t1(ProfArgs a)
         uint32_t qp1 = 0, qp2 = (uint32_t)qf, qpp2 = 2u * (uint32_t)qf;
         Jee3 j3;
         int se0 = 0, se1 = 0, se2 = 0;
+        // the next two groups are loaded ahead (the block's first per-thread
+        // read after the coalesced maximum: mostly from L2)
+        uint4 vn1 = B.group(0), vn2 = B.Gt > 1 ? B.group(1) : vn1;
 #pragma unroll 1
         for (int g = 0; g < B.Gt; ++g) {
-            const uint4 v = B.group(g);
+            const uint4 v = vn1;
+            vn1 = vn2;
+            if (g + 2 < B.Gt) vn2 = B.group(g + 2);
             const uint32_t xv[4] = {v.x, v.y, v.z, v.w};
             uint32_t o0 = 0, o1 = 0, o2 = 0;
 #pragma unroll
