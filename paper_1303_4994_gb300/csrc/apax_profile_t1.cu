@@ -10,7 +10,9 @@
 //      block sums of x;
 //   3. the other candidates, five per walk, on the stream the predecessor
 //      block chose (codes with k >= 24 need no walk: they quantise every
-//      sample of a float32 block to 0).
+//      sample of a float32 block to 0; a lone last candidate, when the
+//      walked codes number 1 more than a multiple of five, rides along in
+//      walk 2 on all three streams instead of taking a walk of its own).
 // Nothing is exchanged between threads inside a walk (no team scans): the
 // greedy JEE token count runs sequentially, three candidates at a time in
 // 10-bit lanes of one register.
@@ -123,6 +125,30 @@ struct Blk {
     }
 };
 
+// A candidate's four block sums from its exact integer sums (attenuation
+// 2^-k, k >= 1): v = {sum y, sum xy, sum y^2, sum d^2}, each rounded once.
+__device__ __forceinline__ void cand_sums(int k, int Eb, int S, int64_t Cs, int Es, int64_t Bs,
+                                          const i128 &Sxx, bool tiny, const uint64_t *txx,
+                                          double *v, int stride)
+{
+    const int64_t Ac = (Cs << k) + (int64_t)Es;  // sum q0 q
+    const int sy = Eb - 23 + k;
+    v[0] = __dmul_rn((double)S, pow2d(sy));
+    v[stride] = round_scaled(((i128)Ac << 24) + (i128)Bs, 2 * (Eb - 23) + k - 24);
+    v[2 * stride] = __dmul_rn(__ll2double_rn(Cs), pow2d(2 * sy));
+    const i128 D = Sxx - ((i128)Ac << (k + 49)) - ((i128)Bs << (k + 25)) + ((i128)Cs << (2 * k + 48));
+    if (tiny) {
+        // D >= 0: sum (X - y)^2 of the other samples, in units of 2^-48
+        W256 w;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) w.l[i] = txx[i];
+        w256_add(w, (u128)D, 145, false);
+        v[3 * stride] = round_w256(w, 2 * Eb - 239);
+    } else {
+        v[3 * stride] = round_scaled(D, 2 * Eb - 94);
+    }
+}
+
 // One walk over the block for M candidates (codes[0 .. M)), all k >= 1.
 // Writes the candidates' four block sums to sv[4c + q][t] and their packet
 // bytes; txx (tiny blocks) is the side sum of the tiny samples' x^2 on the
@@ -218,23 +244,7 @@ __device__ __forceinline__ void walk(const Blk &B, int Eb, int s, const uint32_t
         const int nib = jj[c / 3].lane(c % 3);
         const uint32_t bits = 48u + 4u * (uint32_t)nib + 4u * (uint32_t)se[c];
         bytes[c] = 4u * ((bits + 31u) >> 5);
-        const int64_t Ac = (Cs[c] << k) + (int64_t)Es[c];  // sum q0 q
-        const int sy = Eb - 23 + k;
-        sv[4 * c + 0][t] = __dmul_rn((double)S[c], pow2d(sy));
-        sv[4 * c + 1][t] = round_scaled(((i128)Ac << 24) + (i128)Bs[c], 2 * (Eb - 23) + k - 24);
-        sv[4 * c + 2][t] = __dmul_rn(__ll2double_rn(Cs[c]), pow2d(2 * sy));
-        const i128 D = Sxx - ((i128)Ac << (k + 49)) - ((i128)Bs[c] << (k + 25)) +
-                       ((i128)Cs[c] << (2 * k + 48));
-        if (tiny) {
-            // D >= 0: sum (X - y)^2 of the other samples, in units of 2^-48
-            W256 w;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) w.l[i] = txx[i];
-            w256_add(w, (u128)D, 145, false);
-            sv[4 * c + 3][t] = round_w256(w, 2 * Eb - 239);
-        } else {
-            sv[4 * c + 3][t] = round_scaled(D, 2 * Eb - 94);
-        }
+        cand_sums(k, Eb, S[c], Cs[c], Es[c], Bs[c], Sxx, tiny, txx, &sv[4 * c][t], kP);
     }
 }
 
@@ -269,11 +279,153 @@ __device__ __forceinline__ void run_partials(const ProfArgs &a, double (*sv)[kP]
     }
 }
 
+// The code-0 pass (one block, one thread): the three streams' packet bits
+// at code 0 (the best-stream decision), candidate 0's sums and the block's
+// sums of x; with LONE, also one more candidate (code 128 kL) on all three
+// streams.  R0 is zeroed for tiny samples (their x enters through the side
+// sums); their q0 and q are 0 at every code.
+struct Code0 {
+    uint32_t bits3[3] = {0u, 0u, 0u};
+    int64_t Sq0 = 0, SR0 = 0, C0 = 0, A0 = 0, B0 = 0;
+    bool tiny = false;
+    int kL = 1;
+    uint32_t bitsL[3] = {0u, 0u, 0u};
+    int SL = 0, EL = 0;
+    int64_t CL = 0, BL = 0;
+};
+
+template <bool LONE>
+__device__ __forceinline__ void code0_pass(const Blk &B, float b0, float b24, uint32_t tthr, int eb,
+                                           Code0 &z)
+{
+    const float x0 = __uint_as_float(__ldg(reinterpret_cast<const uint32_t *>(B.xp)));
+    const int qf = __float2int_rn(__fmul_rn(x0, b0));
+    uint32_t qp1 = 0, qp2 = (uint32_t)qf, qpp2 = 2u * (uint32_t)qf;
+    Jee3 j3;
+    int se0 = 0, se1 = 0, se2 = 0;
+    // the lone candidate: 2^(23 - Eb - kL) (clamped: blocks out of range
+    // are swept again by the team kernel)
+    const float bkL = __int_as_float(min(max(150 - eb - z.kL, 1), 254) << 23);
+    const uint32_t kL = (uint32_t)z.kL;
+    const int qfL = LONE ? __float_as_int(__fmaf_rn(x0, bkL, kMagic)) - kMagicBits : 0;
+    uint32_t lp1 = 0, lp2 = (uint32_t)qfL, lpp2 = 2u * (uint32_t)qfL;
+    Jee3 jL;
+    int sL0 = 0, sL1 = 0, sL2 = 0;
+    int SL = 0, EL = 0;
+    int64_t CL = 0, BL = 0;
+    int64_t Sq0 = 0, SR0 = 0, C0 = 0, A0 = 0, B0 = 0;
+    bool tiny = false;
+    // the next two groups are loaded ahead (the block's first per-thread
+    // read after the coalesced maximum: mostly from L2)
+    uint4 vn1 = B.group(0), vn2 = B.Gt > 1 ? B.group(1) : vn1;
+#pragma unroll 1
+    for (int g = 0; g < B.Gt; ++g) {
+        const uint4 v = vn1;
+        vn1 = vn2;
+        if (g + 2 < B.Gt) vn2 = B.group(g + 2);
+        const uint32_t xv[4] = {v.x, v.y, v.z, v.w};
+        uint32_t o0 = 0, o1 = 0, o2 = 0, l0 = 0, l1 = 0, l2 = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float xf = __uint_as_float(xv[i]);
+            const bool ti = ((xv[i] & 0x7fffffffu) - 1u) < tthr - 1u;
+            tiny |= ti;
+            const int q = __float2int_rn(__fmul_rn(xf, b0));
+            int R = __float2int_rn(__fmaf_rn(__int2float_rn(q), -16777216.0f, __fmul_rn(xf, b24)));
+            R = ti ? 0 : R;  // a tiny sample's x enters through the side sums
+            const uint32_t uq = (uint32_t)q;
+            o0 |= btw(uq);
+            o1 |= btw(uq - qp1);
+            o2 |= btw(uq - 2u * qp2 + qpp2);
+            qp1 = uq;
+            qpp2 = qp2;
+            qp2 = uq;
+            Sq0 += q;
+            SR0 += R;
+            C0 += (int64_t)q * q;
+            A0 += (int64_t)q * R;
+            B0 += (int64_t)R * R;
+            if constexpr (LONE) {
+                const int ql = __float_as_int(__fmaf_rn(xf, bkL, kMagic)) - kMagicBits;
+                const uint32_t ul = (uint32_t)ql;
+                l0 |= btw(ul);
+                l1 |= btw(ul - lp1);
+                l2 |= btw(ul - 2u * lp2 + lpp2);
+                lp1 = ul;
+                lpp2 = lp2;
+                lp2 = ul;
+                SL += ql;
+                CL += (int64_t)ql * ql;
+                EL += (q - (int)(ul << kL)) * ql;  // |(q0 - 2^k q) q| <= 2^22
+                BL += (int64_t)R * ql;             // (R = 0 where q = 0)
+            }
+        }
+        const uint32_t e0 = ewidth(o0), e1 = ewidth(o1), e2 = ewidth(o2);
+        se0 += (int)e0;
+        se1 += (int)e1;
+        se2 += (int)e2;
+        const uint32_t E = e0 | (e1 << 10) | (e2 << 20);
+        if (g == 0) j3.first(E);
+        else j3.push(E);
+        if constexpr (LONE) {
+            const uint32_t f0 = ewidth(l0), f1 = ewidth(l1), f2 = ewidth(l2);
+            sL0 += (int)f0;
+            sL1 += (int)f1;
+            sL2 += (int)f2;
+            const uint32_t F = f0 | (f1 << 10) | (f2 << 20);
+            if (g == 0) jL.first(F);
+            else jL.push(F);
+        }
+    }
+    z.bits3[0] = 48u + 4u * (uint32_t)(j3.lane(0) + se0);
+    z.bits3[1] = 48u + 4u * (uint32_t)(j3.lane(1) + se1);
+    z.bits3[2] = 48u + 4u * (uint32_t)(j3.lane(2) + se2);
+    // the padding copies of a ragged block's last sample
+    const int pad = 4 - B.nl;
+    if (pad) {
+        const uint32_t xl = B.last();
+        const float xf = __uint_as_float(xl);
+        const bool ti = ((xl & 0x7fffffffu) - 1u) < tthr - 1u;
+        const int q = __float2int_rn(__fmul_rn(xf, b0));
+        int R = __float2int_rn(__fmaf_rn(__int2float_rn(q), -16777216.0f, __fmul_rn(xf, b24)));
+        R = ti ? 0 : R;
+        Sq0 -= pad * q;
+        SR0 -= pad * R;
+        C0 -= (int64_t)pad * ((int64_t)q * q);
+        A0 -= (int64_t)pad * ((int64_t)q * R);
+        B0 -= (int64_t)pad * ((int64_t)R * R);
+        if constexpr (LONE) {
+            const int ql = __float_as_int(__fmaf_rn(xf, bkL, kMagic)) - kMagicBits;
+            SL -= pad * ql;
+            CL -= (int64_t)pad * ((int64_t)ql * ql);
+            EL -= pad * ((q - (int)((uint32_t)ql << kL)) * ql);
+            BL -= (int64_t)pad * ((int64_t)R * ql);
+        }
+    }
+    z.Sq0 = Sq0;
+    z.SR0 = SR0;
+    z.C0 = C0;
+    z.A0 = A0;
+    z.B0 = B0;
+    z.tiny = tiny;
+    if constexpr (LONE) {
+        z.bitsL[0] = 48u + 4u * (uint32_t)(jL.lane(0) + sL0);
+        z.bitsL[1] = 48u + 4u * (uint32_t)(jL.lane(1) + sL1);
+        z.bitsL[2] = 48u + 4u * (uint32_t)(jL.lane(2) + sL2);
+        z.SL = SL;
+        z.EL = EL;
+        z.CL = CL;
+        z.BL = BL;
+    }
+}
+
 // 8 CTAs of 64 threads per SM (at most 128 registers): 1216 resident warps
 // take the 2048 warps of a 64 MiB float32 array in one wave with room to spare.
 __global__ void __launch_bounds__(kP, 8) k_profile_f32_t1(ProfArgs a)
 {
     __shared__ double s_v[4 * kC][kP];
+    __shared__ double s_lone[4][kP];
+    __shared__ uint32_t s_lone_b[kP];
     __shared__ uint64_t s_txx[kP][4];
     __shared__ int s_best[kP / 32];
     __shared__ int s_halo;
@@ -364,72 +516,22 @@ __global__ void __launch_bounds__(kP, 8) k_profile_f32_t1(ProfArgs a)
     const float b0 = __int_as_float((150 - eb) << 23);                   // 2^(23 - Eb)
     const float b24 = __int_as_float(min(max(174 - eb, 1), 254) << 23);  // 2^(47 - Eb)
     const uint32_t tthr = (uint32_t)max(eb + 103, 1) << 23;              // |x| < 2^(Eb-24)
-    uint32_t bits3[3] = {0u, 0u, 0u};
-    int64_t Sq0 = 0, SR0 = 0, C0 = 0, A0 = 0, B0 = 0;
-    bool tiny = false;
+    // the walks' lone last candidate: when the walked codes number 1 more
+    // than a multiple of kC, the last one is taken in the code-0 pass (on
+    // all three streams: the block's stream is known only after it) instead
+    // of in a walk of its own
+    int ct = a.ncand;
+    while (ct > 1 && (a.codes[ct - 1] >> 7) >= 24) --ct;
+    const bool lone = ct > 1 && (ct - 1) % kC == 1;
+    Code0 z;
+    z.kL = lone ? (int)(a.codes[ct - 1] >> 7) : 1;
     if (dv) {
-        const int qf = __float2int_rn(__fmul_rn(__uint_as_float(__ldg(reinterpret_cast<const uint32_t *>(B.xp))), b0));
-        uint32_t qp1 = 0, qp2 = (uint32_t)qf, qpp2 = 2u * (uint32_t)qf;
-        Jee3 j3;
-        int se0 = 0, se1 = 0, se2 = 0;
-        // the next two groups are loaded ahead (the block's first per-thread
-        // read after the coalesced maximum: mostly from L2)
-        uint4 vn1 = B.group(0), vn2 = B.Gt > 1 ? B.group(1) : vn1;
-#pragma unroll 1
-        for (int g = 0; g < B.Gt; ++g) {
-            const uint4 v = vn1;
-            vn1 = vn2;
-            if (g + 2 < B.Gt) vn2 = B.group(g + 2);
-            const uint32_t xv[4] = {v.x, v.y, v.z, v.w};
-            uint32_t o0 = 0, o1 = 0, o2 = 0;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const float xf = __uint_as_float(xv[i]);
-                const bool ti = ((xv[i] & 0x7fffffffu) - 1u) < tthr - 1u;
-                tiny |= ti;
-                const int q = __float2int_rn(__fmul_rn(xf, b0));
-                int R = __float2int_rn(__fmaf_rn(__int2float_rn(q), -16777216.0f, __fmul_rn(xf, b24)));
-                R = ti ? 0 : R;  // a tiny sample's x enters through the side sums
-                const uint32_t uq = (uint32_t)q;
-                o0 |= btw(uq);
-                o1 |= btw(uq - qp1);
-                o2 |= btw(uq - 2u * qp2 + qpp2);
-                qp1 = uq;
-                qpp2 = qp2;
-                qp2 = uq;
-                Sq0 += q;
-                SR0 += R;
-                C0 += (int64_t)q * q;
-                A0 += (int64_t)q * R;
-                B0 += (int64_t)R * R;
-            }
-            const uint32_t e0 = ewidth(o0), e1 = ewidth(o1), e2 = ewidth(o2);
-            se0 += (int)e0;
-            se1 += (int)e1;
-            se2 += (int)e2;
-            const uint32_t E = e0 | (e1 << 10) | (e2 << 20);
-            if (g == 0) j3.first(E);
-            else j3.push(E);
-        }
-        bits3[0] = 48u + 4u * (uint32_t)(j3.lane(0) + se0);
-        bits3[1] = 48u + 4u * (uint32_t)(j3.lane(1) + se1);
-        bits3[2] = 48u + 4u * (uint32_t)(j3.lane(2) + se2);
-        // the padding copies of a ragged block's last sample
-        const int pad = 4 - B.nl;
-        if (pad) {
-            const uint32_t xl = B.last();
-            const float xf = __uint_as_float(xl);
-            const bool ti = ((xl & 0x7fffffffu) - 1u) < tthr - 1u;
-            const int q = __float2int_rn(__fmul_rn(xf, b0));
-            int R = __float2int_rn(__fmaf_rn(__int2float_rn(q), -16777216.0f, __fmul_rn(xf, b24)));
-            R = ti ? 0 : R;
-            Sq0 -= pad * q;
-            SR0 -= pad * R;
-            C0 -= (int64_t)pad * ((int64_t)q * q);
-            A0 -= (int64_t)pad * ((int64_t)q * R);
-            B0 -= (int64_t)pad * ((int64_t)R * R);
-        }
+        if (lone) code0_pass<true>(B, b0, b24, tthr, eb, z);
+        else code0_pass<false>(B, b0, b24, tthr, eb, z);
     }
+    const uint32_t bits3[3] = {z.bits3[0], z.bits3[1], z.bits3[2]};
+    const int64_t Sq0 = z.Sq0, SR0 = z.SR0, C0 = z.C0, A0 = z.A0, B0 = z.B0;
+    const bool tiny = z.tiny;
     // tiny samples (0 < |x| < 2^(Eb-24)): exact side sums of x on the grid
     // 2^(Eb-237) and of x^2 on 2^(2Eb-239); deeper ones go to the team path
     W256 tx, txx;
@@ -515,6 +617,19 @@ __global__ void __launch_bounds__(kP, 8) k_profile_f32_t1(ProfArgs a)
         for (int m = 8; m >= 1; m >>= 1) by += __shfl_xor_sync(kFull, by, m);
         if ((lane & 15) == 0 && go) atomicAdd(a.bytes + 0, (unsigned long long)by);
     }
+    // the lone candidate's sums and bytes, parked until its turn in step 3
+    if (lone) {
+        double lv[4] = {0.0, 0.0, 0.0, 0.0};
+        uint32_t lb = 0u;
+        if (go) {
+            cand_sums(z.kL, Eb, z.SL, z.CL, z.EL, z.BL, Sxx, tiny, txx.l, lv, 1);
+            const uint32_t bl = s == 0 ? z.bitsL[0] : (s == 1 ? z.bitsL[1] : z.bitsL[2]);
+            lb = 4u * ((bl + 31u) >> 5);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) s_lone[i][t] = lv[i];
+        s_lone_b[t] = lb;
+    }
     __syncthreads();
     run_partials(a, s_v, 6, 0, jfirst);
     __syncthreads();
@@ -525,16 +640,20 @@ __global__ void __launch_bounds__(kP, 8) k_profile_f32_t1(ProfArgs a)
     // block's sum x^2, and its packet has every exponent 0 (the first one
     // absolute, the rest zero diffs, two to a joint token), so it takes no
     // walk.  The codes increase, so these candidates end the list.
-    int ct = a.ncand;
-    while (ct > 1 && (a.codes[ct - 1] >> 7) >= 24) --ct;
+    // (ct: the first such code, from step 2)
     const uint32_t zero_bytes = 4u * ((48u + 4u * (uint32_t)(2 + B.Gt / 2) + 31u) >> 5);
     for (int c0 = 1; c0 < a.ncand;) {
         const bool trivial = c0 >= ct;
-        const int m = min(kC, (trivial ? a.ncand : ct) - c0);
+        const bool folded = lone && c0 == ct - 1;  // the lone candidate, from step 2
+        const int m = folded ? 1 : min(kC, (trivial ? a.ncand : ct) - c0);
         uint32_t bytes[kC];
 #pragma unroll
         for (int i = 0; i < kC; ++i) bytes[i] = 0u;
-        if (go && !trivial) {
+        if (go && folded) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) s_v[i][t] = s_lone[i][t];
+            bytes[0] = s_lone_b[t];
+        } else if (go && !trivial) {
             walk_dispatch<kC>(m, B, Eb, s, s_codes + c0, b0, b24, Sxx, tiny, s_txx[t], s_v, t, bytes);
         } else if (go) {
 #pragma unroll

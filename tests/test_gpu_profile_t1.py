@@ -57,11 +57,12 @@ def test_t1_default_ladder_block_sizes(N):
 
 
 @pytest.mark.parametrize("cands", [
-    [0],                                   # code 0 only
-    [0, 128],                              # one candidate walk of 1
-    [0] + [128 * k for k in range(1, 9)],  # one full walk of 8
-    [0] + [128 * k for k in range(1, 10)],  # 8 + 1
-    [0] + [128 * k for k in range(1, 32)],  # 8 + 8 + 8 + 7 (32 codes, k up to 31)
+    [0],                                    # code 0 only
+    [0, 128],                               # one walked code, taken in the code-0 pass
+    [0] + [128 * k for k in range(1, 6)],   # one full walk of 5
+    [0] + [128 * k for k in range(1, 7)],   # 5, and the sixth in the code-0 pass
+    [0] + [128 * k for k in range(1, 10)],  # 5 + 4
+    [0] + [128 * k for k in range(1, 32)],  # 5 + 5 + 5 + 5 + 3, and k = 24..31 all zero
     [0, 384, 1024, 2048, 3968],
 ])
 def test_t1_candidate_counts(cands):
