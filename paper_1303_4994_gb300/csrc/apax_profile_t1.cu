@@ -12,7 +12,7 @@
 //      block chose (codes with k >= 24 need no walk: they quantise every
 //      sample of a float32 block to 0; a lone last candidate, when the
 //      walked codes number 1 more than a multiple of five, rides along in
-//      walk 2 on all three streams instead of taking a walk of its own).
+//      step 2 on all three streams instead of taking a walk of its own).
 // Nothing is exchanged between threads inside a walk (no team scans): the
 // greedy JEE token count runs sequentially, three candidates at a time in
 // 10-bit lanes of one register.
