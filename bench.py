@@ -69,7 +69,8 @@ def _profile_figure(kernel, key=None):
     """Figures of the committed ncu summary of this workload
     (profiles/traffic_f32_4096x4096.txt): 'kernel bytes' lines give the DRAM
     read + write bytes of one launch, 'issue_active kernel frac' lines the
-    issue-active fraction per scheduler."""
+    issue-active fraction per scheduler, 'fma_heavy kernel frac' lines the
+    FMA-heavy pipe's busy fraction of peak."""
     path = os.path.join(ROOT, "profiles", "traffic_f32_4096x4096.txt")
     try:
         with open(path) as f:
@@ -90,6 +91,10 @@ def _traffic(kernel):
 
 def _issue_active(kernel):
     return _profile_figure(kernel, "issue_active")
+
+
+def _fma_heavy(kernel):
+    return _profile_figure(kernel, "fma_heavy")
 
 
 def _events(fn, reps, stream, flush=None):
@@ -405,14 +410,16 @@ def run_ours(args, rank, world, local_rank):
     # the roofline of the kernel with the largest share of the step: its
     # algorithmic bytes (read s per element, plus the container for encode
     # and decode) over its CUDA-event time, against the measured copy peak;
-    # ncu's issue-active fraction of the same kernel sits beside it
+    # ncu's issue-active fraction of the same kernel and the busy fraction of
+    # its busiest pipe (the FMA-heavy pipe of the integer multiply-adds) sit
+    # beside it: the sweep is bound by integer issue, not by HBM
     dom = max(kern, key=lambda k: kern[k]["ms"])
     alg = {"profile": prof_bytes, "encode": enc_bytes, "decode": dec_bytes}[dom]
     roof = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["gbs"], "peak": peak,
             "unit": "GB/s", "frac": kern[dom]["gbs"] / peak, "traffic": _traffic(dom),
             "algorithmic_bytes": alg, "ms": kern[dom]["ms"],
             "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
-            "ncu_issue_active": _issue_active(dom)}
+            "ncu_issue_active": _issue_active(dom), "ncu_fma_heavy_pipe": _fma_heavy(dom)}
     line = {
         "metric": METRIC,
         "value": round(aggregate_gbs(xb, world, ms), 3),
