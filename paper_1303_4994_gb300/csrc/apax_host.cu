@@ -740,12 +740,14 @@ int apax_profile_from_host(const void *x_host, void *x_dev, int dtype, uint64_t 
         ProfArgs b = a;
         b.run0 = r0;
         b.run1 = r1;
-        // every piece takes the team sweep (no run flags): its runs end soon
-        // after the piece lands, where the one-block-per-thread sweep's long
-        // per-thread walks outlast the copy and hold the SMs' registers
-        // while later pieces wait (64 MiB float32 in 8 pieces: 0.574 ms with
-        // it on every piece, 0.57 on the first quarter only, 0.512 never)
-        b.run_flags = nullptr;
+        // with more than one piece every piece takes the team sweep (no run
+        // flags): its runs end soon after the piece lands, where the
+        // one-block-per-thread sweep's long per-thread walks outlast the copy
+        // and hold the SMs' registers while later pieces wait (64 MiB float32
+        // in 8 pieces: 0.574 ms with it on every piece, 0.57 on the first
+        // quarter only, 0.512 never).  One piece overlaps nothing inside the
+        // call, so it keeps the faster sweep.
+        if (chunks > 1) b.run_flags = nullptr;
         if ((e = launch_profile_runs(b, sk)) != cudaSuccess) return fail(e);
     }
     // join: the copy stream (every piece is on the device) and the sweeps

@@ -422,10 +422,12 @@ def test_profile_from_host_two_in_flight():
         xd = torch.zeros_like(xt)
         b = A.profile_buffers(xt, N, nc)
         slots.append((xd, b, torch.cuda.Stream(), torch.cuda.Stream()))
-    for rep in range(3):
+    # one piece (the whole array, then the one-block-per-thread sweep) and 16
+    # pieces (the team sweep on each as it lands)
+    for rep, chunks in enumerate((16, 1, 16)):
         for xd, (w2, p2, s2), st, cs in slots:
             A.profile_from_host_into(xh, xd, N, list(A.DEFAULT_CANDIDATES), 0.9999, w2, p2, s2,
-                                     stream=st, copy_stream=cs, chunks=16)
+                                     stream=st, copy_stream=cs, chunks=chunks)
         torch.cuda.synchronize()
         for xd, (w2, p2, s2), st, cs in slots:
             assert torch.equal(p2.cpu(), want_p) and torch.equal(s2.cpu(), want_s), rep
