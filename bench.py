@@ -434,6 +434,7 @@ def run_ours(args, rank, world, local_rank):
         "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "elements": n, "block_size": N_BLOCK, "candidates": nc,
+                   "input_sha256": synth.sha256(x_host),
                    "target_corr": TARGET, "l2": "flushed (512 MB write) before every timed step",
                    "launch": "each step replays one CUDA graph of the three calls",
                    "timing": "median of K step times; per-call medians of max(K, 20) runs",
@@ -570,7 +571,12 @@ def run_batched(args, compact=False):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     specs = synth.batch_specs(args.arrays)
-    masters = {k: torch.from_numpy(v).to(dev) for k, v in synth.batch_masters().items()}
+    masters_h = synth.batch_masters()
+    # every array is a wrapped slice of a master: the masters and the job
+    # table (dtype, length, rate, offset) fix all 56.6 GB of input
+    in_sha = synth.sha256(*[masters_h[k] for k in sorted(masters_h)], repr(specs))
+    masters = {k: torch.from_numpy(v).to(dev) for k, v in masters_h.items()}
+    del masters_h
     xs = [_wrapped(masters[dt], off, n) for dt, n, _, off in specs]
     ps = [A.params(N_BLOCK, A.FIXED_RATE, rate, 0) for _, _, rate, _ in specs]
     total = sum(x.numel() * x.element_size() for x in xs)
@@ -653,6 +659,7 @@ def run_batched(args, compact=False):
                             "int16/int32/float32/float64, fixed rate 2:1/3:1/4:1/6:1, N=256 "
                             "(seed 3); each batched operation one graph-captured persistent launch; "
                             "medians of 3 runs of each",
+                "input_sha256": in_sha,
                 "gbs_uncompressed": {n: round(v, 2) for n, v in gbs.items()},
                 "batched_vs_plain": {op: round(ms["plain_" + op] / ms["batched_" + op], 3)
                                      for op in ("encode", "decode", "profile")},
@@ -666,7 +673,7 @@ def run_batched(args, compact=False):
         "data": "synthetic",
         "config": {"workload": f"batched: {k} arrays 4 KB..64 MB, int16/int32/float32/float64, "
                                "fixed rate 2:1/3:1/4:1/6:1, N=256 (seed 3)",
-                   "bytes": total, "l2": "inputs larger than L2"},
+                   "bytes": total, "l2": "inputs larger than L2", "input_sha256": in_sha},
         "ratio": round(total / comp, 4),
         "gbs": {n: round(v, 2) for n, v in gbs.items()},
         "ms": {n: round(v, 3) for n, v in ms.items()},
@@ -699,7 +706,9 @@ def run_sensor(args, compact=False):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     p = A.params(N_BLOCK, A.FIXED_RATE, (4, 1), 0)
-    t = torch.from_numpy(synth.sensor_trace()).to(dev)
+    th = synth.sensor_trace()
+    in_sha = synth.sha256(th)  # the replica is 8,192 copies of it
+    t = torch.from_numpy(th).to(dev)
 
     def bufs(x):
         cap = A.encoded_size(A.I16, x.numel(), p)
@@ -744,6 +753,7 @@ def run_sensor(args, compact=False):
     if compact:
         return {"workload": "int16 sensor trace (262,144 samples, seed 0), fixed rate 4:1, N=256; "
                             "4 GiB = 8,192 copies for throughput",
+                "input_sha256": in_sha,
                 "single_call_us": {"encode": round(lat_enc * 1e3, 2), "decode": round(lat_dec * 1e3, 2)},
                 "replica_gbs_uncompressed": {"encode_bisect": round(xb / ms_enc / 1e6, 2),
                                              "encode_predict": round(xb / ms_encp / 1e6, 2),
@@ -758,7 +768,8 @@ def run_sensor(args, compact=False):
         "ms_per_step": round(ms_enc + ms_dec, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "i16", "data": "synthetic",
         "config": {"workload": "int16 sensor trace (262,144 samples, seed 0), fixed rate 4:1, N=256; "
-                               "throughput on 8,192 copies (4 GiB)", "l2": "inputs larger than L2"},
+                               "throughput on 8,192 copies (4 GiB)", "l2": "inputs larger than L2",
+                   "input_sha256": in_sha},
         "single_call_us": {"encode": round(lat_enc * 1e3, 2), "decode": round(lat_dec * 1e3, 2)},
         "single_call_gbs": {"encode": round(t.numel() * 2 / lat_enc / 1e6, 2),
                             "decode": round(t.numel() * 2 / lat_dec / 1e6, 2)},
@@ -788,6 +799,7 @@ def run_field3d(args, compact=False):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     xh = synth.field3d(args.field3d_n, seed=2).reshape(-1)
+    in_sha = synth.sha256(xh)
     x = torch.from_numpy(xh).to(dev)
     n, xb = x.numel(), x.numel() * 8
     target = 0.99999
@@ -827,6 +839,7 @@ def run_field3d(args, compact=False):
     if compact:
         return {"workload": f"float64 {args.field3d_n}^3 k^-4 field + 4 blobs (seed 2, 1 GiB): "
                             "profile 16 codes -> fixed quality at r>=0.99999 -> decode",
+                "input_sha256": in_sha,
                 "gbs_step_uncompressed": round(xb / step / 1e6, 2),
                 "ms": {k: round(v, 3) for k, v in ms.items()},
                 "gbs_uncompressed": {k: round(xb / v / 1e6, 2) for k, v in ms.items()},
@@ -842,7 +855,7 @@ def run_field3d(args, compact=False):
         "data": "synthetic",
         "config": {"workload": f"float64 {args.field3d_n}^3 k^-4 field + 4 blobs (seed 2): profile 16 "
                                "codes -> fixed quality at r>=0.99999 -> decode, one call each",
-                   "bytes": xb, "l2": "inputs larger than L2"},
+                   "bytes": xb, "l2": "inputs larger than L2", "input_sha256": in_sha},
         "ms": {k: round(v, 3) for k, v in ms.items()},
         "gbs_uncompressed": {k: round(xb / v / 1e6, 2) for k, v in ms.items()},
         "hbm_frac": {"encode": (xb + r.bytes) / ms["encode"] / 1e6 / peak,
@@ -898,13 +911,15 @@ def run_formats(args):
                          "decode_gbs_uncompressed": round(xb / ms_d / 1e6, 2)}
         return res
 
-    field = torch.from_numpy(synth.grf2d(4096, 4096, seed=1).reshape(-1)).to(dev)
+    fh, nh = synth.grf2d(4096, 4096, seed=1).reshape(-1), synth.nyquist_trace()
+    field = torch.from_numpy(fh).to(dev)
     out = {"workload": "float32 4096x4096 field (seed 1), fixed quality code 2048, N=256; "
                        "int16 Nyquist-band trace (sensor trace x (-1)^i, seed 0), 1,024 copies, "
                        "code 0 (lossless), N=256",
+           "input_sha256": {"field": synth.sha256(fh), "nyquist_trace": synth.sha256(nh)},
            "field_f32_code2048": one(field, A.F32, 2048)}
     del field
-    tr = torch.from_numpy(synth.nyquist_trace()).to(dev).repeat(1024)
+    tr = torch.from_numpy(nh).to(dev).repeat(1024)
     out["nyquist_i16_lossless"] = one(tr, A.I16, 0)
     return out
 
@@ -926,9 +941,12 @@ def run_serving(args, compact=False):
     seconds = 10.0 if compact else args.serve_seconds
     trace = synth.serving_trace(seconds)
     # device-resident payload pools (float32 field, int16 trace), 4 GB each
-    field = torch.from_numpy(synth.grf2d(4096, 4096, seed=1).reshape(-1)).to(dev)
-    pool = {"float32": field.repeat(16),
-            "int16": torch.from_numpy(synth.sensor_trace(1 << 25, seed=0)).to(dev).repeat(64)}
+    fh, th = synth.grf2d(4096, 4096, seed=1).reshape(-1), synth.sensor_trace(1 << 25, seed=0)
+    # the requests are slices of the pools (16 and 64 copies of these)
+    in_sha = synth.sha256(fh, th, repr(trace))
+    field = torch.from_numpy(fh).to(dev)
+    pool = {"float32": field.repeat(16), "int16": torch.from_numpy(th).to(dev).repeat(64)}
+    del th
     # the profiler's choice for the field (fixed quality at r >= 0.9999)
     pts, summ = A.profile(field, N_BLOCK, A.DEFAULT_CANDIDATES, TARGET)
     code = int(summ.recommended_code)
@@ -1009,6 +1027,7 @@ def run_serving(args, compact=False):
         return {"workload": f"serving: Poisson 2000 req/s for {seconds:g} s ({len(reqs)} requests, "
                             f"{total / 1e9:.1f} GB), 50/50 encode/decode, 64 KB..256 MB float32 "
                             f"(fixed quality, code {code}) / int16 (4:1) (seed 4)",
+                "input_sha256": in_sha,
                 "open_loop": {"gbs": round(gbs_open, 3), "offered_gbs": round(total / seconds / 1e9, 3),
                               "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
                               "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3)},
@@ -1021,7 +1040,8 @@ def run_serving(args, compact=False):
         "config": {"workload": f"serving: Poisson 2000 req/s for {seconds:g} s, 50/50 "
                                "encode/decode, 64 KB..256 MB float32 (fixed quality, code "
                                f"{code}) / int16 (4:1), 64 GB admission cap (seed 4)",
-                   "requests": len(reqs), "bytes": total, "slots": 4, "max_batch": 256},
+                   "requests": len(reqs), "bytes": total, "slots": 4, "max_batch": 256,
+                   "input_sha256": in_sha},
         "open_loop": {"gbs": round(gbs_open, 3), "offered_gbs": round(total / seconds / 1e9, 3),
                       "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
                       "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3),

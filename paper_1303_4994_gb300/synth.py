@@ -84,6 +84,15 @@ def digest(x: np.ndarray) -> str:
     return hashlib.sha256(np.ascontiguousarray(x).tobytes()).hexdigest()[:16]
 
 
+def sha256(*parts) -> str:
+    """SHA-256 of arrays (their bytes, C order) and strings, in order: the
+    fingerprint of a workload's generated inputs in the benchmark results."""
+    h = hashlib.sha256()
+    for x in parts:
+        h.update(x.encode() if isinstance(x, str) else np.ascontiguousarray(x).tobytes())
+    return h.hexdigest()
+
+
 # Workloads named by what they are (used by tests and the benchmark).
 SENSOR_I16 = dict(name="int16 sensor trace 262144 samples, fixed rate 4:1",
                   n=262144, block_size=256, rate=(4, 1))
