@@ -253,8 +253,9 @@ int apax_profile_format(const void *x, int dtype, uint64_t n, uint32_t block_siz
  * cudaHostAlloc), leaving its copy in x_dev (device, n elements of dtype):
  * the array goes to the device in `chunks` pieces (1..64, whole runs of 16
  * blocks each) with cudaMemcpyAsync on copy_stream, and each piece is swept
- * (by the sweep with a team of threads per block, whose short per-block
- * latency ends each piece's sweep soon after it lands)
+ * (with more than one piece by the sweep with a team of threads per block,
+ * whose short per-block latency ends each piece's sweep soon after it
+ * lands; one piece takes apax_profile's own sweep once it is there)
  * as soon as it is there, on one of sixteen library-owned streams (created on
  * first use per device and kept for the process's CUDA context, so not
  * valid across cudaDeviceReset), so the copy hides behind the sweep.  The copies and
