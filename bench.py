@@ -13,8 +13,10 @@ runs the step from pinned host memory through the public calls: the
 host-input sweep (the array crosses in pieces on a copy stream while pieces
 already there are swept), encode, decode, and the copy of the container, the
 profile points and the decoded array back; two steps are in flight (a
-stream of arrays), and the one-step-at-a-time time is reported beside it.  `cpu_baseline` is the oracle on
-every host core (threads over block ranges) and, beside it, on one core.
+stream of arrays), and the one-step-at-a-time time is reported beside it.
+`cpu_baseline` is the oracle on every host core (threads over block ranges)
+and, beside it, on one core.  Every workload's results carry
+`input_sha256`, the fingerprint of its generated inputs.
 At N = 1 the default run also measures (`workloads`) the int16 sensor trace
 at 4:1, the float64 512^3 field, the version-2 container formats, the
 batched workload (all 8,192 arrays, 3 timed runs of each operation) and the
