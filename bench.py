@@ -511,6 +511,26 @@ def cpu_baseline(rows: int = CPU_ROWS, threads=0, x=None):
             "seconds": round(dt, 2)}
 
 
+def oracle_codec(x, mode, num, den, code, sample):
+    """The oracle's encode and decode GB/s of uncompressed data on a bounded
+    sample x (host array) of a workload, on every host core (threads over
+    block ranges) and on one core; a baseline beside the GPU numbers."""
+    import oracle as O
+
+    out = {"unit": "GB/s", "kind": "oracle", "cpu": cpu_model(), "nproc": os.cpu_count(),
+           "sample": sample}
+    for name, threads in (("all_cores", 0), ("one_core", None)):
+        t0 = time.perf_counter()
+        c = O.encode(x, N_BLOCK, mode, num, den, code, threads=threads)
+        t1 = time.perf_counter()
+        O.decode(c, x.dtype, x.size, threads=threads)
+        t2 = time.perf_counter()
+        out[name] = {"encode": round(x.nbytes / (t1 - t0) / 1e9, 5),
+                     "decode": round(x.nbytes / (t2 - t1) / 1e9, 5),
+                     "cores": 1 if threads is None else O.threads(threads)}
+    return out
+
+
 def run_reference(args, rank, world):
     """The reference arm: the oracle (the paper has no code to install) on
     the host cores, on the same sample as cpu_baseline, one sample per step."""
@@ -752,10 +772,13 @@ def run_sensor(args, compact=False):
     assert A.read_result(erp).status == 0 and A.read_result(erp).bytes == cb
     peak, peak_kind = _peaks()
     enc_gbs, dec_gbs = (xb + cb) / ms_enc / 1e6, (xb + cb) / ms_dec / 1e6
+    ocodec = oracle_codec(th, A.FIXED_RATE, 4, 1, 0,
+                          "the whole 262,144-sample trace (512 KB), fixed rate 4:1, BISECT")
     if compact:
         return {"workload": "int16 sensor trace (262,144 samples, seed 0), fixed rate 4:1, N=256; "
                             "4 GiB = 8,192 copies for throughput",
                 "input_sha256": in_sha,
+                "oracle_codec": ocodec,
                 "single_call_us": {"encode": round(lat_enc * 1e3, 2), "decode": round(lat_dec * 1e3, 2)},
                 "replica_gbs_uncompressed": {"encode_bisect": round(xb / ms_enc / 1e6, 2),
                                              "encode_predict": round(xb / ms_encp / 1e6, 2),
@@ -772,6 +795,7 @@ def run_sensor(args, compact=False):
         "config": {"workload": "int16 sensor trace (262,144 samples, seed 0), fixed rate 4:1, N=256; "
                                "throughput on 8,192 copies (4 GiB)", "l2": "inputs larger than L2",
                    "input_sha256": in_sha},
+        "oracle_codec": ocodec,
         "single_call_us": {"encode": round(lat_enc * 1e3, 2), "decode": round(lat_dec * 1e3, 2)},
         "single_call_gbs": {"encode": round(t.numel() * 2 / lat_enc / 1e6, 2),
                             "decode": round(t.numel() * 2 / lat_dec / 1e6, 2)},
@@ -838,10 +862,14 @@ def run_field3d(args, compact=False):
         ms = {k: timed(f, args.steps) for k, f in (("profile", prof), ("encode", enc), ("decode", dec))}
     peak, peak_kind = _peaks()
     step = sum(ms.values())
+    code = int(pt.code)
+    ocodec = oracle_codec(xh[:1 << 21], A.FIXED_QUALITY, 1, 1, code,
+                          f"first 2,097,152 elements (16 MiB) of the field, fixed quality at code {code}")
     if compact:
         return {"workload": f"float64 {args.field3d_n}^3 k^-4 field + 4 blobs (seed 2, 1 GiB): "
                             "profile 16 codes -> fixed quality at r>=0.99999 -> decode",
                 "input_sha256": in_sha,
+                "oracle_codec": ocodec,
                 "gbs_step_uncompressed": round(xb / step / 1e6, 2),
                 "ms": {k: round(v, 3) for k, v in ms.items()},
                 "gbs_uncompressed": {k: round(xb / v / 1e6, 2) for k, v in ms.items()},
@@ -858,6 +886,7 @@ def run_field3d(args, compact=False):
         "config": {"workload": f"float64 {args.field3d_n}^3 k^-4 field + 4 blobs (seed 2): profile 16 "
                                "codes -> fixed quality at r>=0.99999 -> decode, one call each",
                    "bytes": xb, "l2": "inputs larger than L2", "input_sha256": in_sha},
+        "oracle_codec": ocodec,
         "ms": {k: round(v, 3) for k, v in ms.items()},
         "gbs_uncompressed": {k: round(xb / v / 1e6, 2) for k, v in ms.items()},
         "hbm_frac": {"encode": (xb + r.bytes) / ms["encode"] / 1e6 / peak,
