@@ -70,6 +70,21 @@ def test_t1_candidate_counts(cands):
     _check(x, 64, cands)
 
 
+def test_t1_error_sum_at_its_bound():
+    # blocks of +-(2^23 - 1) (block exponent 23, X = x): at k = 1 every sample
+    # has q = RNE(X / 2) on a tie, so (q0 - 2 q) q = -2^22 and a block's
+    # 32-bit error sum reaches -2^30; the other codes and blocks of a walk
+    # (k up to 22) around them
+    rng = np.random.default_rng(41)
+    N = 256
+    x = _walk(N * MIN_BLOCKS + 3 * N, seed=41, scale=1000.0)
+    m = np.float32(2 ** 23 - 1)
+    for b in range(0, MIN_BLOCKS, 97):
+        x[b * N:(b + 1) * N] = np.where(rng.random(N) < 0.5, m, -m)
+    cands = [0, 128] + [256 * k for k in range(1, 12)]
+    _check(x, N, cands)
+
+
 def test_t1_image_field_full_ladder():
     x = synth.grf2d(1024, 1024, seed=5).reshape(-1)  # 16,384 blocks of 64
     _check(x, 64, list(A.DEFAULT_CANDIDATES))
