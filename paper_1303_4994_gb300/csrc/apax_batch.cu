@@ -72,10 +72,14 @@ namespace {
 std::mutex g_tune_mu;
 std::map<std::string, apax_batch_config> g_tune_cache;
 
-// Copy one table into the workspace.
+// Copy one table into the workspace.  A plan's copy from pageable memory
+// can return before its DMA lands: the wait after it lets work on any
+// stream (non-blocking ones too) see the table.
 bool upload(apax_batch *b, void *dst, const void *src, size_t bytes)
 {
-    if (!b->pinned) return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!b->pinned)
+        return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
+               cudaStreamSynchronize(0) == cudaSuccess;
     const size_t off = align_up(b->pinned_used, 16);
     if (off + bytes > b->pinned_bytes) return false;
     memcpy(b->pinned + off, src, bytes);
