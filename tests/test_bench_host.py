@@ -14,7 +14,6 @@ def test_profile_figures_parse():
     assert isinstance(t, int) and 67_108_864 <= t < 2 * 67_108_864  # about one read of 64 MiB
     for f in (bench._issue_active("profile"), bench._fma_heavy("profile")):
         assert isinstance(f, float) and 0.0 < f < 1.0
-    assert isinstance(bench._traffic("encode"), int) and isinstance(bench._traffic("decode"), int)
     assert bench._traffic("no_such_kernel") is None and bench._issue_active("encode") is None
 
 
