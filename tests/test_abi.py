@@ -173,3 +173,20 @@ def test_batch_argument_checks(lib):
     fr = _batch_ws([_job(n=1 << 20, p=A.params(256, A.FIXED_RATE, (4, 1)), cap=1 << 22)])[1]
     fq = _batch_ws([_job(n=1 << 20, cap=1 << 23)])[1]
     assert fq > fr
+
+
+def test_copy_container_argument_checks(lib):
+    # host-side checks of apax_copy_container (nothing is launched): null or
+    # misaligned pointers and overlapping source and destination are refused,
+    # an empty destination is a no-op
+    f = lib.apax_copy_container
+    src, res, dst = 0x10000, 0x20000, 0x40000
+    assert f(None, res, dst, 64, None) == -1
+    assert f(src, None, dst, 64, None) == -1
+    assert f(src, res, None, 64, None) == -1
+    assert f(src + 2, res, dst, 64, None) == -1   # source not 4-byte aligned
+    assert f(src, res, dst + 1, 64, None) == -1   # destination not 4-byte aligned
+    assert f(src, res + 4, dst, 64, None) == -1   # result not 8-byte aligned
+    assert f(src, res, src + 32, 64, None) == -1  # destination inside the source span
+    assert f(src + 32, res, src, 64, None) == -1  # and the other way round
+    assert f(src, res, dst, 0, None) == 0         # nothing to copy
