@@ -86,12 +86,13 @@ def test_cpu_model_named():
 
 
 def test_committed_traffic_figures_are_read():
-    # the roofline's `traffic` comes from the committed ncu summary: each
-    # kernel of the step has a per-launch DRAM figure, and the sweep's is
-    # close to one read of the 64 MiB input (no re-reads)
+    # the roofline's `traffic` comes from the committed ncu summary: the
+    # dominant kernel (the sweep) has a per-launch DRAM figure close to one
+    # read of the 64 MiB input (no re-reads); a kernel changed since its
+    # capture has none (null in the bench line)
     xb = 4096 * 4096 * 4
-    for k in ("profile", "encode", "decode"):
-        t = bench._traffic(k)
-        assert isinstance(t, int) and t > 0, k
     assert xb <= bench._traffic("profile") < 1.1 * xb
+    for k in ("encode", "decode"):
+        t = bench._traffic(k)
+        assert t is None or (isinstance(t, int) and t > 0), k
     assert bench._traffic("no_such_kernel") is None
